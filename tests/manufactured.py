@@ -1,0 +1,84 @@
+"""Manufactured solution of the accuracy tests (Sec. 4.1): exact s, c and the
+source terms f1, f2 that make them solve the sulfation system, derived
+symbolically from Eq. maineq with phi(c) = alpha c + beta."""
+import functools
+
+import numpy as np
+import sympy as sp
+
+
+@functools.lru_cache(maxsize=None)
+def _funcs(params):
+    a, d, m_s, m_c, alpha, beta = params
+    x, y, t = sp.symbols("x y t", real=True)
+    s = 2 + sp.sin(x) * sp.cos(y) * sp.sin(t + sp.sqrt(2))
+    c = 3 + sp.sin(sp.Rational(1, 2) * x) * sp.cos(3 * y) * sp.sin(2 * t + sp.sqrt(3))
+    phi = alpha * c + beta
+    f1 = sp.diff(phi * s, t) + (a / m_c) * phi * s * c - d * (sp.diff(phi * sp.diff(s, x), x) +
+                                                               sp.diff(phi * sp.diff(s, y), y))
+    f2 = sp.diff(c, t) + (a / m_s) * phi * s * c
+    mk = lambda e: sp.lambdify((x, y, t), e, "numpy")  # noqa: E731
+    return mk(s), mk(c), mk(f1), mk(f2)
+
+
+def exact(params, X, Y, t):
+    fs, fc, _, _ = _funcs(tuple(params))
+    return fs(X, Y, t) + 0 * X, fc(X, Y, t) + 0 * X
+
+
+def sources(params, X, Y, t):
+    _, _, f1, f2 = _funcs(tuple(params))
+    return f1(X, Y, t) + 0 * X, f2(X, Y, t) + 0 * X
+
+
+def run_oracle(oracle_mod, phi, N, lo, hi, params, T=1.0, dt_factor=1.0):
+    """Advance the oracle from the exact data at t = 0 to t = T with dt = h (the
+    paper's choice, Sec. 4) and return (s, c, type, X, Y)."""
+    import workloads
+
+    X, Y = workloads.node_coords(2, lo, hi, N)
+    h = (hi - lo) / N
+    nsteps = int(round(T / (dt_factor * h)))
+    dt = T / nsteps
+    o = oracle_mod.Oracle(phi, 2, lo, hi, N)
+    full = tuple(params) + (1.0, 0.0, 0.0)
+    o.set_model(full)
+    o.set_solver(newton_tol=1e-11)
+    s0, c0 = exact(params, X, Y, 0.0)
+    o.set_state(s0, c0, 0.0)
+    g = o.level_ghosts(0)
+    for k in range(nsteps):
+        t0, t1 = k * dt, (k + 1) * dt
+        f1o, f2o = sources(params, X, Y, t0)
+        f1n, f2n = sources(params, X, Y, t1)
+        o.set_sources(f1o, f1n, f2o, f2n)
+        sb, _ = exact(params, g["B"][:, 0], g["B"][:, 1], t1)
+        o.set_ghost_sb(sb)
+        o.step(dt, 1)
+    s, c, ty = o.get_state()
+    return s, c, ty, X, Y, nsteps * dt
+
+
+def rel_errors(params, s, c, ty, X, Y, T, h):
+    """Relative L1 and Linf errors of s and c on inside nodes, and of |grad s|,
+    |grad c| by central differences on inside nodes whose four neighbours are
+    active (Sec. 4.1)."""
+    se, ce = exact(params, X, Y, T)
+    ins = ty == 1
+    out = {}
+    for name, num, ex in (("s", s, se), ("c", c, ce)):
+        e = np.abs(num - ex)[ins]
+        out[name + "_inf"] = e.max() / np.abs(ex[ins]).max()
+        out[name + "_1"] = e.sum() / np.abs(ex[ins]).sum()
+        gx = (np.roll(num, -1, 1) - np.roll(num, 1, 1)) / (2 * h)
+        gy = (np.roll(num, -1, 0) - np.roll(num, 1, 0)) / (2 * h)
+        ex_gx = (np.roll(ex, -1, 1) - np.roll(ex, 1, 1)) / (2 * h)
+        ex_gy = (np.roll(ex, -1, 0) - np.roll(ex, 1, 0)) / (2 * h)
+        gn = np.sqrt(gx ** 2 + gy ** 2)
+        ge = np.sqrt(ex_gx ** 2 + ex_gy ** 2)
+        act = (ty == 1) | (ty == 2)
+        ok = ins & np.roll(act, 1, 0) & np.roll(act, -1, 0) & np.roll(act, 1, 1) & np.roll(act, -1, 1)
+        eg = np.abs(gn - ge)[ok]
+        out["g" + name + "_inf"] = eg.max() / np.abs(ge[ok]).max()
+        out["g" + name + "_1"] = eg.sum() / np.abs(ge[ok]).sum()
+    return out
