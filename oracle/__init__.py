@@ -74,6 +74,8 @@ def _load():
         "oracle_prolong": (ctypes.c_int, [P, ctypes.c_int, dp, dp]),
         "oracle_inject": (ctypes.c_int, [P, dp, ctypes.c_int, dp]),
         "oracle_cycles": (ctypes.c_int, [P, ctypes.c_double, dp, dp, dp, ctypes.c_int, dp]),
+        "oracle_coarsest_matrix": (ctypes.c_int, [P, ctypes.c_double, dp, dp]),
+        "oracle_coarsest_solve": (ctypes.c_int, [P, ctypes.c_double, dp, dp, dp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -281,6 +283,20 @@ class Oracle:
         out = np.zeros(2 * self.level_info(l)["n"] ** self.dim)
         self._chk(self.lib.oracle_inject(self.h, _d(Wc0), l, _d(out)))
         return out
+
+    def coarsest_matrix(self, dt, Wc0):
+        nact = self.level_info(self.nlev - 1)["nact"]
+        A = np.zeros((2 * nact, 2 * nact))
+        Wc0 = np.ascontiguousarray(Wc0, dtype=np.float64)
+        self.lib.oracle_coarsest_matrix(self.h, dt, _d(Wc0), _d(A))
+        return A
+
+    def coarsest_solve(self, dt, Wc0, rhs_c):
+        Wc0 = np.ascontiguousarray(Wc0, dtype=np.float64)
+        rhs_c = np.ascontiguousarray(rhs_c, dtype=np.float64)
+        x = np.zeros_like(rhs_c)
+        self._chk(self.lib.oracle_coarsest_solve(self.h, dt, _d(Wc0), _d(rhs_c), _d(x)))
+        return x
 
     def cycles(self, dt, Wc0, rhs, x, ncycles):
         Wc0 = np.ascontiguousarray(Wc0, dtype=np.float64)

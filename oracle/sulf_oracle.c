@@ -925,15 +925,22 @@ static int lu_factor(double *A, int *piv, int m)
     return OR_OK;
 }
 
+/* solve A x = b from the factors of lu_factor: the factorisation swapped whole
+   rows, so P A = L U with P the product of the interchanges; apply them all to
+   b in order, then forward substitution with the unit lower L and back
+   substitution with U */
 static void lu_solve(const double *A, const int *piv, int m, double *b)
 {
-    for (int k = 0; k < m; k++) {
+    for (int k = 0; k < m; k++)
         if (piv[k] != k) {
             double t = b[k];
             b[k] = b[piv[k]];
             b[piv[k]] = t;
         }
-        for (int i = k + 1; i < m; i++) b[i] -= A[(long)i * m + k] * b[k];
+    for (int i = 1; i < m; i++) {
+        double s = b[i];
+        for (int k = 0; k < i; k++) s -= A[(long)i * m + k] * b[k];
+        b[i] = s;
     }
     for (int i = m - 1; i >= 0; i--) {
         double s = b[i];
@@ -1512,5 +1519,35 @@ int oracle_cycles(void *h, double dt, const double *Wc0, const double *rhs, doub
         rnorms[k] = maxabs_active(L, L->res);
     }
     memcpy(x, L->x, sizeof(double) * 2 * L->nn);
+    return OR_OK;
+}
+
+/* the assembled Jacobian of the coarsest level after injecting the finest Wc0
+   (2*nact rows, active nodes in box order, (s,c) interleaved); returns nact */
+int oracle_coarsest_matrix(void *h, double dt, const double *Wc0, double *A_out)
+{
+    Oracle *O = (Oracle *)h;
+    O->dt = dt;
+    memcpy(O->lev[0].Wc, Wc0, sizeof(double) * 2 * O->lev[0].nn);
+    for (int l = 1; l < O->L; l++) inject_Wc(&O->lev[l - 1], &O->lev[l]);
+    OLevel *C = &O->lev[O->L - 1];
+    assemble_dense(O, C);
+    memcpy(A_out, C->A, sizeof(double) * 4 * (size_t)C->nact * C->nact);
+    return C->nact;
+}
+
+/* solve the coarsest level's system for a given right-hand side (level-sized,
+   interleaved), after injecting the finest Wc0 and factoring */
+int oracle_coarsest_solve(void *h, double dt, const double *Wc0, const double *rhs_c, double *x_c)
+{
+    Oracle *O = (Oracle *)h;
+    O->dt = dt;
+    memcpy(O->lev[0].Wc, Wc0, sizeof(double) * 2 * O->lev[0].nn);
+    int rc = prepare_hierarchy(O);
+    if (rc) return rc;
+    OLevel *C = &O->lev[O->L - 1];
+    memcpy(C->rhs, rhs_c, sizeof(double) * 2 * C->nn);
+    coarsest_solve(C);
+    memcpy(x_c, C->x, sizeof(double) * 2 * C->nn);
     return OR_OK;
 }

@@ -206,6 +206,25 @@ def test_multigrid_converges_to_dense_solution(oracle_mod, geom, N):
     assert rn[-1] <= 1e-10 * np.abs(F).max()
 
 
+@pytest.mark.parametrize("dim,N,mk", [(2, 64, lambda: workloads.disk(64)), (3, 32, lambda: workloads.rounded_box(32))])
+def test_coarsest_solve_matches_dense_solve(oracle_mod, dim, N, mk):
+    """the coarsest-level direct solve (R12) equals numpy's solve of the same
+    assembled Jacobian"""
+    o = _oracle(oracle_mod, mk(), dim, N)
+    rng = np.random.default_rng(9)
+    W, _ = _rand_state(rng, o.level_type(0))
+    A = o.coarsest_matrix(2.0 / N, W)
+    tc = o.level_type(o.nlev - 1)
+    ac = np.nonzero((tc == 1) | (tc == 2))[0]
+    b = np.zeros(2 * tc.size)
+    b[0::2][ac] = rng.standard_normal(len(ac))
+    b[1::2][ac] = rng.standard_normal(len(ac))
+    x = o.coarsest_solve(2.0 / N, W, b)
+    xd = np.linalg.solve(A, np.stack([b[0::2][ac], b[1::2][ac]], 1).ravel())
+    xm = np.stack([x[0::2][ac], x[1::2][ac]], 1).ravel()
+    assert np.abs(xm - xd).max() <= 1e-12 * np.abs(xd).max()
+
+
 def _orders(errs):
     e = np.array(errs)
     return np.log2(e[:-1] / e[1:])
