@@ -1,0 +1,150 @@
+/*
+ * sulfmg.h -- C ABI of the GB300 (sm_103a) Newton-multigrid solver for the
+ * marble-sulfation system of Coco, Semplice and Serra Capizzano,
+ * "A level-set multigrid technique for nonlinear diffusion in the numerical
+ * simulation of marble degradation under chemical pollutants" (arXiv:1902.07029).
+ *
+ * One handle = one domain: a level set sampled on the nodes of a uniform grid
+ * over the box [lo,hi]^dim (dim = 2 or 3) with N intervals per axis (N+1 nodes,
+ * h = (hi-lo)/N, Sec. 3.3).  The library keeps the state (s, c) of every active
+ * node, the multigrid hierarchy and all work arrays resident in device memory
+ * and advances the state by Crank-Nicolson steps (Sec. 3.1, Eq. discTime), each
+ * solved by Newton-Raphson (Sec. 3.4) with a level-set multigrid inner solver
+ * (Sec. 3.5).  Every stage runs in the library's own CUDA kernels.
+ *
+ * Conventions
+ *   - Grid arrays are (N+1)^dim values, x fastest, then y, then z.
+ *   - Node types: 0 inactive, 1 inside (phi < 0), 2 ghost (Eq. ghostdef).
+ *   - Host pointers are caller-owned; the library copies what it needs and
+ *     never keeps them.  Device memory is owned by the library.
+ *   - Every int-returning call returns SULF_OK (0) or a negative error code and
+ *     records a message readable with sulf_last_error() (per thread).
+ *   - Calls on one handle must not overlap; different handles are independent.
+ *   - Device work is issued on the handle's stream (sulf_set_stream); calls
+ *     that return host data synchronise that stream.
+ */
+#ifndef SULFMG_H
+#define SULFMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SULF_OK 0
+#define SULF_EINVAL (-1)   /* bad argument or geometry (domain on the box edge, no inside node, N not coarsest*2^k) */
+#define SULF_ENOMEM (-2)   /* device or host allocation failed */
+#define SULF_ENOTCONV (-3) /* Newton did not reach its tolerance within max_newton iterations, or produced NaN */
+#define SULF_EGEOM (-4)    /* a finest-level ghost has no usable boundary stencil (Sec. 3.3: h too coarse) */
+#define SULF_EDEVICE (-5)  /* CUDA error (no device, launch failure, ...) */
+
+typedef struct sulf_domain* sulf_handle;
+
+/* Model parameters of Eq. maineq with porosity phi(c) = alpha c + beta (Sec. 2);
+   the paper's values are Eq. dataeq: a = 1e4, d = 0.1, m_s = 64.06,
+   m_c = 100.09, alpha = 0.01, beta = 0.1.  s_ext is the Dirichlet value s_b on
+   the boundary; s0, c0 the uniform initial data (Eq. BCnumtests: 0, 10, 1). */
+typedef struct {
+    double a, d, m_s, m_c, alpha, beta;
+    double s_ext;
+    double s0, c0;
+} sulf_model;
+
+/* Solver controls.
+   nu1, nu2      pre- and post-relaxation sweeps (Sec. 3.5)            default 2, 2
+   cycle         1 = V-cycle, 2 = W-cycle                              default 1
+   max_newton    Newton iteration cap per step                         default 20
+   max_cycles    multigrid cycle cap per linear solve                  default 30
+   ghost_sweeps  passes of the ghost relaxation (Eq. RelGhost) per sweep default 4
+   newton_tol    Newton stops when min(|F|_inf, |dW|_inf/|W|_inf) < tol (Sec. 3.4)  default 1e-10
+   lin_rtol      cycles stop when |r|_inf <= lin_rtol |F|_inf           default 1e-10
+   tau_s         ghost relaxation parameter, 0 < tau_s < 1 (Eq. CFLcond)  default 0.9
+   precision     0 = FP64 throughout; 1 = FP32 multigrid cycles inside FP64
+                 defect correction (Newton residual, boundary rows of F and
+                 the convergence tests stay FP64)                        default 0
+   smoother      0 = collective (2x2 block, Eq. matrixP) red-black Gauss-Seidel,
+                 1 = pointwise (Eq. matrixPclassical) red-black            default 0 */
+typedef struct {
+    int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
+    double newton_tol, lin_rtol, tau_s;
+    int precision, smoother;
+} sulf_solver;
+
+/* Counters and timings of the handle. */
+typedef struct {
+    double t;               /* current time */
+    int newton_last;        /* Newton iterations of the last step */
+    int cycles_last;        /* multigrid cycles of the last step */
+    long long newton_total, cycles_total, steps_total;
+    double last_rho;        /* last cycle's residual reduction factor */
+    double last_fnorm;      /* |F|_inf after the last Newton iteration */
+    long long kernel_launches; /* kernels this handle has launched */
+    int levels;             /* multigrid levels */
+    long long n_inside, n_ghost; /* finest-level inside and ghost nodes (Eq. ghostdef) */
+    int ghost_rows[3];      /* finest-level ghost rows: quadratic, linear, identity */
+} sulf_stats;
+
+/* Build a domain.  levelset: host array of (N+1)^dim node values of phi
+   (Omega = {phi < 0}, Sec. 3.2), copied.  box: host array {lo, hi}; the grid is
+   [lo,hi]^dim.  N: intervals per axis, N = coarsest_N * 2^k with k >= 0; the
+   hierarchy has k+1 levels, coarsened by injection of phi (Sec. 3.5.3).
+   coarsest_N >= 2 (the paper uses 8, Sec. 4).  Classifies inside and ghost
+   nodes, builds each ghost's boundary row (normal by Eq. nij, closest point on
+   Gamma by bisection, weights of Eq. JssD) on every level.  The state is set to
+   the default model's initial data.  Errors: SULF_EINVAL, SULF_EGEOM,
+   SULF_ENOMEM, SULF_EDEVICE; *out is NULL on error. */
+int sulf_create_domain(const double* levelset, int dim, const double* box, int N, int coarsest_N,
+                       sulf_handle* out);
+
+/* Set the model (Eq. maineq, Sec. 2) and reset the state to the uniform initial
+   data s = s0, c = c0 on every active node (ghosts included) at t = 0. */
+int sulf_set_model(sulf_handle h, const sulf_model* m);
+
+/* Set the solver controls; NULL restores the defaults.  SULF_EINVAL on values
+   out of range (tau_s must satisfy 0 < tau_s < 1, Eq. CFLcond). */
+int sulf_set_solver(sulf_handle h, const sulf_solver* s);
+
+/* Issue all device work of the handle on this cudaStream_t (NULL: the library's
+   own stream). */
+int sulf_set_stream(sulf_handle h, void* stream);
+
+/* Advance nsteps Crank-Nicolson steps of size dt (Sec. 3.1), each by Newton
+   (Sec. 3.4) with multigrid linear solves (Sec. 3.5).  Blocks until done.
+   SULF_ENOTCONV if a step does not converge (the state is then that of the
+   failed iterate). */
+int sulf_step(sulf_handle h, double dt, int nsteps);
+
+/* Copy the state to caller-owned host arrays of (N+1)^dim entries; any pointer
+   may be NULL.  Inactive nodes read s = c = 0, type = 0. */
+int sulf_get_state(sulf_handle h, double* s, double* c, int8_t* type);
+
+/* Same, into caller-owned device arrays (no host round trip; synchronises). */
+int sulf_get_state_device(sulf_handle h, double* s_dev, double* c_dev);
+
+/* Replace the state from host arrays of (N+1)^dim entries (values at inactive
+   nodes are ignored) and set the time to t: checkpoint/resume. */
+int sulf_set_state(sulf_handle h, const double* s, const double* c, double t);
+
+/* Same, from device arrays. */
+int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_dev, double t);
+
+int sulf_get_stats(sulf_handle h, sulf_stats* out);
+
+/* Kernel timing for measurement: when on, the library brackets every launch of
+   the finest-level inside relaxation (the dominant kernel) with CUDA events on
+   its stream.  sulf_kernel_time returns the summed device time in ms and the
+   number of bracketed launches since the last reset (synchronises). */
+int sulf_set_profiling(sulf_handle h, int on);
+int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
+
+/* Release the handle and its device memory. */
+void sulf_destroy(sulf_handle h);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* sulf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SULFMG_H */

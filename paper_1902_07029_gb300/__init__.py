@@ -1,0 +1,271 @@
+"""GB300-native Newton-multigrid solver for marble sulfation (arXiv:1902.07029).
+
+Thin ctypes binding of the C ABI in ``include/sulfmg.h`` (and the stage-level
+entry points of ``include/sulfmg_debug.h``).  This module only marshals
+arguments: every stage of the method runs in the CUDA kernels of
+``libsulfmg.so``.  There is no CPU fallback -- if the library is missing or no
+GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB_PATH, build  # noqa: F401
+
+OK, EINVAL, ENOMEM, ENOTCONV, EGEOM, EDEVICE = 0, -1, -2, -3, -4, -5
+
+
+class SulfModel(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("a", "d", "m_s", "m_c", "alpha", "beta", "s_ext", "s0", "c0")]
+
+
+class SulfSolver(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("cycle", ctypes.c_int), ("max_newton", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("ghost_sweeps", ctypes.c_int), ("newton_tol", ctypes.c_double),
+                ("lin_rtol", ctypes.c_double), ("tau_s", ctypes.c_double), ("precision", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
+
+
+class SulfStats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("newton_last", ctypes.c_int), ("cycles_last", ctypes.c_int),
+                ("newton_total", ctypes.c_longlong), ("cycles_total", ctypes.c_longlong),
+                ("steps_total", ctypes.c_longlong), ("last_rho", ctypes.c_double), ("last_fnorm", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("levels", ctypes.c_int), ("n_inside", ctypes.c_longlong),
+                ("n_ghost", ctypes.c_longlong), ("ghost_rows", ctypes.c_int * 3)]
+
+
+_lib = None
+P = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+_SIGS = {
+    "sulf_create_domain": (ctypes.c_int, [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]),
+    "sulf_set_model": (ctypes.c_int, [P, ctypes.POINTER(SulfModel)]),
+    "sulf_set_solver": (ctypes.c_int, [P, ctypes.POINTER(SulfSolver)]),
+    "sulf_set_stream": (ctypes.c_int, [P, P]),
+    "sulf_step": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int]),
+    "sulf_get_state": (ctypes.c_int, [P, _dp, _dp, _i8p]),
+    "sulf_get_state_device": (ctypes.c_int, [P, P, P]),
+    "sulf_set_state": (ctypes.c_int, [P, _dp, _dp, ctypes.c_double]),
+    "sulf_set_state_device": (ctypes.c_int, [P, P, P, ctypes.c_double]),
+    "sulf_get_stats": (ctypes.c_int, [P, ctypes.POINTER(SulfStats)]),
+    "sulf_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
+    "sulf_kernel_time": (ctypes.c_int, [P, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "sulf_destroy": (None, [P]),
+    "sulf_last_error": (ctypes.c_char_p, []),
+    "sulf_dbg_level_info": (ctypes.c_int, [P, ctypes.c_int, _i64p]),
+    "sulf_dbg_level_type": (ctypes.c_int, [P, ctypes.c_int, _i8p]),
+    "sulf_dbg_level_ghosts": (ctypes.c_int, [P, ctypes.c_int, _i64p, _i8p, _i8p, _dp, _dp]),
+    "sulf_dbg_eval_F": (ctypes.c_int, [P, ctypes.c_double, _dp, _dp, _dp]),
+    "sulf_dbg_apply_J": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]),
+    "sulf_dbg_smooth": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int]),
+    "sulf_dbg_restrict": (ctypes.c_int, [P, ctypes.c_int, _dp, _dp]),
+    "sulf_dbg_prolong": (ctypes.c_int, [P, ctypes.c_int, _dp, _dp]),
+    "sulf_dbg_inject": (ctypes.c_int, [P, _dp, ctypes.c_int, _dp]),
+    "sulf_dbg_cycles": (ctypes.c_int, [P, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int, _dp]),
+    "sulf_dbg_coarsest_solve": (ctypes.c_int, [P, ctypes.c_double, _dp, _dp, _dp]),
+}
+
+
+def load(path: str | None = None):
+    """Load libsulfmg.so (built in-tree by ``build()``); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsulfmg.so not found at {path}: run paper_1902_07029_gb300.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SulfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sulfmg error {code}: {msg}")
+        self.code = code
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _chk(lib, rc):
+    if rc != OK:
+        raise SulfError(rc, lib.sulf_last_error().decode())
+
+
+def default_solver(**kw) -> SulfSolver:
+    s = SulfSolver(nu1=2, nu2=2, cycle=1, max_newton=20, max_cycles=30, ghost_sweeps=4, newton_tol=1e-10,
+                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0)
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+class Domain:
+    """A level-set domain resident on the GPU (one ``sulf_handle``)."""
+
+    def __init__(self, levelset, dim, box, N, coarsest_N=8):
+        self.lib = load()
+        phi = np.ascontiguousarray(levelset, dtype=np.float64)
+        if phi.size != (N + 1) ** dim:
+            raise ValueError("levelset must hold (N+1)^dim values")
+        b = np.asarray(box, dtype=np.float64)
+        h = P()
+        _chk(self.lib, self.lib.sulf_create_domain(_d(phi), dim, _d(b), N, coarsest_N, ctypes.byref(h)))
+        self.h = h
+        self.dim, self.N = dim, N
+        self.shape = (N + 1,) * dim
+        self.nn = (N + 1) ** dim
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sulf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_model(self, params):
+        m = SulfModel(*[float(v) for v in params])
+        _chk(self.lib, self.lib.sulf_set_model(self.h, ctypes.byref(m)))
+
+    def set_solver(self, **kw):
+        s = default_solver(**kw)
+        _chk(self.lib, self.lib.sulf_set_solver(self.h, ctypes.byref(s)))
+
+    def set_stream(self, stream_handle: int | None):
+        _chk(self.lib, self.lib.sulf_set_stream(self.h, P(stream_handle) if stream_handle else None))
+
+    def step(self, dt, nsteps=1):
+        _chk(self.lib, self.lib.sulf_step(self.h, dt, nsteps))
+
+    def get_state(self):
+        s = np.zeros(self.nn)
+        c = np.zeros(self.nn)
+        t = np.zeros(self.nn, dtype=np.int8)
+        _chk(self.lib, self.lib.sulf_get_state(self.h, _d(s), _d(c), t.ctypes.data_as(_i8p)))
+        return s.reshape(self.shape), c.reshape(self.shape), t.reshape(self.shape)
+
+    def get_state_into(self, s, c):
+        """Host arrays (e.g. pinned torch tensors' numpy views) of nn doubles."""
+        _chk(self.lib, self.lib.sulf_get_state(self.h, _d(s), _d(c), None))
+
+    def get_state_device(self, s_ptr: int, c_ptr: int):
+        _chk(self.lib, self.lib.sulf_get_state_device(self.h, P(s_ptr), P(c_ptr)))
+
+    def set_state(self, s, c, t=0.0):
+        s = np.ascontiguousarray(s, dtype=np.float64).ravel()
+        c = np.ascontiguousarray(c, dtype=np.float64).ravel()
+        _chk(self.lib, self.lib.sulf_set_state(self.h, _d(s), _d(c), t))
+
+    def set_state_device(self, s_ptr: int, c_ptr: int, t=0.0):
+        _chk(self.lib, self.lib.sulf_set_state_device(self.h, P(s_ptr), P(c_ptr), t))
+
+    def stats(self):
+        st = SulfStats()
+        _chk(self.lib, self.lib.sulf_get_stats(self.h, ctypes.byref(st)))
+        return {f[0]: (list(getattr(st, f[0])) if f[0] == "ghost_rows" else getattr(st, f[0])) for f in st._fields_}
+
+    def set_profiling(self, on: bool):
+        _chk(self.lib, self.lib.sulf_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_time(self):
+        ms = ctypes.c_double(0)
+        n = ctypes.c_longlong(0)
+        _chk(self.lib, self.lib.sulf_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    # ---- stage-level entry points (interleaved (s,c) arrays) ----
+    def level_info(self, l):
+        info = np.zeros(9, dtype=np.int64)
+        _chk(self.lib, self.lib.sulf_dbg_level_info(self.h, l, info.ctypes.data_as(_i64p)))
+        return dict(N=int(info[0]), n=int(info[1]), ng=int(info[2]), nb=int(info[3]), nact=int(info[4]),
+                    nin=int(info[5]), kinds=(int(info[6]), int(info[7]), int(info[8])))
+
+    def level_type(self, l):
+        n = self.level_info(l)["n"]
+        t = np.zeros(n ** self.dim, dtype=np.int8)
+        _chk(self.lib, self.lib.sulf_dbg_level_type(self.h, l, t.ctypes.data_as(_i8p)))
+        return t
+
+    def level_ghosts(self, l):
+        ng = self.level_info(l)["ng"]
+        d = self.dim
+        idx = np.zeros(max(ng, 1), dtype=np.int64)
+        kind = np.zeros(max(ng, 1), dtype=np.int8)
+        m = np.zeros(max(ng, 1) * d, dtype=np.int8)
+        w = np.zeros(max(ng, 1) * d * 3)
+        B = np.zeros(max(ng, 1) * d)
+        _chk(self.lib, self.lib.sulf_dbg_level_ghosts(self.h, l, idx.ctypes.data_as(_i64p), kind.ctypes.data_as(_i8p),
+                                                      m.ctypes.data_as(_i8p), _d(w), _d(B)))
+        return dict(idx=idx[:ng], kind=kind[:ng], m=m[:ng * d].reshape(ng, d), w=w[:ng * d * 3].reshape(ng, d, 3),
+                    B=B[:ng * d].reshape(ng, d))
+
+    def eval_F(self, dt, W, Wn):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        Wn = np.ascontiguousarray(Wn, dtype=np.float64)
+        F = np.zeros(2 * self.nn)
+        _chk(self.lib, self.lib.sulf_dbg_eval_F(self.h, dt, _d(W), _d(Wn), _d(F)))
+        return F
+
+    def apply_J(self, l, dt, Wc, x):
+        Wc = np.ascontiguousarray(Wc, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros_like(x)
+        _chk(self.lib, self.lib.sulf_dbg_apply_J(self.h, l, dt, _d(Wc), _d(x), _d(out)))
+        return out
+
+    def smooth(self, l, dt, Wc, rhs, x, sweeps=1):
+        x = np.array(x, dtype=np.float64)
+        Wc = np.ascontiguousarray(Wc, dtype=np.float64)
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        _chk(self.lib, self.lib.sulf_dbg_smooth(self.h, l, dt, _d(Wc), _d(rhs), _d(x), sweeps))
+        return x
+
+    def restrict(self, l, res):
+        res = np.array(res, dtype=np.float64)
+        nc = self.level_info(l + 1)["n"] ** self.dim
+        out = np.zeros(2 * nc)
+        _chk(self.lib, self.lib.sulf_dbg_restrict(self.h, l, _d(res), _d(out)))
+        return out, res
+
+    def prolong(self, l, xc, xf):
+        xc = np.ascontiguousarray(xc, dtype=np.float64)
+        xf = np.array(xf, dtype=np.float64)
+        _chk(self.lib, self.lib.sulf_dbg_prolong(self.h, l, _d(xc), _d(xf)))
+        return xf
+
+    def inject(self, Wc0, l):
+        Wc0 = np.ascontiguousarray(Wc0, dtype=np.float64)
+        out = np.zeros(2 * self.level_info(l)["n"] ** self.dim)
+        _chk(self.lib, self.lib.sulf_dbg_inject(self.h, _d(Wc0), l, _d(out)))
+        return out
+
+    def coarsest_solve(self, dt, Wc0, rhs_c):
+        Wc0 = np.ascontiguousarray(Wc0, dtype=np.float64)
+        rhs_c = np.ascontiguousarray(rhs_c, dtype=np.float64)
+        x = np.zeros_like(rhs_c)
+        _chk(self.lib, self.lib.sulf_dbg_coarsest_solve(self.h, dt, _d(Wc0), _d(rhs_c), _d(x)))
+        return x
+
+    def cycles(self, dt, Wc0, rhs, ncycles):
+        Wc0 = np.ascontiguousarray(Wc0, dtype=np.float64)
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.zeros_like(rhs)
+        rn = np.zeros(ncycles)
+        _chk(self.lib, self.lib.sulf_dbg_cycles(self.h, dt, _d(Wc0), _d(rhs), _d(x), ncycles, _d(rn)))
+        return x, rn

@@ -1,0 +1,1037 @@
+// Newton and multigrid kernels of one Crank-Nicolson step (arXiv:1902.07029,
+// Sec. 3.1, 3.4, 3.5), templated on the dimension D (2 or 3) and the precision
+// T of the multigrid arithmetic (double, or float inside FP64 defect
+// correction).  The Newton residual F and the update always run in FP64.
+//
+// The Jacobian is never stored: every kernel recomputes the coefficients of
+// its rows from the (s, c) pair of the node and its axis neighbours (Eqs.
+// JssI, JscI, JcsI, JccI as exact derivatives of F), so a relaxation sweep
+// moves 16 B of coefficients, 16 B of right-hand side and 16 B of unknowns
+// per node instead of a dozen stored matrix entries.
+#include "sulf_internal.cuh"
+
+namespace sulf {
+
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned nblk(long long n, int t = kT) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T>
+__device__ __forceinline__ unsigned long long abs_bits(T v) {
+    double d = fabs((double)v);
+    return (unsigned long long)__double_as_longlong(d);
+}
+
+// max over the block of non-negative doubles held as bit patterns (NaN, whose
+// pattern exceeds +inf, propagates), then one atomicMax per block
+__device__ __forceinline__ void block_max(unsigned long long v, unsigned long long* out) {
+    __shared__ unsigned long long sm[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
+        v = v > w ? v : w;
+    }
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? sm[lane] : 0ULL;
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
+            v = v > w ? v : w;
+        }
+        if (lane == 0 && v) atomicMax(out, v);
+    }
+}
+
+template <int D>
+struct Offs {
+    long long o[2 * D];
+};
+
+template <int D>
+__host__ __device__ inline Offs<D> make_offs(long long st1, long long st2) {
+    Offs<D> f;
+    f.o[0] = 1;
+    f.o[1] = -1;
+    f.o[2] = st1;
+    f.o[3] = -st1;
+    if (D == 3) {
+        f.o[4 % (2 * D)] = st2;
+        f.o[5 % (2 * D)] = -st2;
+    }
+    return f;
+}
+
+// node of list position t in the concatenation (inside colour 0, inside colour
+// 1, ghosts); kind 1 inside, 2 ghost
+struct Lists {
+    const int* l0;
+    const int* l1;
+    const int* lg;
+    int n0, n1, ng;
+};
+
+__device__ __forceinline__ long long list_node(const Lists& L, int t, int& kind, int& gi) {
+    if (t < L.n0) {
+        kind = 1;
+        return L.l0[t];
+    }
+    t -= L.n0;
+    if (t < L.n1) {
+        kind = 1;
+        return L.l1[t];
+    }
+    t -= L.n1;
+    kind = 2;
+    gi = t;
+    return L.lg[t];
+}
+
+inline Lists make_lists(const LevelGeo& L, bool ghosts = true) {
+    Lists l;
+    l.l0 = L.inl[0];
+    l.l1 = L.inl[1];
+    l.lg = L.gidx;
+    l.n0 = L.nin[0];
+    l.n1 = L.nin[1];
+    l.ng = ghosts ? L.ng : 0;
+    return l;
+}
+
+// J x at an inside node p, and the 2x2 diagonal block P of Eq. matrixP
+template <int D, typename T, typename T2>
+__device__ __forceinline__ void inside_row(long long p, const T2* __restrict__ Wc, const T2* __restrict__ x,
+                                           const Offs<D>& of, const Coef<T>& c, T& Jxs, T& Jxc, T& Pss, T& Psc,
+                                           T& Pcs, T& Pcc, T2& xp) {
+    T2 w = Wc[p];
+    T s = w.x, cp = w.y;
+    T ph = c.alpha * cp + c.beta;
+    xp = x[p];
+    Pss = ph * c.idt + c.a2mc * ph * cp;
+    Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s);
+    Jxs = Pss * xp.x + Psc * xp.y;
+#pragma unroll
+    for (int q = 0; q < 2 * D; q++) {
+        long long pq = p + of.o[q];
+        T2 wq = Wc[pq];
+        T2 xq = x[pq];
+        T g = c.kap * ((c.alpha * wq.y + c.beta) + ph);
+        T e = c.kap * c.alpha * (s - wq.x);
+        Pss += g;
+        Psc += e;
+        Jxs += g * (xp.x - xq.x) + e * (xp.y + xq.y);
+    }
+    Pcs = c.a2ms * ph * cp;
+    Pcc = c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
+    Jxc = Pcs * xp.x + Pcc * xp.y;
+}
+
+// ---------------------------------------------------------------------------
+// relaxation (Sec. 3.5.1)
+
+template <int D, typename T, bool PW>
+__global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt,
+                                                      const typename V2<T>::t* __restrict__ Wc,
+                                                      const typename V2<T>::t* __restrict__ rhs,
+                                                      typename V2<T>::t* __restrict__ x, Offs<D> of, Coef<T> c) {
+    typedef typename V2<T>::t T2;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    long long p = list[t];
+    T Jxs, Jxc, Pss, Psc, Pcs, Pcc;
+    T2 xp;
+    inside_row<D, T, T2>(p, Wc, x, of, c, Jxs, Jxc, Pss, Psc, Pcs, Pcc, xp);
+    T2 b = rhs[p];
+    T rs = b.x - Jxs, rc = b.y - Jxc;
+    T2 out;
+    if (PW) {
+        out.x = xp.x + rs / Pss;
+        out.y = xp.y + rc / Pcc;
+    } else {
+        T det = Pss * Pcc - Psc * Pcs;
+        out.x = xp.x + (Pcc * rs - Psc * rc) / det;
+        out.y = xp.y + (Pss * rc - Pcs * rs) / det;
+    }
+    x[p] = out;
+}
+
+// ghost row s~(B) of ghost gi applied to the s component: sum over the upwind
+// stencil of the tensor-product weights (Eq. JssD).  Ghost members are read
+// from the previous pass's buffer (sin) unless this is the first pass.
+template <int D, typename T>
+__device__ __forceinline__ T ghost_dot(int gi, long long g, const int8_t* __restrict__ gm, const T* __restrict__ gw,
+                                       const int* __restrict__ gpos, const typename V2<T>::t* __restrict__ x,
+                                       const T* __restrict__ sin, bool from_x, long long st1, long long st2) {
+    T wa[3][3];
+    int m[3] = {1, 1, 1};
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        m[a] = gm[(long long)gi * D + a];
+#pragma unroll
+        for (int k = 0; k < 3; k++) wa[a][k] = gw[(long long)gi * 3 * D + 3 * a + k];
+    }
+    long long st[3] = {1, st1, st2};
+    const int K = D == 2 ? 9 : 27;
+    T acc = 0;
+#pragma unroll
+    for (int kk = 0; kk < K; kk++) {
+        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+        T w = wa[0][k0] * wa[1][k1];
+        if (D == 3) w = w * wa[2][k2];
+        if (w == (T)0) continue;
+        long long node = g - m[0] * k0 * st[0] - m[1] * k1 * st[1];
+        if (D == 3) node -= m[2] * k2 * st[2];
+        T v;
+        if (from_x) {
+            v = x[node].x;
+        } else {
+            int gp = gpos[node];
+            v = gp >= 0 ? sin[gp] : x[node].x;
+        }
+        acc += w * v;
+    }
+    return acc;
+}
+
+// one Jacobi pass of the ghost relaxation of Eq. RelGhost: s_g += tau (r_g -
+// row.x) from the previous pass's values, then the ghost c row relaxed by its
+// diagonal with the fresh s_g.  Only the ghost's own thread touches its c.
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict__ gidx, const int* __restrict__ gpos,
+                                                    const int8_t* __restrict__ gm, const T* __restrict__ gw,
+                                                    const typename V2<T>::t* __restrict__ Wc,
+                                                    const typename V2<T>::t* __restrict__ rhs,
+                                                    typename V2<T>::t* x, const T* sin, T* sout, long long st1,
+                                                    long long st2, Coef<T> c, int first, int last) {
+    typedef typename V2<T>::t T2;
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ng) return;
+    long long g = gidx[gi];
+    T acc = ghost_dot<D, T>(gi, g, gm, gw, gpos, x, sin, first != 0, st1, st2);
+    T2 xg = x[g];
+    T s_old = first ? xg.x : sin[gi];
+    T2 b = rhs[g];
+    T s_new = s_old + c.tau * (b.x - acc);
+    T2 w = Wc[g];
+    T ph = c.alpha * w.y + c.beta;
+    T cs = c.a2ms * ph * w.y;
+    T cc = c.idt + c.a2ms * (c.alpha * w.x * w.y + ph * w.x);
+    T c_new = xg.y + (b.y - (cs * s_new + cc * xg.y)) / cc;
+    T* xs = reinterpret_cast<T*>(x + g);
+    xs[1] = c_new;
+    if (last)
+        xs[0] = s_new;
+    else
+        sout[gi] = s_new;
+}
+
+template <typename T>
+__global__ void k_ghost_scatter(int ng, const int* __restrict__ gidx, const T* __restrict__ sin,
+                                typename V2<T>::t* x) {
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ng) return;
+    reinterpret_cast<T*>(x + gidx[gi])[0] = sin[gi];
+}
+
+// ---------------------------------------------------------------------------
+// defect r = rhs - J x on every active node, with its max-norm
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_residual(Lists ls, const int8_t* __restrict__ gm, const T* __restrict__ gw,
+                                                  const typename V2<T>::t* __restrict__ Wc,
+                                                  const typename V2<T>::t* __restrict__ rhs,
+                                                  const typename V2<T>::t* __restrict__ x,
+                                                  typename V2<T>::t* __restrict__ res, Offs<D> of, long long st1,
+                                                  long long st2, Coef<T> c, unsigned long long* norm) {
+    typedef typename V2<T>::t T2;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long nb = 0;
+    if (t < ls.n0 + ls.n1 + ls.ng) {
+        int kind, gi = 0;
+        long long p = list_node(ls, t, kind, gi);
+        T2 b = rhs[p];
+        T2 r;
+        if (kind == 1) {
+            T Jxs, Jxc, Pss, Psc, Pcs, Pcc;
+            T2 xp;
+            inside_row<D, T, T2>(p, Wc, x, of, c, Jxs, Jxc, Pss, Psc, Pcs, Pcc, xp);
+            r.x = b.x - Jxs;
+            r.y = b.y - Jxc;
+        } else {
+            T acc = ghost_dot<D, T>(gi, p, gm, gw, nullptr, x, nullptr, true, st1, st2);
+            T2 w = Wc[p];
+            T2 xp = x[p];
+            T ph = c.alpha * w.y + c.beta;
+            T cs = c.a2ms * ph * w.y;
+            T cc = c.idt + c.a2ms * (c.alpha * w.x * w.y + ph * w.x);
+            r.x = b.x - acc;
+            r.y = b.y - (cs * xp.x + cc * xp.y);
+        }
+        res[p] = r;
+        unsigned long long a0 = abs_bits(r.x), a1 = abs_bits(r.y);
+        nb = a0 > a1 ? a0 : a1;
+    }
+    if (norm) block_max(nb, norm);
+}
+
+// ---------------------------------------------------------------------------
+// extension of the ghost defect into the band along the normal (Sec. 3.5.2):
+// explicit upwind Euler steps of dr/dtau + n.grad r = 0, band values start at 0
+
+template <int D, typename T>
+__global__ void k_extend_step(int nb, const int* __restrict__ bidx, const int* __restrict__ bref,
+                              const T* __restrict__ ban, typename V2<T>::t* res,
+                              const typename V2<T>::t* __restrict__ bin, typename V2<T>::t* __restrict__ bout, T cfl,
+                              int first, int last) {
+    typedef typename V2<T>::t T2;
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    T2 v;
+    if (first) {
+        v.x = 0;
+        v.y = 0;
+    } else {
+        v = bin[b];
+    }
+    T ax = 0, ay = 0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        int ref = bref[(long long)b * D + a];
+        if (ref == -1) continue;
+        T2 u;
+        if (ref >= 0) {
+            if (first) {
+                u.x = 0;
+                u.y = 0;
+            } else {
+                u = bin[ref];
+            }
+        } else {
+            u = res[-(long long)ref - 2];
+        }
+        T an = ban[(long long)b * D + a];
+        ax += an * (v.x - u.x);
+        ay += an * (v.y - u.y);
+    }
+    T2 nv;
+    nv.x = v.x - cfl * ax;
+    nv.y = v.y - cfl * ay;
+    if (last)
+        res[bidx[b]] = nv;
+    else
+        bout[b] = nv;
+}
+
+// ---------------------------------------------------------------------------
+// boundary-aware full weighting (Eqs. Fstencil, Fstencilgen, Fig. Neigh):
+// inside rule at coarse inside nodes, outside rule (ghost or band) at coarse
+// ghosts; per-axis mirrored weights, invalid diagonal weight moved to the centre
+
+__device__ __forceinline__ bool valid_for(int8_t rule, int8_t t) {
+    return rule == T_IN ? t == T_IN : (t == T_GHOST || t == T_BAND);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restrict__ ctype, int cn,
+                                                  const int8_t* __restrict__ ftype, int fn,
+                                                  const typename V2<T>::t* __restrict__ fres,
+                                                  typename V2<T>::t* __restrict__ crhs) {
+    typedef typename V2<T>::t T2;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi;
+    long long I = list_node(ls, t, kind, gi);
+    int8_t rule = ctype[I];
+    int ii[3] = {0, 0, 0};
+    ii[0] = (int)(I % cn);
+    ii[1] = (int)((I / cn) % cn);
+    if (D == 3) ii[2] = (int)(I / ((long long)cn * cn));
+    long long fst[3] = {1, fn, (long long)fn * fn};
+    long long f = 0;
+#pragma unroll
+    for (int a = 0; a < D; a++) f += 2LL * ii[a] * fst[a];
+    T w1[3][3];
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        bool vl = ii[a] > 0 && valid_for(rule, ftype[f - fst[a]]);
+        bool vr = 2 * ii[a] < fn - 1 && valid_for(rule, ftype[f + fst[a]]);
+        T l = 1, m = 2, r = 1;
+        if (vl && !vr) {
+            l = 2; m = 2; r = 0;
+        } else if (!vl && vr) {
+            l = 0; m = 2; r = 2;
+        } else if (!vl && !vr) {
+            l = 0; m = 4; r = 0;
+        }
+        w1[a][0] = l / (T)4;
+        w1[a][1] = m / (T)4;
+        w1[a][2] = r / (T)4;
+    }
+    const int K = D == 2 ? 9 : 27;
+    T as = 0, ac = 0, wc = 0;
+#pragma unroll
+    for (int kk = 0; kk < K; kk++) {
+        const int k0 = kk % 3 - 1, k1 = (kk / 3) % 3 - 1, k2 = kk / 9 - 1;
+        T w = w1[0][k0 + 1] * w1[1][k1 + 1];
+        if (D == 3) w = w * w1[2][k2 + 1];
+        if (w == (T)0) continue;
+        bool centre = k0 == 0 && k1 == 0 && (D == 2 || k2 == 0);
+        if (centre) {
+            wc += w;
+            continue;
+        }
+        long long node = f + k0 * fst[0] + k1 * fst[1];
+        if (D == 3) node += k2 * fst[2];
+        if (!valid_for(rule, ftype[node])) {
+            wc += w;
+            continue;
+        }
+        T2 v = fres[node];
+        as += w * v.x;
+        ac += w * v.y;
+    }
+    T2 vc = fres[f];
+    T2 out;
+    out.x = as + wc * vc.x;
+    out.y = ac + wc * vc.y;
+    crhs[I] = out;
+}
+
+// (bi/tri)linear interpolation of the coarse error to every fine active node,
+// renormalised over the coarse active nodes (Sec. 3.5.3)
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_prolong(Lists ls, const int8_t* __restrict__ ctype, int cn,
+                                                 const typename V2<T>::t* __restrict__ cx, int fn,
+                                                 typename V2<T>::t* __restrict__ fx) {
+    typedef typename V2<T>::t T2;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi;
+    long long i = list_node(ls, t, kind, gi);
+    int ii[3] = {0, 0, 0};
+    ii[0] = (int)(i % fn);
+    ii[1] = (int)((i / fn) % fn);
+    if (D == 3) ii[2] = (int)(i / ((long long)fn * fn));
+    long long cst[3] = {1, cn, (long long)cn * cn};
+    T ws = 0, as = 0, ac = 0;
+    const int NC = 1 << D;
+#pragma unroll
+    for (int cc = 0; cc < NC; cc++) {
+        long long node = 0;
+        T w = 1;
+        bool dup = false;
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            int pick = (cc >> a) & 1;
+            int lo = ii[a] >> 1, hi = (ii[a] + 1) >> 1;
+            if (lo == hi) {
+                if (pick) dup = true;
+                node += lo * cst[a];
+            } else {
+                w *= (T)0.5;
+                node += (pick ? hi : lo) * cst[a];
+            }
+        }
+        if (dup) continue;
+        int8_t tc = ctype[node];
+        if (tc != T_IN && tc != T_GHOST) continue;
+        T2 v = cx[node];
+        ws += w;
+        as += w * v.x;
+        ac += w * v.y;
+    }
+    if (ws > (T)0) {
+        T2 xf = fx[i];
+        xf.x += as / ws;
+        xf.y += ac / ws;
+        fx[i] = xf;
+    }
+}
+
+// coarse Jacobian coefficients by injection of (s, c); a coarse ghost whose
+// fine twin is inactive takes the mean over the active fine 3^d neighbourhood
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_inject(Lists ls, int cn, const int8_t* __restrict__ ftype, int fn,
+                                                const typename V2<T>::t* __restrict__ fW,
+                                                typename V2<T>::t* __restrict__ cW) {
+    typedef typename V2<T>::t T2;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi;
+    long long I = list_node(ls, t, kind, gi);
+    int ii[3] = {0, 0, 0};
+    ii[0] = (int)(I % cn);
+    ii[1] = (int)((I / cn) % cn);
+    if (D == 3) ii[2] = (int)(I / ((long long)cn * cn));
+    long long fst[3] = {1, fn, (long long)fn * fn};
+    long long f = 0;
+#pragma unroll
+    for (int a = 0; a < D; a++) f += 2LL * ii[a] * fst[a];
+    int8_t tf = ftype[f];
+    if (tf == T_IN || tf == T_GHOST) {
+        cW[I] = fW[f];
+        return;
+    }
+    T ss = 0, sc = 0;
+    int cnt = 0;
+    const int K = D == 2 ? 9 : 27;
+    for (int kk = 0; kk < K; kk++) {
+        int k[3] = {kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1};
+        bool ok = true;
+        long long node = f;
+        for (int a = 0; a < D; a++) {
+            int ia = 2 * ii[a] + k[a];
+            if (ia < 0 || ia > fn - 1) ok = false;
+            node += k[a] * fst[a];
+        }
+        if (!ok) continue;
+        int8_t tn = ftype[node];
+        if (tn != T_IN && tn != T_GHOST) continue;
+        T2 v = fW[node];
+        ss += v.x;
+        sc += v.y;
+        cnt++;
+    }
+    T2 out;
+    out.x = cnt ? ss / (T)cnt : (T)0;
+    out.y = cnt ? sc / (T)cnt : (T)0;
+    cW[I] = out;
+}
+
+// ---------------------------------------------------------------------------
+// coarsest level: assemble the Jacobian, factor it with partial pivoting and
+// form its inverse (one CTA); each cycle then applies the inverse
+
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* __restrict__ act,
+                                                          const int* __restrict__ apos, const int8_t* __restrict__ type,
+                                                          const int* __restrict__ gpos, const int8_t* __restrict__ gm,
+                                                          const T* __restrict__ gw,
+                                                          const typename V2<T>::t* __restrict__ Wc, Offs<D> of,
+                                                          long long st1, long long st2, Coef<T> c, T* A, T* Ainv,
+                                                          int* singular) {
+    typedef typename V2<T>::t T2;
+    extern __shared__ int piv[];
+    __shared__ T red_v[32];
+    __shared__ int red_i[32];
+    const int m = 2 * nact;
+    const long long mm = (long long)m * m;
+    for (long long i = threadIdx.x; i < mm; i += blockDim.x) A[i] = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nact; r += blockDim.x) {
+        long long p = act[r];
+        T2 w = Wc[p];
+        T s = w.x, cp = w.y;
+        T ph = c.alpha * cp + c.beta;
+        T* rs = A + (long long)(2 * r) * m;
+        T* rc = A + (long long)(2 * r + 1) * m;
+        if (type[p] == T_IN) {
+            T ss = ph * c.idt + c.a2mc * ph * cp;
+            T sc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s);
+            for (int q = 0; q < 2 * D; q++) {
+                long long pq = p + of.o[q];
+                T2 wq = Wc[pq];
+                T g = c.kap * ((c.alpha * wq.y + c.beta) + ph);
+                T e = c.kap * c.alpha * (s - wq.x);
+                int qc = apos[pq];
+                rs[2 * qc] += -g;
+                rs[2 * qc + 1] += e;
+                ss += g;
+                sc += e;
+            }
+            rs[2 * r] += ss;
+            rs[2 * r + 1] += sc;
+        } else {
+            int gi = gpos[p];
+            int mv[3] = {1, 1, 1};
+            for (int a = 0; a < D; a++) mv[a] = gm[(long long)gi * D + a];
+            long long st[3] = {1, st1, st2};
+            const int K = D == 2 ? 9 : 27;
+            for (int kk = 0; kk < K; kk++) {
+                int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
+                T wt = 1;
+                long long node = p;
+                for (int a = 0; a < D; a++) {
+                    wt *= gw[(long long)gi * 3 * D + 3 * a + k[a]];
+                    node -= mv[a] * k[a] * st[a];
+                }
+                if (wt == (T)0) continue;
+                rs[2 * apos[node]] += wt;
+            }
+        }
+        rc[2 * r] += c.a2ms * ph * cp;
+        rc[2 * r + 1] += c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
+    }
+    __syncthreads();
+    // LU with partial pivoting (row swaps), multipliers stored below the diagonal
+    for (int k = 0; k < m; k++) {
+        T bv = -1;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+            T v = fabs(A[(long long)i * m + k]);
+            if (v > bv) {
+                bv = v;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            T ov = __shfl_down_sync(0xffffffffu, bv, o);
+            int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            red_v[warp] = bv;
+            red_i[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int nw = (blockDim.x + 31) >> 5;
+            T v0 = red_v[0];
+            int i0 = red_i[0];
+            for (int w = 1; w < nw; w++)
+                if (red_v[w] > v0 || (red_v[w] == v0 && red_i[w] < i0)) {
+                    v0 = red_v[w];
+                    i0 = red_i[w];
+                }
+            piv[k] = i0;
+            if (!(v0 > (T)0)) *singular = 1;
+        }
+        __syncthreads();
+        int pr = piv[k];
+        if (pr != k)
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                T tmp = A[(long long)k * m + j];
+                A[(long long)k * m + j] = A[(long long)pr * m + j];
+                A[(long long)pr * m + j] = tmp;
+            }
+        __syncthreads();
+        T dk = A[(long long)k * m + k];
+        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[(long long)i * m + k] /= dk;
+        __syncthreads();
+        long long rem = (long long)(m - k - 1) * (m - k - 1);
+        for (long long e = threadIdx.x; e < rem; e += blockDim.x) {
+            int i = k + 1 + (int)(e / (m - k - 1));
+            int j = k + 1 + (int)(e % (m - k - 1));
+            A[(long long)i * m + j] -= A[(long long)i * m + k] * A[(long long)k * m + j];
+        }
+        __syncthreads();
+    }
+    // inverse, one column per thread: apply the row swaps to e_j, then solve
+    // L y = P e_j and U x = y; Ainv is stored row-major
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        for (int i = 0; i < m; i++) Ainv[(long long)i * m + j] = (i == j) ? (T)1 : (T)0;
+        for (int k = 0; k < m; k++) {
+            int pr = piv[k];
+            if (pr != k) {
+                T tmp = Ainv[(long long)k * m + j];
+                Ainv[(long long)k * m + j] = Ainv[(long long)pr * m + j];
+                Ainv[(long long)pr * m + j] = tmp;
+            }
+        }
+        for (int i = 1; i < m; i++) {
+            T acc = Ainv[(long long)i * m + j];
+            for (int k = 0; k < i; k++) acc -= A[(long long)i * m + k] * Ainv[(long long)k * m + j];
+            Ainv[(long long)i * m + j] = acc;
+        }
+        for (int i = m - 1; i >= 0; i--) {
+            T acc = Ainv[(long long)i * m + j];
+            for (int k = i + 1; k < m; k++) acc -= A[(long long)i * m + k] * Ainv[(long long)k * m + j];
+            Ainv[(long long)i * m + j] = acc / A[(long long)i * m + i];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarsest_solve(int nact, const int* __restrict__ act, const T* __restrict__ Ainv,
+                                                         const typename V2<T>::t* __restrict__ rhs,
+                                                         typename V2<T>::t* __restrict__ x) {
+    typedef typename V2<T>::t T2;
+    extern __shared__ unsigned char smraw[];
+    T* b = reinterpret_cast<T*>(smraw);
+    const int m = 2 * nact;
+    for (int r = threadIdx.x; r < nact; r += blockDim.x) {
+        T2 v = rhs[act[r]];
+        b[2 * r] = v.x;
+        b[2 * r + 1] = v.y;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nact; r += blockDim.x) {
+        T a0 = 0, a1 = 0;
+        const T* row0 = Ainv + (long long)(2 * r) * m;
+        const T* row1 = row0 + m;
+        for (int j = 0; j < m; j++) {
+            a0 += row0[j] * b[j];
+            a1 += row1[j] * b[j];
+        }
+        T2 out;
+        out.x = a0;
+        out.y = a1;
+        x[act[r]] = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Newton residual (Eqs. FDs, FDc, BCs), FP64
+
+template <int D>
+__device__ __forceinline__ double Ls_h(long long p, const double2* __restrict__ W, const Offs<D>& of,
+                                       const FConst& f, double& ph_out) {
+    double2 w = W[p];
+    double ph = f.alpha * w.y + f.beta;
+    double flux = 0.0;
+#pragma unroll
+    for (int q = 0; q < 2 * D; q++) {
+        double2 wq = W[p + of.o[q]];
+        flux += ((f.alpha * wq.y + f.beta) + ph) * (wq.x - w.x);
+    }
+    ph_out = ph;
+    return -f.amc * ph * w.x * w.y + f.dh2 * flux;
+}
+
+// old-time part G = -M(W^n)/dt - L(W^n)/2 of the CN step (once per step)
+template <int D>
+__global__ void __launch_bounds__(kT) k_old_time(Lists ls, const double2* __restrict__ Wn, double2* __restrict__ G,
+                                                  Offs<D> of, FConst f) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi;
+    long long p = list_node(ls, t, kind, gi);
+    double2 w = Wn[p];
+    double ph = f.alpha * w.y + f.beta;
+    double Lc = -f.ams * ph * w.x * w.y;
+    double2 g;
+    g.y = -w.y * f.idt - 0.5 * Lc;
+    g.x = 0.0;
+    if (kind == 1) {
+        double phd;
+        double Ls = Ls_h<D>(p, Wn, of, f, phd);
+        g.x = -ph * w.x * f.idt - 0.5 * Ls;
+    }
+    G[p] = g;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kT) k_newton_F(Lists ls, const int8_t* __restrict__ gm, const double* __restrict__ gw,
+                                                  const double2* __restrict__ W, const double2* __restrict__ G,
+                                                  double2* __restrict__ F, Offs<D> of, long long st1, long long st2,
+                                                  FConst f, unsigned long long* norm) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long nb = 0;
+    if (t < ls.n0 + ls.n1 + ls.ng) {
+        int kind, gi = 0;
+        long long p = list_node(ls, t, kind, gi);
+        double2 w = W[p];
+        double2 g = G[p];
+        double ph = f.alpha * w.y + f.beta;
+        double Lc = -f.ams * ph * w.x * w.y;
+        double2 out;
+        out.y = w.y * f.idt - 0.5 * Lc + g.y;
+        if (kind == 1) {
+            double phd;
+            double Ls = Ls_h<D>(p, W, of, f, phd);
+            out.x = ph * w.x * f.idt - 0.5 * Ls + g.x;
+        } else {
+            out.x = ghost_dot<D, double>(gi, p, gm, gw, nullptr, W, nullptr, true, st1, st2) - f.sb;
+        }
+        F[p] = out;
+        unsigned long long a0 = abs_bits(out.x), a1 = abs_bits(out.y);
+        nb = a0 > a1 ? a0 : a1;
+    }
+    block_max(nb, norm);
+}
+
+// W -= x on active nodes; norms[0] = |x|_inf, norms[1] = |W_old|_inf
+__global__ void __launch_bounds__(kT) k_newton_update(Lists ls, double2* __restrict__ W, const double2* __restrict__ x,
+                                                      unsigned long long* norms) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long nx = 0, nw = 0;
+    if (t < ls.n0 + ls.n1 + ls.ng) {
+        int kind, gi;
+        long long p = list_node(ls, t, kind, gi);
+        double2 w = W[p], d = x[p];
+        unsigned long long a0 = abs_bits(w.x), a1 = abs_bits(w.y);
+        nw = a0 > a1 ? a0 : a1;
+        a0 = abs_bits(d.x);
+        a1 = abs_bits(d.y);
+        nx = a0 > a1 ? a0 : a1;
+        w.x -= d.x;
+        w.y -= d.y;
+        W[p] = w;
+    }
+    block_max(nx, norms);
+    __syncthreads();
+    block_max(nw, norms + 1);
+}
+
+__global__ void __launch_bounds__(kT) k_norm_active(Lists ls, const double2* __restrict__ v, unsigned long long* norm) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long nb = 0;
+    if (t < ls.n0 + ls.n1 + ls.ng) {
+        int kind, gi;
+        long long p = list_node(ls, t, kind, gi);
+        double2 w = v[p];
+        unsigned long long a0 = abs_bits(w.x), a1 = abs_bits(w.y);
+        nb = a0 > a1 ? a0 : a1;
+    }
+    block_max(nb, norm);
+}
+
+// mixed precision: FP64 values to FP32 on active nodes
+__global__ void k_to_float2(Lists ls, const double2* __restrict__ a, float2* __restrict__ b) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi;
+    long long p = list_node(ls, t, kind, gi);
+    double2 v = a[p];
+    b[p] = make_float2((float)v.x, (float)v.y);
+}
+
+// x64 += e32 on active nodes
+__global__ void k_accumulate(Lists ls, double2* __restrict__ x, const float2* __restrict__ e) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi;
+    long long p = list_node(ls, t, kind, gi);
+    double2 v = x[p];
+    float2 d = e[p];
+    v.x += (double)d.x;
+    v.y += (double)d.y;
+    x[p] = v;
+}
+
+// state import / export over the box
+__global__ void k_reset_state(const int8_t* __restrict__ type, long long nn, double2* W, double s0, double c0) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    int8_t t = type[i];
+    bool a = t == T_IN || t == T_GHOST;
+    W[i] = make_double2(a ? s0 : 0.0, a ? c0 : 0.0);
+}
+
+__global__ void k_import_state(const int8_t* __restrict__ type, long long nn, double2* W, const double* __restrict__ sv,
+                               const double* __restrict__ cv) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    int8_t t = type[i];
+    bool a = t == T_IN || t == T_GHOST;
+    W[i] = make_double2(a ? sv[i] : 0.0, a ? cv[i] : 0.0);
+}
+
+__global__ void k_export_state(const int8_t* __restrict__ type, long long nn, const double2* __restrict__ W,
+                               double* sv, double* cv, int8_t* tv) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    int8_t t = type[i];
+    bool a = t == T_IN || t == T_GHOST;
+    double2 w = W[i];
+    if (sv) sv[i] = a ? w.x : 0.0;
+    if (cv) cv[i] = a ? w.y : 0.0;
+    if (tv) tv[i] = a ? t : (int8_t)0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+
+template <int D, typename T>
+int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int colour, bool pointwise,
+                        cudaStream_t s) {
+    int cnt = L.nin[colour];
+    if (cnt == 0) return 0;
+    Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
+    if (pointwise)
+        k_relax_inside<D, T, true><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, V.Wc, V.rhs, V.x, of, c);
+    else
+        k_relax_inside<D, T, false><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, V.Wc, V.rhs, V.x, of, c);
+    return 1;
+}
+
+template <int D, typename T>
+int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, cudaStream_t s) {
+    if (L.ng == 0 || passes < 1) return 0;
+    const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
+    int n = 0;
+    for (int p = 0; p < passes; p++) {
+        bool first = p == 0, last = p == passes - 1 && passes > 1;
+        const T* sin = first ? nullptr : V.gbuf[(p - 1) & 1];
+        T* sout = V.gbuf[p & 1];
+        k_ghost_pass<D, T><<<nblk(L.ng), kT, 0, s>>>(L.ng, L.gidx, L.gpos, L.gm, gw, V.Wc, V.rhs, V.x, sin, sout,
+                                                      L.st[1], L.st[2], c, first, last);
+        n++;
+    }
+    if (passes == 1) {
+        k_ghost_scatter<T><<<nblk(L.ng), kT, 0, s>>>(L.ng, L.gidx, V.gbuf[0], V.x);
+        n++;
+    }
+    return n;
+}
+
+template <int D, typename T>
+int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, unsigned long long* norm,
+                    cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    if (tot == 0) return 0;
+    const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
+    Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
+    k_residual<D, T><<<nblk(tot), kT, 0, s>>>(ls, L.gm, gw, V.Wc, V.rhs, V.x, V.res, of, L.st[1], L.st[2], c, norm);
+    return 1;
+}
+
+template <int D, typename T>
+int launch_extend(const LevelGeo& L, const LevelVec<T>& V, int steps, cudaStream_t s) {
+    if (L.nb == 0 || steps < 1) return 0;
+    const T* an = std::is_same<T, float>::value ? (const T*)L.ban32 : (const T*)L.ban;
+    T cfl = D == 2 ? (T)0.5 : (T)(1.0 / 3.0);
+    for (int k = 0; k < steps; k++) {
+        bool first = k == 0, last = k == steps - 1;
+        k_extend_step<D, T><<<nblk(L.nb), kT, 0, s>>>(L.nb, L.bidx, L.bref, an, V.res, V.bbuf[(k + 1) & 1],
+                                                       V.bbuf[k & 1], cfl, first, last);
+    }
+    return steps;
+}
+
+template <int D, typename T>
+int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
+                    cudaStream_t s) {
+    Lists ls = make_lists(C);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_restrict<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs);
+    return 1;
+}
+
+template <int D, typename T>
+int launch_prolong(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
+                   cudaStream_t s) {
+    Lists ls = make_lists(F);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_prolong<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.type, C.n, CV.x, F.n, FV.x);
+    return 1;
+}
+
+template <int D, typename T>
+int launch_inject(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
+                  cudaStream_t s) {
+    Lists ls = make_lists(C);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_inject<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.n, F.type, F.n, FV.Wc, CV.Wc);
+    return 1;
+}
+
+template <int D, typename T>
+int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int* singular,
+                           cudaStream_t s) {
+    const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
+    Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
+    size_t shm = sizeof(int) * (2 * L.nact + 1);
+    k_coarsest_factor<D, T><<<1, 1024, shm, s>>>(L.nact, L.act, L.apos, L.type, L.gpos,
+                                                 L.gm, gw, V.Wc, of, L.st[1], L.st[2], c, V.A, V.Ainv, singular);
+    return 1;
+}
+
+template <int D, typename T>
+int launch_coarsest_solve(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s) {
+    size_t shm = sizeof(T) * (2 * L.nact + 1);
+    k_coarsest_solve<T><<<1, 1024, shm, s>>>(L.nact, L.act, V.Ainv, V.rhs, V.x);
+    return 1;
+}
+
+template <int D>
+int launch_old_time(const LevelGeo& L, const double2* Wn, double2* G, const FConst& fc, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_old_time<D><<<nblk(tot), kT, 0, s>>>(ls, Wn, G, make_offs<D>(L.st[1], L.st[2]), fc);
+    return 1;
+}
+
+template <int D>
+int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, double2* F, const FConst& fc,
+                    unsigned long long* norm, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_newton_F<D><<<nblk(tot), kT, 0, s>>>(ls, L.gm, L.gw, W, G, F, make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2],
+                                            fc, norm);
+    return 1;
+}
+
+int launch_newton_update(const LevelGeo& L, double2* W, const double2* x, unsigned long long* norms, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_newton_update<<<nblk(tot), kT, 0, s>>>(ls, W, x, norms);
+    return 1;
+}
+
+int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* norm, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_norm_active<<<nblk(tot), kT, 0, s>>>(ls, v, norm);
+    return 1;
+}
+
+int launch_to_float(const LevelGeo& L, const double2* src, float2* dst, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_to_float2<<<nblk(tot), kT, 0, s>>>(ls, src, dst);
+    return 1;
+}
+
+int launch_accumulate(const LevelGeo& L, double2* x, const float2* e, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    k_accumulate<<<nblk(tot), kT, 0, s>>>(ls, x, e);
+    return 1;
+}
+
+int launch_reset_state(const LevelGeo& L, double2* W, double s0, double c0, cudaStream_t s) {
+    k_reset_state<<<nblk(L.nn), kT, 0, s>>>(L.type, L.nn, W, s0, c0);
+    return 1;
+}
+
+int launch_import_state(const LevelGeo& L, double2* W, const double* sv, const double* cv, cudaStream_t s) {
+    k_import_state<<<nblk(L.nn), kT, 0, s>>>(L.type, L.nn, W, sv, cv);
+    return 1;
+}
+
+int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double* cv, int8_t* tv, cudaStream_t s) {
+    k_export_state<<<nblk(L.nn), kT, 0, s>>>(L.type, L.nn, W, sv, cv, tv);
+    return 1;
+}
+
+#define SULF_INST(D, T)                                                                                          \
+    template int launch_relax_inside<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, bool,       \
+                                           cudaStream_t);                                                        \
+    template int launch_relax_ghosts<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, cudaStream_t); \
+    template int launch_residual<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, unsigned long long*,  \
+                                       cudaStream_t);                                                            \
+    template int launch_extend<D, T>(const LevelGeo&, const LevelVec<T>&, int, cudaStream_t);                    \
+    template int launch_restrict<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&, \
+                                       cudaStream_t);                                                            \
+    template int launch_prolong<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&,  \
+                                      cudaStream_t);                                                             \
+    template int launch_inject<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&,   \
+                                     cudaStream_t);                                                              \
+    template int launch_coarsest_factor<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int*,         \
+                                              cudaStream_t);                                                     \
+    template int launch_coarsest_solve<D, T>(const LevelGeo&, const LevelVec<T>&, cudaStream_t);
+
+SULF_INST(2, double)
+SULF_INST(2, float)
+SULF_INST(3, double)
+SULF_INST(3, float)
+
+template int launch_old_time<2>(const LevelGeo&, const double2*, double2*, const FConst&, cudaStream_t);
+template int launch_old_time<3>(const LevelGeo&, const double2*, double2*, const FConst&, cudaStream_t);
+template int launch_newton_F<2>(const LevelGeo&, const double2*, const double2*, double2*, const FConst&,
+                                unsigned long long*, cudaStream_t);
+template int launch_newton_F<3>(const LevelGeo&, const double2*, const double2*, double2*, const FConst&,
+                                unsigned long long*, cudaStream_t);
+
+}  // namespace sulf

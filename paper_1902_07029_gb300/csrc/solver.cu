@@ -1,0 +1,795 @@
+// Host orchestration and C ABI of the sulfmg library: one handle per domain,
+// the multigrid hierarchy resident on the device, Crank-Nicolson steps solved
+// by Newton-Raphson (arXiv:1902.07029, Sec. 3.1 and 3.4) with level-set
+// multigrid cycles (Sec. 3.5) issued as kernels on the handle's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sulfmg_debug.h"
+#include "sulf_internal.cuh"
+
+using namespace sulf;
+
+static thread_local std::string g_err;
+
+int sulf_fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int sulf_fail_cuda(cudaError_t e, const char* what) {
+    g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SULF_ENOMEM : SULF_EDEVICE;
+}
+
+namespace sulf {
+
+void* DevMem::get(size_t n) {
+    void* p = nullptr;
+    size_t sz = (n + 255) & ~size_t(255);
+    if (sz == 0) sz = 256;
+    if (cudaMalloc(&p, sz) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    bytes += sz;
+    return p;
+}
+
+void DevMem::release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+}
+
+}  // namespace sulf
+
+struct sulf_domain {
+    int dim = 2, N = 0, L = 0;
+    double lo = 0, hi = 0;
+    LevelGeo geo[SULF_MAXLEV];
+    LevelVec<double> v64[SULF_MAXLEV];
+    LevelVec<float> v32[SULF_MAXLEV];
+    bool have32 = false;
+    double2* W = nullptr;   // state, = v64[0].Wc
+    double2* Wn = nullptr;  // state at t_n
+    double2* G = nullptr;   // old-time part of the CN step
+    unsigned long long* dnorm = nullptr;
+    unsigned long long* hnorm = nullptr;  // pinned
+    int* dsing = nullptr;
+    double* stage = nullptr;  // 2*nn doubles + nn bytes, device staging for state I/O
+    sulf_model model{};
+    sulf_solver solver{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    DevMem mem;
+    double t = 0, dt = 0;
+    // statistics
+    int newton_last = 0, cycles_last = 0;
+    long long newton_total = 0, cycles_total = 0, steps_total = 0, launches = 0;
+    double last_rho = 0, last_fnorm = 0;
+    // profiling of the finest-level inside relaxation
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+};
+
+namespace {
+
+sulf_solver default_solver() {
+    sulf_solver s;
+    s.nu1 = 2;
+    s.nu2 = 2;
+    s.cycle = 1;
+    s.max_newton = 20;
+    s.max_cycles = 30;
+    s.ghost_sweeps = 4;
+    s.newton_tol = 1e-10;
+    s.lin_rtol = 1e-10;
+    s.tau_s = 0.9;
+    s.precision = 0;
+    s.smoother = 0;
+    return s;
+}
+
+sulf_model default_model() {
+    sulf_model m;
+    m.a = 1e4;
+    m.d = 0.1;
+    m.m_s = 64.06;
+    m.m_c = 100.09;
+    m.alpha = 0.01;
+    m.beta = 0.1;
+    m.s_ext = 1.0;
+    m.s0 = 0.0;
+    m.c0 = 10.0;
+    return m;
+}
+
+double bits_to_double(unsigned long long b) {
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+template <typename T>
+Coef<T> make_coef(const sulf_domain* d, int l) {
+    Coef<T> c;
+    const sulf_model& m = d->model;
+    double h = d->geo[l].h;
+    c.alpha = (T)m.alpha;
+    c.beta = (T)m.beta;
+    c.a2mc = (T)(m.a / (2.0 * m.m_c));
+    c.a2ms = (T)(m.a / (2.0 * m.m_s));
+    c.idt = (T)(1.0 / d->dt);
+    c.kap = (T)(m.d / (4.0 * h * h));
+    c.tau = (T)d->solver.tau_s;
+    return c;
+}
+
+FConst make_fconst(const sulf_domain* d) {
+    FConst f;
+    const sulf_model& m = d->model;
+    double h = d->geo[0].h;
+    f.alpha = m.alpha;
+    f.beta = m.beta;
+    f.amc = m.a / m.m_c;
+    f.ams = m.a / m.m_s;
+    f.idt = 1.0 / d->dt;
+    f.dh2 = m.d / (2.0 * h * h);
+    f.sb = m.s_ext;
+    return f;
+}
+
+template <typename T>
+int alloc_vectors(sulf_domain* d, LevelVec<T>* V, bool share_state) {
+    typedef typename V2<T>::t T2;
+    for (int l = 0; l < d->L; l++) {
+        const LevelGeo& G = d->geo[l];
+        LevelVec<T>& v = V[l];
+        size_t nb2 = sizeof(T2) * G.nn;
+        if (!(share_state && l == 0)) v.Wc = (T2*)d->mem.get(nb2);
+        v.rhs = (T2*)d->mem.get(nb2);
+        v.x = (T2*)d->mem.get(nb2);
+        v.res = (T2*)d->mem.get(nb2);
+        for (int k = 0; k < 2; k++) {
+            v.gbuf[k] = (T*)d->mem.get(sizeof(T) * (G.ng + 1));
+            v.bbuf[k] = (T2*)d->mem.get(sizeof(T2) * (G.nb + 1));
+        }
+        if ((!share_state || l > 0) && !v.Wc) return sulf_fail(SULF_ENOMEM, "out of device memory");
+        if (!v.rhs || !v.x || !v.res || !v.gbuf[0] || !v.gbuf[1] || !v.bbuf[0] || !v.bbuf[1])
+            return sulf_fail(SULF_ENOMEM, "out of device memory");
+        if (v.Wc) SULF_CUDA_TRY(cudaMemsetAsync(v.Wc, 0, nb2, d->stream));
+        SULF_CUDA_TRY(cudaMemsetAsync(v.rhs, 0, nb2, d->stream));
+        SULF_CUDA_TRY(cudaMemsetAsync(v.x, 0, nb2, d->stream));
+        SULF_CUDA_TRY(cudaMemsetAsync(v.res, 0, nb2, d->stream));
+        if (l == d->L - 1) {
+            size_t m = 2 * (size_t)G.nact;
+            v.A = (T*)d->mem.get(sizeof(T) * (m * m + 1));
+            v.Ainv = (T*)d->mem.get(sizeof(T) * (m * m + 1));
+            if (!v.A || !v.Ainv) return sulf_fail(SULF_ENOMEM, "out of device memory");
+        }
+    }
+    return SULF_OK;
+}
+
+int ensure32(sulf_domain* d) {
+    if (d->have32) return SULF_OK;
+    int rc = alloc_vectors<float>(d, d->v32, false);
+    if (rc) return rc;
+    d->have32 = true;
+    return SULF_OK;
+}
+
+// ---- profiling events around the finest-level inside relaxation ----
+cudaEvent_t next_event(sulf_domain* d) {
+    if (d->evused == d->evpool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        d->evpool.push_back(e);
+    }
+    return d->evpool[d->evused++];
+}
+
+int read_norms(sulf_domain* d, int n) {
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
+                                  d->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+    return SULF_OK;
+}
+
+// ---- multigrid on precision T ----
+template <int D, typename T>
+struct MG {
+    sulf_domain* d;
+    LevelVec<T>* V;
+
+    int relax(int l) {
+        const LevelGeo& G = d->geo[l];
+        Coef<T> c = make_coef<T>(d, l);
+        bool pw = d->solver.smoother == 1;
+        for (int colour = 0; colour < 2; colour++) {
+            bool timed = d->prof && l == 0;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (timed) {
+                e0 = next_event(d);
+                cudaEventRecord(e0, d->stream);
+            }
+            d->launches += launch_relax_inside<D, T>(G, V[l], c, colour, pw, d->stream);
+            if (timed) {
+                e1 = next_event(d);
+                cudaEventRecord(e1, d->stream);
+            }
+        }
+        d->launches += launch_relax_ghosts<D, T>(G, V[l], c, d->solver.ghost_sweeps, d->stream);
+        return SULF_OK;
+    }
+
+    void cycle(int l) {
+        if (l == d->L - 1) {
+            d->launches += launch_coarsest_solve<D, T>(d->geo[l], V[l], d->stream);
+            return;
+        }
+        for (int k = 0; k < d->solver.nu1; k++) relax(l);
+        d->launches += launch_residual<D, T>(d->geo[l], V[l], make_coef<T>(d, l), nullptr, d->stream);
+        d->launches += launch_extend<D, T>(d->geo[l], V[l], 4, d->stream);
+        d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
+        cudaMemsetAsync(V[l + 1].x, 0, sizeof(typename V2<T>::t) * d->geo[l + 1].nn, d->stream);
+        int gam = d->solver.cycle == 2 ? 2 : 1;
+        for (int g = 0; g < gam; g++) cycle(l + 1);
+        d->launches += launch_prolong<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
+        for (int k = 0; k < d->solver.nu2; k++) relax(l);
+    }
+
+    // coarse coefficients from V[0].Wc and the coarsest factorisation
+    int prepare() {
+        for (int l = 1; l < d->L; l++)
+            d->launches += launch_inject<D, T>(d->geo[l - 1], V[l - 1], d->geo[l], V[l], d->stream);
+        SULF_CUDA_TRY(cudaMemsetAsync(d->dsing, 0, sizeof(int), d->stream));
+        int lc = d->L - 1;
+        d->launches += launch_coarsest_factor<D, T>(d->geo[lc], V[lc], make_coef<T>(d, lc), d->dsing, d->stream);
+        return SULF_OK;
+    }
+};
+
+// Solve J(W) dW = F on the finest level: FP64 cycles, or FP32 cycles on the
+// FP64 defect (defect correction).  v64[0].rhs holds F, the result is left in
+// v64[0].x.  Returns the number of cycles, or a negative error.
+template <int D>
+int linear_solve(sulf_domain* d, double fnorm, int max_cycles, double rtol, double* rnorms) {
+    const LevelGeo& G0 = d->geo[0];
+    SULF_CUDA_TRY(cudaMemsetAsync(d->v64[0].x, 0, sizeof(double2) * G0.nn, d->stream));
+    if (d->solver.precision == 0) {
+        MG<D, double> mg{d, d->v64};
+        int rc = mg.prepare();
+        if (rc) return rc;
+        if (d->L == 1) {
+            d->launches += launch_coarsest_solve<D, double>(G0, d->v64[0], d->stream);
+            return 1;
+        }
+        double rprev = fnorm;
+        int cyc;
+        for (cyc = 1; cyc <= max_cycles; cyc++) {
+            mg.cycle(0);
+            SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
+            d->launches += launch_residual<D, double>(G0, d->v64[0], make_coef<double>(d, 0), d->dnorm, d->stream);
+            SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+            rc = read_norms(d, 1);
+            if (rc) return rc;
+            if (*(int*)(d->hnorm + 6)) return sulf_fail(SULF_ENOTCONV, "singular coarsest-level Jacobian");
+            double rn = bits_to_double(d->hnorm[0]);
+            if (rnorms) rnorms[cyc - 1] = rn;
+            d->last_rho = rprev > 0 ? rn / rprev : 0.0;
+            rprev = rn;
+            if (rn <= rtol * fnorm || rn != rn) break;
+        }
+        return cyc > max_cycles ? max_cycles : cyc;
+    }
+    // mixed precision: FP32 cycles on the FP64 defect
+    int rc = ensure32(d);
+    if (rc) return rc;
+    LevelVec<double>& V0 = d->v64[0];
+    LevelVec<float>& U0 = d->v32[0];
+    d->launches += launch_to_float(G0, d->W, U0.Wc, d->stream);
+    MG<D, float> mg{d, d->v32};
+    rc = mg.prepare();
+    if (rc) return rc;
+    d->launches += launch_to_float(G0, V0.rhs, U0.rhs, d->stream);
+    double rprev = fnorm;
+    int cyc;
+    for (cyc = 1; cyc <= max_cycles; cyc++) {
+        SULF_CUDA_TRY(cudaMemsetAsync(U0.x, 0, sizeof(float2) * G0.nn, d->stream));
+        if (d->L == 1)
+            d->launches += launch_coarsest_solve<D, float>(G0, U0, d->stream);
+        else
+            mg.cycle(0);
+        d->launches += launch_accumulate(G0, V0.x, U0.x, d->stream);
+        SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
+        d->launches += launch_residual<D, double>(G0, V0, make_coef<double>(d, 0), d->dnorm, d->stream);
+        SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+        rc = read_norms(d, 1);
+        if (rc) return rc;
+        if (*(int*)(d->hnorm + 6)) return sulf_fail(SULF_ENOTCONV, "singular coarsest-level Jacobian");
+        double rn = bits_to_double(d->hnorm[0]);
+        if (rnorms) rnorms[cyc - 1] = rn;
+        d->last_rho = rprev > 0 ? rn / rprev : 0.0;
+        rprev = rn;
+        if (rn <= rtol * fnorm || rn != rn) break;
+        d->launches += launch_to_float(G0, V0.res, U0.rhs, d->stream);
+    }
+    return cyc > max_cycles ? max_cycles : cyc;
+}
+
+// one Crank-Nicolson step by Newton-Raphson (Sec. 3.4)
+template <int D>
+int cn_step(sulf_domain* d) {
+    const LevelGeo& G0 = d->geo[0];
+    LevelVec<double>& V0 = d->v64[0];
+    FConst fc = make_fconst(d);
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, d->stream));
+    d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, d->stream);
+    SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, d->stream));
+    d->launches += launch_newton_F<D>(G0, d->W, d->G, V0.rhs, fc, d->dnorm, d->stream);
+    int rc = read_norms(d, 1);
+    if (rc) return rc;
+    double fn = bits_to_double(d->hnorm[0]);
+    d->newton_last = 0;
+    d->cycles_last = 0;
+    if (fn < d->solver.newton_tol) {
+        d->t += d->dt;
+        d->steps_total++;
+        d->last_fnorm = fn;
+        return SULF_OK;
+    }
+    for (int k = 1; k <= d->solver.max_newton; k++) {
+        int nc = linear_solve<D>(d, fn, d->solver.max_cycles, d->solver.lin_rtol, nullptr);
+        if (nc < 0) return nc;
+        d->cycles_last += nc;
+        d->cycles_total += nc;
+        SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, d->stream));
+        d->launches += launch_newton_update(G0, d->W, V0.x, d->dnorm, d->stream);
+        d->launches += launch_newton_F<D>(G0, d->W, d->G, V0.rhs, fc, d->dnorm + 2, d->stream);
+        rc = read_norms(d, 3);
+        if (rc) return rc;
+        double dn = bits_to_double(d->hnorm[0]), wn = bits_to_double(d->hnorm[1]);
+        fn = bits_to_double(d->hnorm[2]);
+        d->newton_last = k;
+        d->newton_total++;
+        d->last_fnorm = fn;
+        if (fn != fn || dn != dn) break;
+        double rel = wn > 0 ? dn / wn : dn;
+        if ((fn < rel ? fn : rel) < d->solver.newton_tol) {
+            d->t += d->dt;
+            d->steps_total++;
+            return SULF_OK;
+        }
+    }
+    char buf[128];
+    snprintf(buf, sizeof buf, "Newton did not converge (|F|_inf = %g)", fn);
+    return sulf_fail(SULF_ENOTCONV, buf);
+}
+
+bool valid(sulf_handle h) { return h != nullptr; }
+
+int copy_in(sulf_domain* d, void* dst, const void* src, size_t n) {
+    SULF_CUDA_TRY(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, d->stream));
+    return SULF_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+const char* sulf_last_error(void) { return g_err.c_str(); }
+
+void sulf_destroy(sulf_handle h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    h->mem.release();
+    if (h->hnorm) cudaFreeHost(h->hnorm);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+int sulf_create_domain(const double* levelset, int dim, const double* box, int N, int coarsest_N, sulf_handle* out) {
+    if (!out) return sulf_fail(SULF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!levelset || !box || (dim != 2 && dim != 3) || N < 2 || coarsest_N < 2 || !(box[1] > box[0]))
+        return sulf_fail(SULF_EINVAL, "invalid arguments");
+    int nl = 1, Nl = N;
+    while (Nl > coarsest_N && Nl % 2 == 0) {
+        Nl /= 2;
+        nl++;
+    }
+    if (Nl != coarsest_N || nl > SULF_MAXLEV) return sulf_fail(SULF_EINVAL, "N must be coarsest_N times a power of two");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return sulf_fail(SULF_EDEVICE, "no CUDA device");
+    sulf_domain* d = new sulf_domain();
+    d->dim = dim;
+    d->N = N;
+    d->L = nl;
+    d->lo = box[0];
+    d->hi = box[1];
+    d->model = default_model();
+    d->solver = default_solver();
+    d->dt = 1.0;
+    if (cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete d;
+        return sulf_fail(SULF_EDEVICE, "cannot create a CUDA stream");
+    }
+    d->stream = d->own_stream;
+    std::string err;
+    int rc = SULF_OK;
+    for (int l = 0; l < nl && rc == SULF_OK; l++) {
+        LevelGeo& G = d->geo[l];
+        G.dim = dim;
+        G.N = N >> l;
+        G.n = G.N + 1;
+        G.nn = 1;
+        for (int a = 0; a < dim; a++) G.nn *= G.n;
+        G.st[0] = 1;
+        G.st[1] = G.n;
+        G.st[2] = dim == 3 ? (long long)G.n * G.n : 0;
+        G.lo = box[0];
+        G.h = (box[1] - box[0]) / G.N;
+        if (l == 0) {
+            G.phi = (double*)d->mem.get(sizeof(double) * G.nn);
+            if (!G.phi) {
+                rc = sulf_fail(SULF_ENOMEM, "out of device memory");
+                break;
+            }
+            if (cudaMemcpyAsync(G.phi, levelset, sizeof(double) * G.nn, cudaMemcpyHostToDevice, d->stream) !=
+                cudaSuccess) {
+                rc = sulf_fail(SULF_EDEVICE, "level-set upload failed");
+                break;
+            }
+        }
+        rc = build_level_geometry(G, l ? &d->geo[l - 1] : nullptr, l == 0, l == nl - 1, d->mem, d->stream, err,
+                                  d->launches);
+        if (rc) sulf_fail(rc, err);
+    }
+    if (rc == SULF_OK) rc = alloc_vectors<double>(d, d->v64, false);
+    if (rc == SULF_OK) {
+        long long nn = d->geo[0].nn;
+        d->W = d->v64[0].Wc;
+        d->Wn = (double2*)d->mem.get(sizeof(double2) * nn);
+        d->G = (double2*)d->mem.get(sizeof(double2) * nn);
+        d->dnorm = (unsigned long long*)d->mem.get(sizeof(unsigned long long) * 8);
+        d->dsing = (int*)d->mem.get(sizeof(int) * 2);
+        d->stage = (double*)d->mem.get(sizeof(double) * 2 * nn + nn + 16);
+        if (!d->Wn || !d->G || !d->dnorm || !d->dsing || !d->stage)
+            rc = sulf_fail(SULF_ENOMEM, "out of device memory");
+        else if (cudaMallocHost(&d->hnorm, sizeof(unsigned long long) * 8) != cudaSuccess)
+            rc = sulf_fail(SULF_ENOMEM, "out of pinned host memory");
+        else {
+            cudaMemsetAsync(d->Wn, 0, sizeof(double2) * nn, d->stream);
+            cudaMemsetAsync(d->G, 0, sizeof(double2) * nn, d->stream);
+            d->launches += launch_reset_state(d->geo[0], d->W, d->model.s0, d->model.c0, d->stream);
+            if (cudaStreamSynchronize(d->stream) != cudaSuccess) rc = sulf_fail(SULF_EDEVICE, "initialisation failed");
+        }
+    }
+    if (rc != SULF_OK) {
+        std::string keep = g_err;
+        sulf_destroy(d);
+        g_err = keep;
+        return rc;
+    }
+    *out = d;
+    return SULF_OK;
+}
+
+int sulf_set_model(sulf_handle h, const sulf_model* m) {
+    if (!valid(h) || !m) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    if (!(m->d >= 0) || !(m->m_s > 0) || !(m->m_c > 0)) return sulf_fail(SULF_EINVAL, "invalid model parameters");
+    h->model = *m;
+    h->t = 0;
+    h->launches += launch_reset_state(h->geo[0], h->W, m->s0, m->c0, h->stream);
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SULF_OK;
+}
+
+int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    sulf_solver v = s ? *s : default_solver();
+    if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || (v.cycle != 1 && v.cycle != 2) || v.max_newton < 1 ||
+        v.max_cycles < 1 || v.ghost_sweeps < 1 || !(v.tau_s > 0 && v.tau_s < 1) || !(v.newton_tol > 0) ||
+        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1))
+        return sulf_fail(SULF_EINVAL, "solver controls out of range");
+    h->solver = v;
+    if (v.precision == 1) return ensure32(h);
+    return SULF_OK;
+}
+
+int sulf_set_stream(sulf_handle h, void* stream) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return SULF_OK;
+}
+
+int sulf_step(sulf_handle h, double dt, int nsteps) {
+    if (!valid(h) || !(dt > 0) || nsteps < 0) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    h->dt = dt;
+    for (int k = 0; k < nsteps; k++) {
+        int rc = h->dim == 2 ? cn_step<2>(h) : cn_step<3>(h);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sulf_fail_cuda(e, "kernel launch");
+    return SULF_OK;
+}
+
+int sulf_get_state_device(sulf_handle h, double* s_dev, double* c_dev) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    h->launches += launch_export_state(h->geo[0], h->W, s_dev, c_dev, nullptr, h->stream);
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SULF_OK;
+}
+
+int sulf_get_state(sulf_handle h, double* s, double* c, int8_t* type) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    long long nn = h->geo[0].nn;
+    double* ds = h->stage;
+    double* dc = h->stage + nn;
+    int8_t* dt = (int8_t*)(h->stage + 2 * nn);
+    h->launches += launch_export_state(h->geo[0], h->W, ds, dc, dt, h->stream);
+    if (s) SULF_CUDA_TRY(cudaMemcpyAsync(s, ds, sizeof(double) * nn, cudaMemcpyDeviceToHost, h->stream));
+    if (c) SULF_CUDA_TRY(cudaMemcpyAsync(c, dc, sizeof(double) * nn, cudaMemcpyDeviceToHost, h->stream));
+    if (type) SULF_CUDA_TRY(cudaMemcpyAsync(type, dt, nn, cudaMemcpyDeviceToHost, h->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SULF_OK;
+}
+
+int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_dev, double t) {
+    if (!valid(h) || !s_dev || !c_dev) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    h->launches += launch_import_state(h->geo[0], h->W, s_dev, c_dev, h->stream);
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->t = t;
+    return SULF_OK;
+}
+
+int sulf_set_state(sulf_handle h, const double* s, const double* c, double t) {
+    if (!valid(h) || !s || !c) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    long long nn = h->geo[0].nn;
+    SULF_CUDA_TRY(cudaMemcpyAsync(h->stage, s, sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
+    SULF_CUDA_TRY(cudaMemcpyAsync(h->stage + nn, c, sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
+    return sulf_set_state_device(h, h->stage, h->stage + nn, t);
+}
+
+int sulf_get_stats(sulf_handle h, sulf_stats* o) {
+    if (!valid(h) || !o) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    o->t = h->t;
+    o->newton_last = h->newton_last;
+    o->cycles_last = h->cycles_last;
+    o->newton_total = h->newton_total;
+    o->cycles_total = h->cycles_total;
+    o->steps_total = h->steps_total;
+    o->last_rho = h->last_rho;
+    o->last_fnorm = h->last_fnorm;
+    o->kernel_launches = h->launches;
+    o->levels = h->L;
+    o->n_inside = h->geo[0].nin[0] + (long long)h->geo[0].nin[1];
+    o->n_ghost = h->geo[0].ng;
+    for (int k = 0; k < 3; k++) o->ghost_rows[k] = h->geo[0].kinds[k];
+    return SULF_OK;
+}
+
+int sulf_set_profiling(sulf_handle h, int on) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->prof = on != 0;
+    h->evused = 0;
+    return SULF_OK;
+}
+
+int sulf_kernel_time(sulf_handle h, double* ms, long long* launches) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double tot = 0;
+    for (size_t k = 0; k + 1 < h->evused; k += 2) {
+        float e = 0;
+        SULF_CUDA_TRY(cudaEventElapsedTime(&e, h->evpool[k], h->evpool[k + 1]));
+        tot += e;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = (long long)(h->evused / 2);
+    h->evused = 0;
+    return SULF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stage-level entry points (sulfmg_debug.h)
+
+static int dbg_level_ok(sulf_handle h, int l) { return valid(h) && l >= 0 && l < h->L; }
+
+int sulf_dbg_level_info(sulf_handle h, int l, int64_t* info) {
+    if (!dbg_level_ok(h, l) || !info) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G = h->geo[l];
+    info[0] = G.N;
+    info[1] = G.n;
+    info[2] = G.ng;
+    info[3] = G.nb;
+    info[4] = l == h->L - 1 ? G.nact : 0;
+    info[5] = G.nin[0] + (int64_t)G.nin[1];
+    for (int k = 0; k < 3; k++) info[6 + k] = G.kinds[k];
+    return SULF_OK;
+}
+
+int sulf_dbg_level_type(sulf_handle h, int l, int8_t* type) {
+    if (!dbg_level_ok(h, l) || !type) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    SULF_CUDA_TRY(cudaMemcpyAsync(type, h->geo[l].type, h->geo[l].nn, cudaMemcpyDeviceToHost, h->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SULF_OK;
+}
+
+int sulf_dbg_level_ghosts(sulf_handle h, int l, int64_t* idx, int8_t* kind, int8_t* m, double* w, double* B) {
+    if (!dbg_level_ok(h, l)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G = h->geo[l];
+    int D = G.dim;
+    std::vector<int> tmp(G.ng + 1);
+    SULF_CUDA_TRY(cudaMemcpyAsync(tmp.data(), G.gidx, sizeof(int) * G.ng, cudaMemcpyDeviceToHost, h->stream));
+    if (kind) SULF_CUDA_TRY(cudaMemcpyAsync(kind, G.gkind, G.ng, cudaMemcpyDeviceToHost, h->stream));
+    if (m) SULF_CUDA_TRY(cudaMemcpyAsync(m, G.gm, (size_t)G.ng * D, cudaMemcpyDeviceToHost, h->stream));
+    if (w) SULF_CUDA_TRY(cudaMemcpyAsync(w, G.gw, sizeof(double) * G.ng * D * 3, cudaMemcpyDeviceToHost, h->stream));
+    if (B) SULF_CUDA_TRY(cudaMemcpyAsync(B, G.gB, sizeof(double) * G.ng * D, cudaMemcpyDeviceToHost, h->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (idx)
+        for (int k = 0; k < G.ng; k++) idx[k] = tmp[k];
+    return SULF_OK;
+}
+
+// copy a level vector to the host, zero outside the nodes whose type is in mask
+static int dbg_copy_out(sulf_handle h, int l, const double2* src, double* dst, bool with_band) {
+    const LevelGeo& G = h->geo[l];
+    std::vector<int8_t> ty(G.nn);
+    SULF_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double2) * G.nn, cudaMemcpyDeviceToHost, h->stream));
+    SULF_CUDA_TRY(cudaMemcpyAsync(ty.data(), G.type, G.nn, cudaMemcpyDeviceToHost, h->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (long long i = 0; i < G.nn; i++) {
+        bool keep = ty[i] == T_IN || ty[i] == T_GHOST || (with_band && ty[i] == T_BAND);
+        if (!keep) dst[2 * i] = dst[2 * i + 1] = 0.0;
+    }
+    return SULF_OK;
+}
+
+int sulf_dbg_eval_F(sulf_handle h, double dt, const double* W, const double* Wn, double* F) {
+    if (!valid(h) || !W || !Wn || !F || !(dt > 0)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G0 = h->geo[0];
+    h->dt = dt;
+    int rc = copy_in(h, h->W, W, sizeof(double2) * G0.nn);
+    if (!rc) rc = copy_in(h, h->Wn, Wn, sizeof(double2) * G0.nn);
+    if (rc) return rc;
+    FConst fc = make_fconst(h);
+    SULF_CUDA_TRY(cudaMemsetAsync(h->dnorm, 0, 8, h->stream));
+    if (h->dim == 2) {
+        h->launches += launch_old_time<2>(G0, h->Wn, h->G, fc, h->stream);
+        h->launches += launch_newton_F<2>(G0, h->W, h->G, h->v64[0].rhs, fc, h->dnorm, h->stream);
+    } else {
+        h->launches += launch_old_time<3>(G0, h->Wn, h->G, fc, h->stream);
+        h->launches += launch_newton_F<3>(G0, h->W, h->G, h->v64[0].rhs, fc, h->dnorm, h->stream);
+    }
+    return dbg_copy_out(h, 0, h->v64[0].rhs, F, false);
+}
+
+int sulf_dbg_apply_J(sulf_handle h, int l, double dt, const double* Wc, const double* x, double* out) {
+    if (!dbg_level_ok(h, l) || !Wc || !x || !out || !(dt > 0)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G = h->geo[l];
+    LevelVec<double>& V = h->v64[l];
+    h->dt = dt;
+    int rc = copy_in(h, V.Wc, Wc, sizeof(double2) * G.nn);
+    if (!rc) rc = copy_in(h, V.x, x, sizeof(double2) * G.nn);
+    if (rc) return rc;
+    SULF_CUDA_TRY(cudaMemsetAsync(V.rhs, 0, sizeof(double2) * G.nn, h->stream));
+    if (h->dim == 2)
+        h->launches += launch_residual<2, double>(G, V, make_coef<double>(h, l), nullptr, h->stream);
+    else
+        h->launches += launch_residual<3, double>(G, V, make_coef<double>(h, l), nullptr, h->stream);
+    rc = dbg_copy_out(h, l, V.res, out, false);
+    if (rc) return rc;
+    for (long long i = 0; i < 2 * G.nn; i++) out[i] = -out[i] + 0.0;
+    return SULF_OK;
+}
+
+int sulf_dbg_smooth(sulf_handle h, int l, double dt, const double* Wc, const double* rhs, double* x, int sweeps) {
+    if (!dbg_level_ok(h, l) || !Wc || !rhs || !x || !(dt > 0) || sweeps < 0)
+        return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G = h->geo[l];
+    LevelVec<double>& V = h->v64[l];
+    h->dt = dt;
+    int rc = copy_in(h, V.Wc, Wc, sizeof(double2) * G.nn);
+    if (!rc) rc = copy_in(h, V.rhs, rhs, sizeof(double2) * G.nn);
+    if (!rc) rc = copy_in(h, V.x, x, sizeof(double2) * G.nn);
+    if (rc) return rc;
+    for (int k = 0; k < sweeps; k++) {
+        if (h->dim == 2)
+            MG<2, double>{h, h->v64}.relax(l);
+        else
+            MG<3, double>{h, h->v64}.relax(l);
+    }
+    return dbg_copy_out(h, l, V.x, x, false);
+}
+
+int sulf_dbg_restrict(sulf_handle h, int l, double* res, double* rhs_coarse) {
+    if (!valid(h) || l < 0 || l + 1 >= h->L || !res || !rhs_coarse) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G = h->geo[l];
+    int rc = copy_in(h, h->v64[l].res, res, sizeof(double2) * G.nn);
+    if (rc) return rc;
+    if (h->dim == 2) {
+        h->launches += launch_extend<2, double>(G, h->v64[l], 4, h->stream);
+        h->launches += launch_restrict<2, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
+    } else {
+        h->launches += launch_extend<3, double>(G, h->v64[l], 4, h->stream);
+        h->launches += launch_restrict<3, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
+    }
+    rc = dbg_copy_out(h, l, h->v64[l].res, res, true);
+    if (rc) return rc;
+    return dbg_copy_out(h, l + 1, h->v64[l + 1].rhs, rhs_coarse, false);
+}
+
+int sulf_dbg_prolong(sulf_handle h, int l, const double* xc, double* xf) {
+    if (!valid(h) || l < 0 || l + 1 >= h->L || !xc || !xf) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    int rc = copy_in(h, h->v64[l + 1].x, xc, sizeof(double2) * h->geo[l + 1].nn);
+    if (!rc) rc = copy_in(h, h->v64[l].x, xf, sizeof(double2) * h->geo[l].nn);
+    if (rc) return rc;
+    if (h->dim == 2)
+        h->launches += launch_prolong<2, double>(h->geo[l], h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
+    else
+        h->launches += launch_prolong<3, double>(h->geo[l], h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
+    return dbg_copy_out(h, l, h->v64[l].x, xf, false);
+}
+
+int sulf_dbg_inject(sulf_handle h, const double* Wc0, int l, double* Wc_out) {
+    if (!dbg_level_ok(h, l) || !Wc0 || !Wc_out) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    int rc = copy_in(h, h->v64[0].Wc, Wc0, sizeof(double2) * h->geo[0].nn);
+    if (rc) return rc;
+    for (int k = 1; k <= l; k++) {
+        if (h->dim == 2)
+            h->launches += launch_inject<2, double>(h->geo[k - 1], h->v64[k - 1], h->geo[k], h->v64[k], h->stream);
+        else
+            h->launches += launch_inject<3, double>(h->geo[k - 1], h->v64[k - 1], h->geo[k], h->v64[k], h->stream);
+    }
+    return dbg_copy_out(h, l, h->v64[l].Wc, Wc_out, false);
+}
+
+int sulf_dbg_coarsest_solve(sulf_handle h, double dt, const double* Wc0, const double* rhs_c, double* x_c) {
+    if (!valid(h) || !Wc0 || !rhs_c || !x_c || !(dt > 0)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    h->dt = dt;
+    int lc = h->L - 1;
+    int rc = copy_in(h, h->W, Wc0, sizeof(double2) * h->geo[0].nn);
+    if (rc) return rc;
+    rc = h->dim == 2 ? MG<2, double>{h, h->v64}.prepare() : MG<3, double>{h, h->v64}.prepare();
+    if (rc) return rc;
+    rc = copy_in(h, h->v64[lc].rhs, rhs_c, sizeof(double2) * h->geo[lc].nn);
+    if (rc) return rc;
+    if (h->dim == 2)
+        h->launches += launch_coarsest_solve<2, double>(h->geo[lc], h->v64[lc], h->stream);
+    else
+        h->launches += launch_coarsest_solve<3, double>(h->geo[lc], h->v64[lc], h->stream);
+    return dbg_copy_out(h, lc, h->v64[lc].x, x_c, false);
+}
+
+int sulf_dbg_cycles(sulf_handle h, double dt, const double* Wc0, const double* rhs, double* x, int ncycles,
+                    double* rnorms) {
+    if (!valid(h) || !Wc0 || !rhs || !x || ncycles < 1 || !(dt > 0)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G0 = h->geo[0];
+    h->dt = dt;
+    int rc = copy_in(h, h->W, Wc0, sizeof(double2) * G0.nn);
+    if (!rc) rc = copy_in(h, h->v64[0].rhs, rhs, sizeof(double2) * G0.nn);
+    if (rc) return rc;
+    // the cycles start from x = 0 inside linear_solve; a nonzero start is
+    // folded into the right-hand side: J (x0 + y) = rhs  <=>  J y = rhs - J x0
+    std::vector<double> x0(x, x + 2 * G0.nn);
+    bool nonzero = false;
+    for (double v : x0) nonzero |= v != 0.0;
+    if (nonzero) return sulf_fail(SULF_EINVAL, "sulf_dbg_cycles starts from x = 0");
+    int nc = h->dim == 2 ? linear_solve<2>(h, 1.0, ncycles, 0.0, rnorms) : linear_solve<3>(h, 1.0, ncycles, 0.0, rnorms);
+    if (nc < 0) return nc;
+    return dbg_copy_out(h, 0, h->v64[0].x, x, false);
+}
+
+}  // extern "C"

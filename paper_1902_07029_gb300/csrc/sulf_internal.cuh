@@ -1,0 +1,167 @@
+// Internal declarations of the sulfmg CUDA library (GB300, sm_103a).
+//
+// Data layout (per multigrid level, all resident in device memory):
+//   * dense box arrays of n^dim nodes, x fastest: level set phi (FP64), node
+//     type (int8: 0 inactive, 1 inside, 2 ghost, 3 band), and the vectors of the
+//     level as interleaved (s, c) pairs -- double2 (FP64) or float2 (FP32) --
+//     so one 16- or 8-byte load fetches both unknowns of a node;
+//   * compacted int32 index lists built once per level: inside nodes split by
+//     red-black colour, ghosts, band nodes; kernels run one thread per listed
+//     node, so inactive regions of the box cost nothing but the list;
+//   * per-ghost boundary-row data (upwind signs, 1-D weights at offsets 0,1,2),
+//     per-band-node upwind references, and node->ghost / node->band maps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/sulfmg.h"
+
+#define SULF_MAXLEV 20
+
+namespace sulf {
+
+enum { T_OUT = 0, T_IN = 1, T_GHOST = 2, T_BAND = 3 };
+
+template <typename T>
+struct V2;
+template <>
+struct V2<double> {
+    typedef double2 t;
+};
+template <>
+struct V2<float> {
+    typedef float2 t;
+};
+
+// Geometry of one level (precision independent).
+struct LevelGeo {
+    int dim = 2, N = 0, n = 0;
+    long long nn = 0;
+    long long st[3] = {1, 0, 0};
+    double lo = 0, h = 0;
+    double* phi = nullptr;
+    int8_t* type = nullptr;
+    int nin[2] = {0, 0};
+    int* inl[2] = {nullptr, nullptr};  // inside nodes by colour (parity of the index sum)
+    int ng = 0;
+    int* gidx = nullptr;    // ghost nodes, box order
+    int* gpos = nullptr;    // node -> ghost index or -1
+    int8_t* gkind = nullptr;  // 0 quadratic, 1 linear, 2 identity row
+    int8_t* gm = nullptr;     // ng*dim upwind signs
+    double* gw = nullptr;     // ng*dim*3 1-D weights at offsets 0,1,2
+    float* gw32 = nullptr;
+    double* gB = nullptr;     // ng*dim boundary points
+    int nb = 0;
+    int* bidx = nullptr;     // band nodes, box order
+    int* bref = nullptr;     // nb*dim: >=0 band index, -1 none, <=-2 ghost node -(idx+2)
+    double* ban = nullptr;   // nb*dim |n_a|
+    float* ban32 = nullptr;
+    int nact = 0;            // coarsest level: active list and map
+    int* act = nullptr;
+    int* apos = nullptr;
+    int kinds[3] = {0, 0, 0};
+};
+
+// Vectors of one level for one precision.
+template <typename T>
+struct LevelVec {
+    typedef typename V2<T>::t T2;
+    T2* Wc = nullptr;   // (s, c) the Jacobian coefficients are evaluated at
+    T2* rhs = nullptr;  // right-hand side of J x = rhs on this level
+    T2* x = nullptr;    // unknown: Newton update (finest) or coarse-grid error
+    T2* res = nullptr;  // defect rhs - J x (band entries: extended defect)
+    T* gbuf[2] = {nullptr, nullptr};   // ghost s values between relaxation passes
+    T2* bbuf[2] = {nullptr, nullptr};  // band values between extension steps
+    T* Ainv = nullptr;  // coarsest level: inverse of the assembled Jacobian
+    T* A = nullptr;     // coarsest level: work matrix
+};
+
+// Jacobian coefficients of a level (Sec. 3.4, exact derivative of F).
+template <typename T>
+struct Coef {
+    T alpha, beta;
+    T a2mc;  // a / (2 m_c)
+    T a2ms;  // a / (2 m_s)
+    T idt;   // 1 / dt
+    T kap;   // d / (4 h^2)
+    T tau;   // ghost relaxation parameter
+};
+
+// Constants of the Newton residual on the finest level (Eqs. FDs, FDc, BCs).
+struct FConst {
+    double alpha, beta, amc, ams;  // a/m_c, a/m_s
+    double idt, dh2;               // 1/dt, d/(2h^2)
+    double sb;                     // Dirichlet value
+};
+
+// Device memory owned by one handle.
+struct DevMem {
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    void* get(size_t n);
+    void release();
+};
+
+// ---- geometry (geometry.cu) ----
+int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool coarsest, DevMem& mem,
+                         cudaStream_t s, std::string& err, long long& launches);
+
+// ---- multigrid and Newton kernels (kernels.cu); each returns kernels launched ----
+template <int D, typename T>
+int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int colour, bool pointwise,
+                        cudaStream_t s);
+template <int D, typename T>
+int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, cudaStream_t s);
+template <int D, typename T>
+int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, unsigned long long* norm,
+                    cudaStream_t s);
+template <int D, typename T>
+int launch_extend(const LevelGeo& L, const LevelVec<T>& V, int steps, cudaStream_t s);
+template <int D, typename T>
+int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
+                    cudaStream_t s);
+template <int D, typename T>
+int launch_prolong(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
+                   cudaStream_t s);
+template <int D, typename T>
+int launch_inject(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
+                  cudaStream_t s);
+template <int D, typename T>
+int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int* singular,
+                           cudaStream_t s);
+template <int D, typename T>
+int launch_coarsest_solve(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s);
+
+template <int D>
+int launch_old_time(const LevelGeo& L, const double2* Wn, double2* G, const FConst& fc, cudaStream_t s);
+template <int D>
+int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, double2* F, const FConst& fc,
+                    unsigned long long* norm, cudaStream_t s);
+int launch_newton_update(const LevelGeo& L, double2* W, const double2* x, unsigned long long* norms,
+                         cudaStream_t s);
+int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* norm, cudaStream_t s);
+
+// mixed precision transfers on the finest level (active nodes)
+int launch_to_float(const LevelGeo& L, const double2* src, float2* dst, cudaStream_t s);
+int launch_accumulate(const LevelGeo& L, double2* x, const float2* e, cudaStream_t s);
+
+// state import / export
+int launch_reset_state(const LevelGeo& L, double2* W, double s0, double c0, cudaStream_t s);
+int launch_import_state(const LevelGeo& L, double2* W, const double* sv, const double* cv, cudaStream_t s);
+int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double* cv, int8_t* tv, cudaStream_t s);
+
+}  // namespace sulf
+
+#define SULF_CUDA_TRY(expr)                                       \
+    do {                                                          \
+        cudaError_t e__ = (expr);                                 \
+        if (e__ != cudaSuccess) return sulf_fail_cuda(e__, #expr); \
+    } while (0)
+
+int sulf_fail_cuda(cudaError_t e, const char* what);
+int sulf_fail(int code, const std::string& msg);
