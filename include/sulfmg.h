@@ -138,6 +138,30 @@ int sulf_get_stats(sulf_handle h, sulf_stats* out);
 int sulf_set_profiling(sulf_handle h, int on);
 int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
 
+/* Newton residual F(W; W^n) (Eqs. FDs, FDc, BCs) of the finest level and its
+   max-norm, computed on caller-owned DEVICE buffers without allocating any
+   device memory.  The paper has no counterpart: this entry point exists for
+   callers that cannot call cudaMalloc at that moment -- code recording a CUDA
+   graph (allocation is not allowed during stream capture) or a loop that must
+   not pay the device-wide synchronisation of an allocation.
+     W_dev, Wn_dev  interleaved (s, c) per node, 2*(N+1)^dim doubles: the
+                    iterate and the state at t_n (values at inactive nodes are
+                    not read)
+     F_dev          output, same layout; written on active nodes only
+     fnorm_dev      output, one double: |F|_inf over the active nodes
+   Work is queued on the handle's stream and the call returns without waiting.
+   Scratch: a static array inside the library holding 65536 partial maxima
+   (512 KiB), kept by every GPU that loads the library until the process exits;
+   the call fails with SULF_EINVAL when the finest level has more than
+   16,777,216 active nodes.  The first call on a device looks up the array's
+   device address (cudaGetSymbolAddress), so make that first call before any
+   stream capture.  Every call shares the array, and each call overwrites the
+   slots it uses before reading them (nothing has to start at zero); calls
+   that overlap on the GPU -- on different streams at the same time -- race on
+   it. */
+int sulf_newton_residual_noalloc(sulf_handle h, double dt, const double* W_dev, const double* Wn_dev, double* F_dev,
+                                 double* fnorm_dev);
+
 /* Release the handle and its device memory. */
 void sulf_destroy(sulf_handle h);
 

@@ -56,6 +56,7 @@ _SIGS = {
     "sulf_get_stats": (ctypes.c_int, [P, ctypes.POINTER(SulfStats)]),
     "sulf_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
     "sulf_kernel_time": (ctypes.c_int, [P, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "sulf_newton_residual_noalloc": (ctypes.c_int, [P, ctypes.c_double, P, P, P, P]),
     "sulf_destroy": (None, [P]),
     "sulf_last_error": (ctypes.c_char_p, []),
     "sulf_dbg_level_info": (ctypes.c_int, [P, ctypes.c_int, _i64p]),
@@ -179,6 +180,12 @@ class Domain:
         st = SulfStats()
         _chk(self.lib, self.lib.sulf_get_stats(self.h, ctypes.byref(st)))
         return {f[0]: (list(getattr(st, f[0])) if f[0] == "ghost_rows" else getattr(st, f[0])) for f in st._fields_}
+
+    def newton_residual_noalloc(self, dt, W_ptr: int, Wn_ptr: int, F_ptr: int, fnorm_ptr: int):
+        """F(W; W^n) and |F|_inf on caller-owned device buffers (device
+        pointers as ints); queued on the handle's stream, no allocation."""
+        _chk(self.lib, self.lib.sulf_newton_residual_noalloc(self.h, dt, P(W_ptr), P(Wn_ptr), P(F_ptr),
+                                                             P(fnorm_ptr)))
 
     def set_profiling(self, on: bool):
         _chk(self.lib, self.lib.sulf_set_profiling(self.h, 1 if on else 0))

@@ -379,6 +379,16 @@ int copy_in(sulf_domain* d, void* dst, const void* src, size_t n) {
 
 }  // namespace
 
+// read-only views of a handle for entry points defined in other files
+namespace sulf {
+const LevelGeo* handle_fine_geo(sulf_handle h) { return h ? &h->geo[0] : nullptr; }
+const sulf_model* handle_model(sulf_handle h) { return h ? &h->model : nullptr; }
+cudaStream_t handle_stream(sulf_handle h) { return h ? h->stream : nullptr; }
+void handle_count_launches(sulf_handle h, int n) {
+    if (h) h->launches += n;
+}
+}  // namespace sulf
+
 // ===========================================================================
 // C ABI
 

@@ -155,6 +155,12 @@ int launch_reset_state(const LevelGeo& L, double2* W, double s0, double c0, cuda
 int launch_import_state(const LevelGeo& L, double2* W, const double* sv, const double* cv, cudaStream_t s);
 int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double* cv, int8_t* tv, cudaStream_t s);
 
+// read-only views of a handle (solver.cu)
+const LevelGeo* handle_fine_geo(sulf_handle h);
+const sulf_model* handle_model(sulf_handle h);
+cudaStream_t handle_stream(sulf_handle h);
+void handle_count_launches(sulf_handle h, int n);
+
 }  // namespace sulf
 
 #define SULF_CUDA_TRY(expr)                                       \
