@@ -39,16 +39,32 @@ import workloads  # noqa: E402
 METRIC = "fine-grid node-updates/s per CN step"
 UNIT = "node-updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 (non-tensor) arithmetic rate of a GB300 from the nominal figure of
-# 1.25 TFLOP/s; the relaxation kernel is bound by it (about 100 FP64 flops per
-# node update against about 100 bytes of compulsory traffic).
-FP64_PEAK_TFLOPS = 1.25
-# FP64 flops of one inside-node relaxation in 2-D (coefficients of the 2x2
-# block and the row, five-point stencil, 2x2 solve) and its compulsory bytes:
-# list index 4, rhs 16, x write 16, Wc and x of the node and (shared with the
-# other colour) its neighbours 2*16 + 2*16.
-RELAX_FLOPS_2D = 100
-RELAX_BYTES_2D = 100
+# Compulsory bytes of one inside-node relaxation (one colour) with the
+# stencil coefficients precomputed per Newton iteration, 2-D: rhs 16, inverse
+# of the 2x2 block 32, own edge coefficients 2*16, the other colour's edge
+# coefficients 2*16 and x 16 (each read once per sweep), x written 16 -- in
+# FP64; half in FP32.  About 23 flops per update: memory-bound (HBM or L2).
+RELAX_BYTES_2D = {"fp64": 144, "mixed": 72}
+RELAX_FLOPS_2D = 23
+
+
+def whole_job_value(elapsed_ms_local: float, units_local: int, device=None) -> tuple[float, float]:
+    """Replicas run independently; the job's time is the slowest rank's and its
+    throughput the units of all ranks over that time.  Returns (value per
+    second, max elapsed ms)."""
+    import torch
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([elapsed_ms_local, float(units_local)], dtype=torch.float64, device=device)
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        elapsed_ms, units = float(tmax.item()), float(tsum.item())
+    else:
+        elapsed_ms, units = elapsed_ms_local, float(units_local)
+    return units / (elapsed_ms / 1e3), elapsed_ms
 
 
 def rank_info():
@@ -251,12 +267,8 @@ def run_gpu(args):
     elapsed_ms = sum(a.elapsed_time(b) for a, b in ev)
     st1 = dom.stats()
     launches = st1["kernel_launches"] - launches0
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    value, elapsed_ms = whole_job_value(elapsed_ms, nact * args.steps, device=dev)
     clocks = sampler.stop() if sampler else None
-    value = world * nact * args.steps / (elapsed_ms / 1e3)
 
     # end to end through the C ABI with host buffers: each step uploads the
     # state, advances one CN step and downloads it (pinned host memory)
@@ -282,17 +294,17 @@ def run_gpu(args):
         peaks = measured_peaks()
         avg_us = 1e3 * relax_ms / max(relax_n, 1)
         nodes_per_launch = st0["n_inside"] / 2.0
-        achieved = RELAX_FLOPS_2D * nodes_per_launch / (avg_us * 1e-6) / 1e12 if dim == 2 else None
-        roofline = {"kernel": "k_relax_inside (finest level, one colour)", "bound": "alu",
-                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+        nbytes = RELAX_BYTES_2D[args.precision] * nodes_per_launch
+        achieved = nbytes / (avg_us * 1e-6) / 1e9 if dim == 2 and relax_n else None
+        hbm = peaks.get("hbm_gbs")
+        roofline = {"kernel": "k_relax_inside (finest level, one colour)", "bound": "hbm",
+                    "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": None,
                     "avg_launch_us": avg_us, "launches": relax_n,
-                    "algorithmic": f"{RELAX_FLOPS_2D} FP64 flop and {RELAX_BYTES_2D} B per inside-node update; "
-                                   f"{nodes_per_launch:.0f} nodes per launch",
-                    "hbm_gbs_effective": RELAX_BYTES_2D * nodes_per_launch / (avg_us * 1e-6) / 1e9,
-                    "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                    "peak_note": "FP64 rate: nominal 1.25 TFLOP/s of GB300 (no measured FP64 peak in "
-                                 "MEASURED_PEAKS.json)"}
+                    "algorithmic": f"{RELAX_BYTES_2D[args.precision]} B and {RELAX_FLOPS_2D} flop per inside-node "
+                                   f"update; {nodes_per_launch:.0f} nodes per launch",
+                    "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); the finest level's working "
+                                 "set is partly L2-resident, so the fraction can exceed what HBM alone allows"}
         if prec == 1:
             roofline["kind"] = "fp32 relaxation inside fp64 defect correction"
         cb = cpu_baseline(args.workload, budget_s=args.cpu_budget) if args.cpu_budget > 0 else None

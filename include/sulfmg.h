@@ -64,11 +64,13 @@ typedef struct {
                  defect correction (Newton residual, boundary rows of F and
                  the convergence tests stay FP64)                        default 0
    smoother      0 = collective (2x2 block, Eq. matrixP) red-black Gauss-Seidel,
-                 1 = pointwise (Eq. matrixPclassical) red-black            default 0 */
+                 1 = pointwise (Eq. matrixPclassical) red-black            default 0
+   graphs        1 = each multigrid cycle is captured once as a CUDA graph and
+                 replayed; 0 = kernels launched one by one               default 1 */
 typedef struct {
     int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;
-    int precision, smoother;
+    int precision, smoother, graphs;
 } sulf_solver;
 
 /* Counters and timings of the handle. */

@@ -26,7 +26,7 @@ class SulfSolver(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("cycle", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("ghost_sweeps", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("lin_rtol", ctypes.c_double), ("tau_s", ctypes.c_double), ("precision", ctypes.c_int),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class SulfStats(ctypes.Structure):
@@ -107,7 +107,7 @@ def _chk(lib, rc):
 
 def default_solver(**kw) -> SulfSolver:
     s = SulfSolver(nu1=2, nu2=2, cycle=1, max_newton=20, max_cycles=30, ghost_sweeps=4, newton_tol=1e-10,
-                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0)
+                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1)
     for k, v in kw.items():
         setattr(s, k, v)
     return s

@@ -101,59 +101,142 @@ inline Lists make_lists(const LevelGeo& L, bool ghosts = true) {
     return l;
 }
 
-// J x at an inside node p, and the 2x2 diagonal block P of Eq. matrixP
-template <int D, typename T, typename T2>
-__device__ __forceinline__ void inside_row(long long p, const T2* __restrict__ Wc, const T2* __restrict__ x,
-                                           const Offs<D>& of, const Coef<T>& c, T& Jxs, T& Jxc, T& Pss, T& Psc,
-                                           T& Pcs, T& Pcc, T2& xp) {
+// pointers of the stencil coefficients, passed by value to the kernels
+template <int D, typename T>
+struct CoefPtr {
+    typedef typename V2<T>::t T2;
+    const T2* edge[3];
+    const T2* Pa;
+    const T2* Pb;
+    const T2* Ia;
+    const T2* Ib;
+    const T2* gc;
+};
+
+template <int D, typename T>
+inline CoefPtr<D, T> coef_ptr(const LevelVec<T>& V) {
+    CoefPtr<D, T> c;
+    for (int a = 0; a < 3; a++) c.edge[a] = V.edge[a];
+    c.Pa = V.Pa;
+    c.Pb = V.Pb;
+    c.Ia = V.Ia;
+    c.Ib = V.Ib;
+    c.gc = V.gc;
+    return c;
+}
+
+// off-diagonal part of the s row of an inside node applied to x (Eq. JssI
+// and Eq. JscI as exact derivatives): sum over the axis neighbours q of
+// J^ss_pq x^s_q + J^sc_pq x^c_q with J^ss_pq = -g and J^sc_pq = +-e
+template <int D, typename T>
+__device__ __forceinline__ T offdiag_s(long long p, const CoefPtr<D, T>& cf, const typename V2<T>::t* __restrict__ x,
+                                       const long long* st) {
+    typedef typename V2<T>::t T2;
+    T acc = 0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        T2 ge = cf.edge[a][p];
+        T2 xe = x[p + st[a]];
+        T2 gw = cf.edge[a][p - st[a]];
+        T2 xw = x[p - st[a]];
+        acc += (ge.y * xe.y - ge.x * xe.x) - (gw.x * xw.x + gw.y * xw.y);
+    }
+    return acc;
+}
+
+// stencil coefficients of every active node from Wc: edges toward the +axis
+// neighbours, and the 2x2 diagonal block and its inverse (inside) or the c
+// row (ghost).  Sec. 3.4: J^ss_pp = phi/dt + (a/2m_c) phi c + sum g,
+// J^sc_pp = alpha s/dt + (a/2m_c)(alpha s c + phi s) + sum e,
+// J^cs_pp = (a/2m_s) phi c, J^cc_pp = 1/dt + (a/2m_s)(alpha s c + phi s).
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2<T>::t* __restrict__ Wc,
+                                               typename V2<T>::t* e0, typename V2<T>::t* e1, typename V2<T>::t* e2,
+                                               typename V2<T>::t* Pa, typename V2<T>::t* Pb, typename V2<T>::t* Ia,
+                                               typename V2<T>::t* Ib, typename V2<T>::t* gc, Coef<T> c) {
+    typedef typename V2<T>::t T2;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi = 0;
+    long long p = list_node(ls, t, kind, gi);
+    const long long st[3] = {1, n, (long long)n * n};
+    int ii[3] = {(int)(p % n), (int)((p / n) % n), D == 3 ? (int)(p / ((long long)n * n)) : 0};
+    T2* edge[3] = {e0, e1, e2};
     T2 w = Wc[p];
     T s = w.x, cp = w.y;
     T ph = c.alpha * cp + c.beta;
-    xp = x[p];
-    Pss = ph * c.idt + c.a2mc * ph * cp;
-    Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s);
-    Jxs = Pss * xp.x + Psc * xp.y;
+    T sg = 0, se = 0;
 #pragma unroll
-    for (int q = 0; q < 2 * D; q++) {
-        long long pq = p + of.o[q];
-        T2 wq = Wc[pq];
-        T2 xq = x[pq];
-        T g = c.kap * ((c.alpha * wq.y + c.beta) + ph);
-        T e = c.kap * c.alpha * (s - wq.x);
-        Pss += g;
-        Psc += e;
-        Jxs += g * (xp.x - xq.x) + e * (xp.y + xq.y);
+    for (int a = 0; a < D; a++) {
+        if (ii[a] < n - 1) {
+            T2 wq = Wc[p + st[a]];
+            T2 ge;
+            ge.x = c.kap * ((c.alpha * wq.y + c.beta) + ph);
+            ge.y = c.kap * c.alpha * (s - wq.x);
+            edge[a][p] = ge;
+            sg += ge.x;
+            se += ge.y;
+        }
+        if (kind == 1) {  // inside nodes are never on the box edge
+            T2 wq = Wc[p - st[a]];
+            sg += c.kap * ((c.alpha * wq.y + c.beta) + ph);
+            se += c.kap * c.alpha * (s - wq.x);
+        }
     }
-    Pcs = c.a2ms * ph * cp;
-    Pcc = c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
-    Jxc = Pcs * xp.x + Pcc * xp.y;
+    T Pcs = c.a2ms * ph * cp;
+    T Pcc = c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
+    if (kind == 1) {
+        T Pss = ph * c.idt + c.a2mc * ph * cp + sg;
+        T Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s) + se;
+        T inv = (T)1 / (Pss * Pcc - Psc * Pcs);
+        T2 v;
+        v.x = Pss;
+        v.y = Psc;
+        Pa[p] = v;
+        v.x = Pcs;
+        v.y = Pcc;
+        Pb[p] = v;
+        v.x = Pcc * inv;
+        v.y = -Psc * inv;
+        Ia[p] = v;
+        v.x = -Pcs * inv;
+        v.y = Pss * inv;
+        Ib[p] = v;
+    } else {
+        T2 v;
+        v.x = Pcs;
+        v.y = Pcc;
+        gc[gi] = v;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // relaxation (Sec. 3.5.1)
 
 template <int D, typename T, bool PW>
-__global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt,
-                                                      const typename V2<T>::t* __restrict__ Wc,
+__global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
                                                       const typename V2<T>::t* __restrict__ rhs,
-                                                      typename V2<T>::t* __restrict__ x, Offs<D> of, Coef<T> c) {
+                                                      typename V2<T>::t* __restrict__ x, long long st1, long long st2) {
     typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     long long p = list[t];
-    T Jxs, Jxc, Pss, Psc, Pcs, Pcc;
-    T2 xp;
-    inside_row<D, T, T2>(p, Wc, x, of, c, Jxs, Jxc, Pss, Psc, Pcs, Pcc, xp);
+    const long long st[3] = {1, st1, st2};
+    T off = offdiag_s<D, T>(p, cf, x, st);
     T2 b = rhs[p];
-    T rs = b.x - Jxs, rc = b.y - Jxc;
     T2 out;
     if (PW) {
-        out.x = xp.x + rs / Pss;
-        out.y = xp.y + rc / Pcc;
+        // Eq. matrixPclassical: the diagonal of the 2x2 block only
+        T2 xp = x[p];
+        T2 pa = cf.Pa[p], pb = cf.Pb[p];
+        out.x = (b.x - off - pa.y * xp.y) / pa.x;
+        out.y = (b.y - pb.x * xp.x) / pb.y;
     } else {
-        T det = Pss * Pcc - Psc * Pcs;
-        out.x = xp.x + (Pcc * rs - Psc * rc) / det;
-        out.y = xp.y + (Pss * rc - Pcs * rs) / det;
+        // Eq. matrixP: x_p + P^{-1} (b - J x) = P^{-1} (b - (J - P) x)
+        T2 ia = cf.Ia[p], ib = cf.Ib[p];
+        T r = b.x - off;
+        out.x = ia.x * r + ia.y * b.y;
+        out.y = ib.x * r + ib.y * b.y;
     }
     x[p] = out;
 }
@@ -202,7 +285,7 @@ __device__ __forceinline__ T ghost_dot(int gi, long long g, const int8_t* __rest
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict__ gidx, const int* __restrict__ gpos,
                                                     const int8_t* __restrict__ gm, const T* __restrict__ gw,
-                                                    const typename V2<T>::t* __restrict__ Wc,
+                                                    const typename V2<T>::t* __restrict__ gc,
                                                     const typename V2<T>::t* __restrict__ rhs,
                                                     typename V2<T>::t* x, const T* sin, T* sout, long long st1,
                                                     long long st2, Coef<T> c, int first, int last) {
@@ -215,11 +298,8 @@ __global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict
     T s_old = first ? xg.x : sin[gi];
     T2 b = rhs[g];
     T s_new = s_old + c.tau * (b.x - acc);
-    T2 w = Wc[g];
-    T ph = c.alpha * w.y + c.beta;
-    T cs = c.a2ms * ph * w.y;
-    T cc = c.idt + c.a2ms * (c.alpha * w.x * w.y + ph * w.x);
-    T c_new = xg.y + (b.y - (cs * s_new + cc * xg.y)) / cc;
+    T2 q = gc[gi];  // (J^cs_gg, J^cc_gg)
+    T c_new = xg.y + (b.y - (q.x * s_new + q.y * xg.y)) / q.y;
     T* xs = reinterpret_cast<T*>(x + g);
     xs[1] = c_new;
     if (last)
@@ -241,11 +321,10 @@ __global__ void k_ghost_scatter(int ng, const int* __restrict__ gidx, const T* _
 
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_residual(Lists ls, const int8_t* __restrict__ gm, const T* __restrict__ gw,
-                                                  const typename V2<T>::t* __restrict__ Wc,
-                                                  const typename V2<T>::t* __restrict__ rhs,
+                                                  CoefPtr<D, T> cf, const typename V2<T>::t* __restrict__ rhs,
                                                   const typename V2<T>::t* __restrict__ x,
-                                                  typename V2<T>::t* __restrict__ res, Offs<D> of, long long st1,
-                                                  long long st2, Coef<T> c, unsigned long long* norm) {
+                                                  typename V2<T>::t* __restrict__ res, long long st1, long long st2,
+                                                  unsigned long long* norm) {
     typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nb = 0;
@@ -253,22 +332,19 @@ __global__ void __launch_bounds__(kT) k_residual(Lists ls, const int8_t* __restr
         int kind, gi = 0;
         long long p = list_node(ls, t, kind, gi);
         T2 b = rhs[p];
+        T2 xp = x[p];
         T2 r;
         if (kind == 1) {
-            T Jxs, Jxc, Pss, Psc, Pcs, Pcc;
-            T2 xp;
-            inside_row<D, T, T2>(p, Wc, x, of, c, Jxs, Jxc, Pss, Psc, Pcs, Pcc, xp);
-            r.x = b.x - Jxs;
-            r.y = b.y - Jxc;
+            const long long st[3] = {1, st1, st2};
+            T off = offdiag_s<D, T>(p, cf, x, st);
+            T2 pa = cf.Pa[p], pb = cf.Pb[p];
+            r.x = b.x - (pa.x * xp.x + pa.y * xp.y + off);
+            r.y = b.y - (pb.x * xp.x + pb.y * xp.y);
         } else {
             T acc = ghost_dot<D, T>(gi, p, gm, gw, nullptr, x, nullptr, true, st1, st2);
-            T2 w = Wc[p];
-            T2 xp = x[p];
-            T ph = c.alpha * w.y + c.beta;
-            T cs = c.a2ms * ph * w.y;
-            T cc = c.idt + c.a2ms * (c.alpha * w.x * w.y + ph * w.x);
+            T2 q = cf.gc[gi];
             r.x = b.x - acc;
-            r.y = b.y - (cs * xp.x + cc * xp.y);
+            r.y = b.y - (q.x * xp.x + q.y * xp.y);
         }
         res[p] = r;
         unsigned long long a0 = abs_bits(r.x), a1 = abs_bits(r.y);
@@ -328,7 +404,8 @@ __global__ void k_extend_step(int nb, const int* __restrict__ bidx, const int* _
 // ---------------------------------------------------------------------------
 // boundary-aware full weighting (Eqs. Fstencil, Fstencilgen, Fig. Neigh):
 // inside rule at coarse inside nodes, outside rule (ghost or band) at coarse
-// ghosts; per-axis mirrored weights, invalid diagonal weight moved to the centre
+// ghosts; per-axis mirrored weights, invalid diagonal weight moved to the
+// centre.  Also zeroes the coarse error at the coarse active nodes.
 
 __device__ __forceinline__ bool valid_for(int8_t rule, int8_t t) {
     return rule == T_IN ? t == T_IN : (t == T_GHOST || t == T_BAND);
@@ -338,7 +415,8 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restrict__ ctype, int cn,
                                                   const int8_t* __restrict__ ftype, int fn,
                                                   const typename V2<T>::t* __restrict__ fres,
-                                                  typename V2<T>::t* __restrict__ crhs) {
+                                                  typename V2<T>::t* __restrict__ crhs,
+                                                  typename V2<T>::t* __restrict__ cx) {
     typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
@@ -398,6 +476,10 @@ __global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restr
     out.x = as + wc * vc.x;
     out.y = ac + wc * vc.y;
     crhs[I] = out;
+    T2 z;
+    z.x = 0;
+    z.y = 0;
+    cx[I] = z;  // the coarse-grid error starts from zero
 }
 
 // (bi/tri)linear interpolation of the coarse error to every fine active node,
@@ -505,20 +587,25 @@ __global__ void __launch_bounds__(kT) k_inject(Lists ls, int cn, const int8_t* _
 // coarsest level: assemble the Jacobian, factor it with partial pivoting and
 // form its inverse (one CTA); each cycle then applies the inverse
 
-template <int D, typename T>
+template <int D, typename T, bool SMEM>
 __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* __restrict__ act,
                                                           const int* __restrict__ apos, const int8_t* __restrict__ type,
                                                           const int* __restrict__ gpos, const int8_t* __restrict__ gm,
                                                           const T* __restrict__ gw,
                                                           const typename V2<T>::t* __restrict__ Wc, Offs<D> of,
-                                                          long long st1, long long st2, Coef<T> c, T* A, T* Ainv,
+                                                          long long st1, long long st2, Coef<T> c, T* Ag, T* Ainv_g,
                                                           int* singular) {
     typedef typename V2<T>::t T2;
-    extern __shared__ int piv[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red_v[32];
     __shared__ int red_i[32];
     const int m = 2 * nact;
     const long long mm = (long long)m * m;
+    // with SMEM the work matrix and the inverse live in shared memory (small
+    // coarsest levels) and the inverse is copied out at the end
+    T* A = SMEM ? reinterpret_cast<T*>(smem_raw) : Ag;
+    T* Ainv = SMEM ? A + mm : Ainv_g;
+    int* piv = reinterpret_cast<int*>(smem_raw + (SMEM ? 2 * mm * sizeof(T) : 0));
     for (long long i = threadIdx.x; i < mm; i += blockDim.x) A[i] = 0;
     __syncthreads();
     for (int r = threadIdx.x; r < nact; r += blockDim.x) {
@@ -646,6 +733,10 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
             Ainv[(long long)i * m + j] = acc / A[(long long)i * m + i];
         }
     }
+    if (SMEM) {
+        __syncthreads();
+        for (long long i = threadIdx.x; i < mm; i += blockDim.x) Ainv_g[i] = Ainv[i];
+    }
 }
 
 template <typename T>
@@ -653,8 +744,9 @@ __global__ void __launch_bounds__(1024) k_coarsest_solve(int nact, const int* __
                                                          const typename V2<T>::t* __restrict__ rhs,
                                                          typename V2<T>::t* __restrict__ x) {
     typedef typename V2<T>::t T2;
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     T* b = reinterpret_cast<T*>(smraw);
+    T* out = b + 2 * nact;
     const int m = 2 * nact;
     for (int r = threadIdx.x; r < nact; r += blockDim.x) {
         T2 v = rhs[act[r]];
@@ -662,18 +754,21 @@ __global__ void __launch_bounds__(1024) k_coarsest_solve(int nact, const int* __
         b[2 * r + 1] = v.y;
     }
     __syncthreads();
+    // one warp per row of the inverse, lanes over its columns
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < m; r += nw) {
+        const T* row = Ainv + (long long)r * m;
+        T acc = 0;
+        for (int j = lane; j < m; j += 32) acc += row[j] * b[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[r] = acc;
+    }
+    __syncthreads();
     for (int r = threadIdx.x; r < nact; r += blockDim.x) {
-        T a0 = 0, a1 = 0;
-        const T* row0 = Ainv + (long long)(2 * r) * m;
-        const T* row1 = row0 + m;
-        for (int j = 0; j < m; j++) {
-            a0 += row0[j] * b[j];
-            a1 += row1[j] * b[j];
-        }
-        T2 out;
-        out.x = a0;
-        out.y = a1;
-        x[act[r]] = out;
+        T2 v;
+        v.x = out[2 * r];
+        v.y = out[2 * r + 1];
+        x[act[r]] = v;
     }
 }
 
@@ -842,15 +937,26 @@ __global__ void k_export_state(const int8_t* __restrict__ type, long long nn, co
 // host launchers
 
 template <int D, typename T>
+int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    if (tot == 0) return 0;
+    k_coefs<D, T><<<nblk(tot), kT, 0, s>>>(ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa, V.Pb, V.Ia, V.Ib,
+                                            V.gc, c);
+    return 1;
+}
+
+template <int D, typename T>
 int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int colour, bool pointwise,
                         cudaStream_t s) {
     int cnt = L.nin[colour];
     if (cnt == 0) return 0;
-    Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
+    (void)c;
+    CoefPtr<D, T> cf = coef_ptr<D, T>(V);
     if (pointwise)
-        k_relax_inside<D, T, true><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, V.Wc, V.rhs, V.x, of, c);
+        k_relax_inside<D, T, true><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
     else
-        k_relax_inside<D, T, false><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, V.Wc, V.rhs, V.x, of, c);
+        k_relax_inside<D, T, false><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
     return 1;
 }
 
@@ -863,7 +969,7 @@ int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
         bool first = p == 0, last = p == passes - 1 && passes > 1;
         const T* sin = first ? nullptr : V.gbuf[(p - 1) & 1];
         T* sout = V.gbuf[p & 1];
-        k_ghost_pass<D, T><<<nblk(L.ng), kT, 0, s>>>(L.ng, L.gidx, L.gpos, L.gm, gw, V.Wc, V.rhs, V.x, sin, sout,
+        k_ghost_pass<D, T><<<nblk(L.ng), kT, 0, s>>>(L.ng, L.gidx, L.gpos, L.gm, gw, V.gc, V.rhs, V.x, sin, sout,
                                                       L.st[1], L.st[2], c, first, last);
         n++;
     }
@@ -880,9 +986,10 @@ int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, u
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
+    (void)c;
     const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
-    Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
-    k_residual<D, T><<<nblk(tot), kT, 0, s>>>(ls, L.gm, gw, V.Wc, V.rhs, V.x, V.res, of, L.st[1], L.st[2], c, norm);
+    k_residual<D, T><<<nblk(tot), kT, 0, s>>>(ls, L.gm, gw, coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2],
+                                               norm);
     return 1;
 }
 
@@ -904,7 +1011,7 @@ int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C,
                     cudaStream_t s) {
     Lists ls = make_lists(C);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_restrict<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs);
+    k_restrict<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs, CV.x);
     return 1;
 }
 
@@ -931,15 +1038,25 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
                            cudaStream_t s) {
     const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
     Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
-    size_t shm = sizeof(int) * (2 * L.nact + 1);
-    k_coarsest_factor<D, T><<<1, 1024, shm, s>>>(L.nact, L.act, L.apos, L.type, L.gpos,
-                                                 L.gm, gw, V.Wc, of, L.st[1], L.st[2], c, V.A, V.Ainv, singular);
+    const size_t m = 2 * (size_t)L.nact;
+    const size_t piv_bytes = sizeof(int) * (m + 1);
+    const size_t smem_full = 2 * m * m * sizeof(T) + piv_bytes;
+    if (smem_full <= 220 * 1024) {
+        auto kern = k_coarsest_factor<D, T, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_full);
+        kern<<<1, 1024, smem_full, s>>>(L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw, V.Wc, of, L.st[1], L.st[2],
+                                        c, V.A, V.Ainv, singular);
+    } else {
+        k_coarsest_factor<D, T, false><<<1, 1024, piv_bytes, s>>>(L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw,
+                                                                  V.Wc, of, L.st[1], L.st[2], c, V.A, V.Ainv,
+                                                                  singular);
+    }
     return 1;
 }
 
 template <int D, typename T>
 int launch_coarsest_solve(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s) {
-    size_t shm = sizeof(T) * (2 * L.nact + 1);
+    size_t shm = sizeof(T) * (4 * (size_t)L.nact + 2);
     k_coarsest_solve<T><<<1, 1024, shm, s>>>(L.nact, L.act, V.Ainv, V.rhs, V.x);
     return 1;
 }
@@ -1006,6 +1123,7 @@ int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double*
 }
 
 #define SULF_INST(D, T)                                                                                          \
+    template int launch_coefs<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, cudaStream_t);          \
     template int launch_relax_inside<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, bool,       \
                                            cudaStream_t);                                                        \
     template int launch_relax_ghosts<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, cudaStream_t); \

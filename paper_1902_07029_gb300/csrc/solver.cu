@@ -73,6 +73,20 @@ struct sulf_domain {
     bool prof = false;
     std::vector<cudaEvent_t> evpool;
     size_t evused = 0;
+    double prof_ms = 0;
+    long long prof_n = 0;
+    // one multigrid cycle captured as a CUDA graph, per precision; recaptured
+    // when anything baked into it changes
+    struct CycleGraph {
+        cudaGraphExec_t exec = nullptr;
+        double dt = 0;
+        sulf_solver sv{};
+        bool prof = false;
+        cudaStream_t stream = nullptr;
+        long long kernels = 0;
+        size_t ev0 = 0, ev1 = 0;
+    } graph[2];
+    bool capturing = false;
 };
 
 namespace {
@@ -90,6 +104,7 @@ sulf_solver default_solver() {
     s.tau_s = 0.9;
     s.precision = 0;
     s.smoother = 0;
+    s.graphs = 1;
     return s;
 }
 
@@ -157,6 +172,14 @@ int alloc_vectors(sulf_domain* d, LevelVec<T>* V, bool share_state) {
             v.gbuf[k] = (T*)d->mem.get(sizeof(T) * (G.ng + 1));
             v.bbuf[k] = (T2*)d->mem.get(sizeof(T2) * (G.nb + 1));
         }
+        for (int a = 0; a < G.dim; a++) v.edge[a] = (T2*)d->mem.get(nb2);
+        v.Pa = (T2*)d->mem.get(nb2);
+        v.Pb = (T2*)d->mem.get(nb2);
+        v.Ia = (T2*)d->mem.get(nb2);
+        v.Ib = (T2*)d->mem.get(nb2);
+        v.gc = (T2*)d->mem.get(sizeof(T2) * (G.ng + 1));
+        if (!v.Pa || !v.Pb || !v.Ia || !v.Ib || !v.gc || !v.edge[0] || !v.edge[1] || (G.dim == 3 && !v.edge[2]))
+            return sulf_fail(SULF_ENOMEM, "out of device memory");
         if ((!share_state || l > 0) && !v.Wc) return sulf_fail(SULF_ENOMEM, "out of device memory");
         if (!v.rhs || !v.x || !v.res || !v.gbuf[0] || !v.gbuf[1] || !v.bbuf[0] || !v.bbuf[1])
             return sulf_fail(SULF_ENOMEM, "out of device memory");
@@ -212,14 +235,17 @@ struct MG {
         for (int colour = 0; colour < 2; colour++) {
             bool timed = d->prof && l == 0;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
+            // inside stream capture a plain record only adds a dependency; the
+            // external flag makes it an event-record node of the graph
+            unsigned fl = d->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
             if (timed) {
                 e0 = next_event(d);
-                cudaEventRecord(e0, d->stream);
+                cudaEventRecordWithFlags(e0, d->stream, fl);
             }
             d->launches += launch_relax_inside<D, T>(G, V[l], c, colour, pw, d->stream);
             if (timed) {
                 e1 = next_event(d);
-                cudaEventRecord(e1, d->stream);
+                cudaEventRecordWithFlags(e1, d->stream, fl);
             }
         }
         d->launches += launch_relax_ghosts<D, T>(G, V[l], c, d->solver.ghost_sweeps, d->stream);
@@ -235,23 +261,118 @@ struct MG {
         d->launches += launch_residual<D, T>(d->geo[l], V[l], make_coef<T>(d, l), nullptr, d->stream);
         d->launches += launch_extend<D, T>(d->geo[l], V[l], 4, d->stream);
         d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
-        cudaMemsetAsync(V[l + 1].x, 0, sizeof(typename V2<T>::t) * d->geo[l + 1].nn, d->stream);
         int gam = d->solver.cycle == 2 ? 2 : 1;
         for (int g = 0; g < gam; g++) cycle(l + 1);
         d->launches += launch_prolong<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
         for (int k = 0; k < d->solver.nu2; k++) relax(l);
     }
 
-    // coarse coefficients from V[0].Wc and the coarsest factorisation
+    // coarse coefficients from V[0].Wc, the stencil coefficients of every
+    // level and the coarsest factorisation (once per Newton iteration)
     int prepare() {
         for (int l = 1; l < d->L; l++)
             d->launches += launch_inject<D, T>(d->geo[l - 1], V[l - 1], d->geo[l], V[l], d->stream);
+        for (int l = 0; l < d->L; l++)
+            d->launches += launch_coefs<D, T>(d->geo[l], V[l], make_coef<T>(d, l), d->stream);
         SULF_CUDA_TRY(cudaMemsetAsync(d->dsing, 0, sizeof(int), d->stream));
         int lc = d->L - 1;
         d->launches += launch_coarsest_factor<D, T>(d->geo[lc], V[lc], make_coef<T>(d, lc), d->dsing, d->stream);
         return SULF_OK;
     }
 };
+
+// sum the device time of the event pairs [from, to) of the pool
+int accumulate_prof(sulf_domain* d, size_t from, size_t to) {
+    for (size_t k = from; k + 1 < to; k += 2) {
+        float e = 0;
+        SULF_CUDA_TRY(cudaEventElapsedTime(&e, d->evpool[k], d->evpool[k + 1]));
+        d->prof_ms += e;
+        d->prof_n++;
+    }
+    return SULF_OK;
+}
+
+// One cycle of the linear solve on the finest level, then the FP64 defect
+// r = F - J dW, its max-norm and the coarsest-level singularity flag copied to
+// pinned host memory.  FP64: a multigrid cycle on J dW = F.  Mixed: an FP32
+// cycle on J e = r from e = 0, dW += e, then the next FP32 right-hand side.
+template <int D>
+int cycle_body(sulf_domain* d) {
+    const LevelGeo& G0 = d->geo[0];
+    LevelVec<double>& V0 = d->v64[0];
+    if (d->solver.precision == 0) {
+        if (d->L == 1)
+            d->launches += launch_coarsest_solve<D, double>(G0, V0, d->stream);
+        else
+            MG<D, double>{d, d->v64}.cycle(0);
+    } else {
+        LevelVec<float>& U0 = d->v32[0];
+        SULF_CUDA_TRY(cudaMemsetAsync(U0.x, 0, sizeof(float2) * G0.nn, d->stream));
+        if (d->L == 1)
+            d->launches += launch_coarsest_solve<D, float>(G0, U0, d->stream);
+        else
+            MG<D, float>{d, d->v32}.cycle(0);
+        d->launches += launch_accumulate(G0, V0.x, U0.x, d->stream);
+    }
+    SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
+    d->launches += launch_residual<D, double>(G0, V0, make_coef<double>(d, 0), d->dnorm, d->stream);
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, d->stream));
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    if (d->solver.precision == 1) d->launches += launch_to_float(G0, V0.res, d->v32[0].rhs, d->stream);
+    return SULF_OK;
+}
+
+bool same_solver(const sulf_solver& a, const sulf_solver& b) { return memcmp(&a, &b, sizeof a) == 0; }
+
+// run one cycle: replay the captured graph (capturing it first if needed), or
+// launch the kernels directly
+template <int D>
+int run_cycle(sulf_domain* d) {
+    int p = d->solver.precision;
+    if (!d->solver.graphs) {
+        size_t e0 = d->evused;
+        int rc = cycle_body<D>(d);
+        if (rc) return rc;
+        SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+        rc = accumulate_prof(d, e0, d->evused);
+        d->evused = e0;
+        return rc;
+    }
+    sulf_domain::CycleGraph& g = d->graph[p];
+    if (!g.exec || g.dt != d->dt || !same_solver(g.sv, d->solver) || g.prof != d->prof || g.stream != d->stream) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        d->evused = 0;
+        g.ev0 = 0;
+        long long l0 = d->launches;
+        SULF_CUDA_TRY(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+        d->capturing = true;
+        int rc = cycle_body<D>(d);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(d->stream, &graph);
+        d->capturing = false;
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return sulf_fail_cuda(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return sulf_fail_cuda(e, "cudaGraphInstantiate");
+        g.kernels = d->launches - l0;
+        d->launches = l0;
+        g.ev1 = d->evused;
+        g.dt = d->dt;
+        g.sv = d->solver;
+        g.prof = d->prof;
+        g.stream = d->stream;
+    }
+    SULF_CUDA_TRY(cudaGraphLaunch(g.exec, d->stream));
+    d->launches += g.kernels;
+    SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+    if (d->prof) return accumulate_prof(d, g.ev0, g.ev1);
+    return SULF_OK;
+}
 
 // Solve J(W) dW = F on the finest level: FP64 cycles, or FP32 cycles on the
 // FP64 defect (defect correction).  v64[0].rhs holds F, the result is left in
@@ -260,55 +381,24 @@ template <int D>
 int linear_solve(sulf_domain* d, double fnorm, int max_cycles, double rtol, double* rnorms) {
     const LevelGeo& G0 = d->geo[0];
     SULF_CUDA_TRY(cudaMemsetAsync(d->v64[0].x, 0, sizeof(double2) * G0.nn, d->stream));
+    int rc;
     if (d->solver.precision == 0) {
-        MG<D, double> mg{d, d->v64};
-        int rc = mg.prepare();
+        rc = MG<D, double>{d, d->v64}.prepare();
+    } else {
+        rc = ensure32(d);
         if (rc) return rc;
-        if (d->L == 1) {
-            d->launches += launch_coarsest_solve<D, double>(G0, d->v64[0], d->stream);
-            return 1;
-        }
-        double rprev = fnorm;
-        int cyc;
-        for (cyc = 1; cyc <= max_cycles; cyc++) {
-            mg.cycle(0);
-            SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
-            d->launches += launch_residual<D, double>(G0, d->v64[0], make_coef<double>(d, 0), d->dnorm, d->stream);
-            SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
-            rc = read_norms(d, 1);
-            if (rc) return rc;
-            if (*(int*)(d->hnorm + 6)) return sulf_fail(SULF_ENOTCONV, "singular coarsest-level Jacobian");
-            double rn = bits_to_double(d->hnorm[0]);
-            if (rnorms) rnorms[cyc - 1] = rn;
-            d->last_rho = rprev > 0 ? rn / rprev : 0.0;
-            rprev = rn;
-            if (rn <= rtol * fnorm || rn != rn) break;
-        }
-        return cyc > max_cycles ? max_cycles : cyc;
+        d->launches += launch_to_float(G0, d->W, d->v32[0].Wc, d->stream);
+        // the FP64 defect of the outer iteration needs the FP64 finest-level coefficients
+        d->launches += launch_coefs<D, double>(G0, d->v64[0], make_coef<double>(d, 0), d->stream);
+        rc = MG<D, float>{d, d->v32}.prepare();
+        if (rc) return rc;
+        d->launches += launch_to_float(G0, d->v64[0].rhs, d->v32[0].rhs, d->stream);
     }
-    // mixed precision: FP32 cycles on the FP64 defect
-    int rc = ensure32(d);
     if (rc) return rc;
-    LevelVec<double>& V0 = d->v64[0];
-    LevelVec<float>& U0 = d->v32[0];
-    d->launches += launch_to_float(G0, d->W, U0.Wc, d->stream);
-    MG<D, float> mg{d, d->v32};
-    rc = mg.prepare();
-    if (rc) return rc;
-    d->launches += launch_to_float(G0, V0.rhs, U0.rhs, d->stream);
     double rprev = fnorm;
     int cyc;
     for (cyc = 1; cyc <= max_cycles; cyc++) {
-        SULF_CUDA_TRY(cudaMemsetAsync(U0.x, 0, sizeof(float2) * G0.nn, d->stream));
-        if (d->L == 1)
-            d->launches += launch_coarsest_solve<D, float>(G0, U0, d->stream);
-        else
-            mg.cycle(0);
-        d->launches += launch_accumulate(G0, V0.x, U0.x, d->stream);
-        SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
-        d->launches += launch_residual<D, double>(G0, V0, make_coef<double>(d, 0), d->dnorm, d->stream);
-        SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
-        rc = read_norms(d, 1);
+        rc = run_cycle<D>(d);
         if (rc) return rc;
         if (*(int*)(d->hnorm + 6)) return sulf_fail(SULF_ENOTCONV, "singular coarsest-level Jacobian");
         double rn = bits_to_double(d->hnorm[0]);
@@ -316,7 +406,6 @@ int linear_solve(sulf_domain* d, double fnorm, int max_cycles, double rtol, doub
         d->last_rho = rprev > 0 ? rn / rprev : 0.0;
         rprev = rn;
         if (rn <= rtol * fnorm || rn != rn) break;
-        d->launches += launch_to_float(G0, V0.res, U0.rhs, d->stream);
     }
     return cyc > max_cycles ? max_cycles : cyc;
 }
@@ -399,6 +488,8 @@ const char* sulf_last_error(void) { return g_err.c_str(); }
 void sulf_destroy(sulf_handle h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& g : h->graph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     h->mem.release();
     if (h->hnorm) cudaFreeHost(h->hnorm);
@@ -508,7 +599,7 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
     sulf_solver v = s ? *s : default_solver();
     if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || (v.cycle != 1 && v.cycle != 2) || v.max_newton < 1 ||
         v.max_cycles < 1 || v.ghost_sweeps < 1 || !(v.tau_s > 0 && v.tau_s < 1) || !(v.newton_tol > 0) ||
-        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1))
+        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1))
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
     if (v.precision == 1) return ensure32(h);
@@ -593,22 +684,18 @@ int sulf_set_profiling(sulf_handle h, int on) {
     if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
     SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->prof = on != 0;
-    h->evused = 0;
+    h->prof_ms = 0;
+    h->prof_n = 0;
     return SULF_OK;
 }
 
 int sulf_kernel_time(sulf_handle h, double* ms, long long* launches) {
     if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
     SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    double tot = 0;
-    for (size_t k = 0; k + 1 < h->evused; k += 2) {
-        float e = 0;
-        SULF_CUDA_TRY(cudaEventElapsedTime(&e, h->evpool[k], h->evpool[k + 1]));
-        tot += e;
-    }
-    if (ms) *ms = tot;
-    if (launches) *launches = (long long)(h->evused / 2);
-    h->evused = 0;
+    if (ms) *ms = h->prof_ms;
+    if (launches) *launches = h->prof_n;
+    h->prof_ms = 0;
+    h->prof_n = 0;
     return SULF_OK;
 }
 
@@ -695,10 +782,13 @@ int sulf_dbg_apply_J(sulf_handle h, int l, double dt, const double* Wc, const do
     if (!rc) rc = copy_in(h, V.x, x, sizeof(double2) * G.nn);
     if (rc) return rc;
     SULF_CUDA_TRY(cudaMemsetAsync(V.rhs, 0, sizeof(double2) * G.nn, h->stream));
-    if (h->dim == 2)
+    if (h->dim == 2) {
+        h->launches += launch_coefs<2, double>(G, V, make_coef<double>(h, l), h->stream);
         h->launches += launch_residual<2, double>(G, V, make_coef<double>(h, l), nullptr, h->stream);
-    else
+    } else {
+        h->launches += launch_coefs<3, double>(G, V, make_coef<double>(h, l), h->stream);
         h->launches += launch_residual<3, double>(G, V, make_coef<double>(h, l), nullptr, h->stream);
+    }
     rc = dbg_copy_out(h, l, V.res, out, false);
     if (rc) return rc;
     for (long long i = 0; i < 2 * G.nn; i++) out[i] = -out[i] + 0.0;
@@ -715,6 +805,10 @@ int sulf_dbg_smooth(sulf_handle h, int l, double dt, const double* Wc, const dou
     if (!rc) rc = copy_in(h, V.rhs, rhs, sizeof(double2) * G.nn);
     if (!rc) rc = copy_in(h, V.x, x, sizeof(double2) * G.nn);
     if (rc) return rc;
+    if (h->dim == 2)
+        h->launches += launch_coefs<2, double>(G, V, make_coef<double>(h, l), h->stream);
+    else
+        h->launches += launch_coefs<3, double>(G, V, make_coef<double>(h, l), h->stream);
     for (int k = 0; k < sweeps; k++) {
         if (h->dim == 2)
             MG<2, double>{h, h->v64}.relax(l);

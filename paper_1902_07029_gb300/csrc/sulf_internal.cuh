@@ -79,6 +79,15 @@ struct LevelVec {
     T2* bbuf[2] = {nullptr, nullptr};  // band values between extension steps
     T* Ainv = nullptr;  // coarsest level: inverse of the assembled Jacobian
     T* A = nullptr;     // coarsest level: work matrix
+    // Jacobian stencil coefficients, refreshed once per Newton iteration from
+    // Wc (the matrix is constant during a linear solve):
+    T2* edge[3] = {nullptr, nullptr, nullptr};  // per node (g, e) toward the +axis neighbour:
+                                                // g = kappa (phi_q + phi_p), e = kappa alpha (s_p - s_q)
+    T2* Pa = nullptr;  // inside nodes: (J^ss_pp, J^sc_pp)
+    T2* Pb = nullptr;  //               (J^cs_pp, J^cc_pp)
+    T2* Ia = nullptr;  //               rows of the inverse of that 2x2 block
+    T2* Ib = nullptr;
+    T2* gc = nullptr;  // per ghost: (J^cs_gg, J^cc_gg)
 };
 
 // Jacobian coefficients of a level (Sec. 3.4, exact derivative of F).
@@ -112,6 +121,8 @@ int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool c
                          cudaStream_t s, std::string& err, long long& launches);
 
 // ---- multigrid and Newton kernels (kernels.cu); each returns kernels launched ----
+template <int D, typename T>
+int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cudaStream_t s);
 template <int D, typename T>
 int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int colour, bool pointwise,
                         cudaStream_t s);
