@@ -325,19 +325,154 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """256 random-star instances, sizes uniform in {129, 257, 513, 1025}^2,
+    mixed precision, advanced together by the batching runtime; compared with
+    the same instances advanced one after the other in plain FP64."""
+    import torch
+
+    import paper_1902_07029_gb300 as pkg
+
+    pkg.build()
+    rng = np.random.default_rng(4)
+    n_inst = args.instances
+    sizes = rng.choice([128, 256, 512, 1024], size=n_inst)
+    params = [workloads.random_star_params(rng) for _ in range(n_inst)]
+
+    def make(precision):
+        doms = []
+        for N, (a, p, s_ext) in zip(sizes, params):
+            d = pkg.Domain(workloads.random_star(int(N), a, p), 2, (-1.0, 1.0), int(N))
+            m = list(workloads.PAPER_MODEL)
+            m[6] = s_ext
+            d.set_model(m)
+            d.set_solver(precision=precision)
+            doms.append(d)
+        return doms
+
+    dts = [2.0 / float(N) for N in sizes]
+    steps = args.steps
+    out = {}
+    for label, precision, batched in (("batched_mixed", 1, True), ("sequential_fp64", 0, False)):
+        doms = make(precision)
+        nact = sum(d.stats()["n_inside"] + d.stats()["n_ghost"] for d in doms)
+        if batched:
+            b = pkg.Batch(doms, nstreams=args.streams)
+            b.step(dts, 1)  # warm-up: graphs, cluster kernels
+            for d in doms:
+                d.set_model(d_model(d, doms, sizes, params))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.step(dts, steps)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            b.close()
+        else:
+            for d, dt in zip(doms, dts):
+                d.step(dt, 1)
+            for d in doms:
+                d.set_model(d_model(d, doms, sizes, params))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for d, dt in zip(doms, dts):
+                d.step(dt, steps)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+        out[label] = {"value": nact * steps / el, "seconds": el}
+        for d in doms:
+            d.close()
+    line = {"metric": METRIC, "value": out["batched_mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {n_inst} random stars, sizes uniform in {{129,257,513,1025}}^2",
+                       "precision": "mixed", "streams": args.streams, "cn_steps_per_instance": steps},
+            "sequential_fp64": out["sequential_fp64"], "batched_mixed": out["batched_mixed"]}
+    print(json.dumps(line), flush=True)
+
+
+def d_model(d, doms, sizes, params):
+    i = doms.index(d)
+    m = list(workloads.PAPER_MODEL)
+    m[6] = params[i][2]
+    return m
+
+
+def run_serve(args):
+    """Poisson arrivals (seed 5) of jobs: 70% 2-D random stars with
+    N in {256, 512, 1024, 2048}, 30% 3-D random rounded boxes with N in
+    {64, 128}; 20-100 CN steps each, mixed precision, HBM budget 150 GB."""
+    import paper_1902_07029_gb300 as pkg
+
+    pkg.build()
+    rng = np.random.default_rng(5)
+    jobs = []
+    for _ in range(args.jobs):
+        if rng.random() < 0.7:
+            N = int(rng.choice([256, 512, 1024, 2048]))
+            a, p, s_ext = workloads.random_star_params(rng)
+            phi = workloads.random_star(N, a, p)
+            dim, cN = 2, 8
+            m = list(workloads.PAPER_MODEL)
+            m[6] = s_ext
+        else:
+            N = int(rng.choice([64, 128]))
+            phi, _, _ = workloads.random_rounded_box(N, rng)
+            dim, cN = 3, 4
+            m = list(workloads.PAPER_MODEL)
+        nsteps = int(rng.integers(20, 101))
+        dt = 2.0 / N if dim == 2 else 0.5 * 2.0 / N
+        jobs.append((phi, dim, N, cN, m, dt, nsteps))
+    rate = args.rate
+    gaps = rng.exponential(1.0 / rate, size=len(jobs))
+    srv = pkg.Server(budget_bytes=150 << 30, nworkers=args.streams)
+    t0 = time.perf_counter()
+    ids = []
+    for (phi, dim, N, cN, m, dt, nsteps), gap in zip(jobs, gaps):
+        time.sleep(gap)
+        ids.append(srv.submit(phi, dim, N, m, dt, nsteps, coarsest_N=cN, precision=1))
+    failed = 0
+    nodes = 0.0
+    for i, (phi, dim, N, cN, m, dt, nsteps) in zip(ids, jobs):
+        try:
+            s, c, res = srv.wait(i)
+            nodes += float(np.count_nonzero(phi < 0)) * nsteps
+        except pkg.SulfError:
+            failed += 1
+    el = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    line = {"metric": "jobs/s and p50/p99 job latency", "value": st["completed"] / el, "unit": "jobs/s",
+            "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": "Poisson-arrival serving of random star / rounded-box jobs", "jobs": len(jobs),
+                       "arrival_rate_per_s": rate, "workers": args.streams, "budget_GB": 150},
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"], "failed": failed,
+            "max_running": st["max_running"], "peak_reserved_GB": st["peak_reserved_bytes"] / 2 ** 30,
+            "inside_node_updates_per_s": nodes / el, "wall_s": el}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sulfmg", choices=["sulfmg", "reference"])
-    ap.add_argument("--workload", default="star1025", choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--workload", default="star1025", choices=sorted(workloads.WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--instances", type=int, default=256, help="batch: number of instances")
+    ap.add_argument("--streams", type=int, default=8, help="batch/serve: worker streams")
+    ap.add_argument("--jobs", type=int, default=40, help="serve: number of jobs")
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate (jobs/s)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle CPU work for cpu_baseline")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

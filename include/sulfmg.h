@@ -66,11 +66,15 @@ typedef struct {
    smoother      0 = collective (2x2 block, Eq. matrixP) red-black Gauss-Seidel,
                  1 = pointwise (Eq. matrixPclassical) red-black            default 0
    graphs        1 = each multigrid cycle is captured once as a CUDA graph and
-                 replayed; 0 = kernels launched one by one               default 1 */
+                 replayed; 0 = kernels launched one by one               default 1
+   fuse_below    the first level with at most this many active nodes and all
+                 coarser ones run as one single-CTA kernel per V-cycle;
+                 0 = every level as separate kernels (W-cycles always are)
+                                                                         default 1500 */
 typedef struct {
     int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;
-    int precision, smoother, graphs;
+    int precision, smoother, graphs, fuse_below;
 } sulf_solver;
 
 /* Counters and timings of the handle. */
@@ -85,6 +89,7 @@ typedef struct {
     int levels;             /* multigrid levels */
     long long n_inside, n_ghost; /* finest-level inside and ghost nodes (Eq. ghostdef) */
     int ghost_rows[3];      /* finest-level ghost rows: quadratic, linear, identity */
+    unsigned long long device_bytes; /* device memory the handle holds */
 } sulf_stats;
 
 /* Build a domain.  levelset: host array of (N+1)^dim node values of phi
@@ -166,6 +171,67 @@ int sulf_newton_residual_noalloc(sulf_handle h, double dt, const double* W_dev, 
 
 /* Release the handle and its device memory. */
 void sulf_destroy(sulf_handle h);
+
+/* ---- batching: many independent domains advanced together ----
+   The handles stay owned by the caller (one batch per set of handles; do not
+   use them elsewhere while sulf_batch_step runs).  nstreams host workers, each
+   with its own CUDA stream, take the instances largest-work-first, so the GPU
+   runs several instances' kernels at once.  Results are those of advancing
+   each handle alone. */
+typedef struct sulf_batch_s* sulf_batch;
+int sulf_batch_create(const sulf_handle* handles, int n, int nstreams, sulf_batch* out);
+/* advance instance i by nsteps[i] CN steps of size dt[i]; returns the first
+   failing instance's error (all instances are attempted) */
+int sulf_batch_step(sulf_batch b, const double* dt, const int* nsteps);
+int sulf_batch_status(sulf_batch b, int* status); /* per-instance return codes of the last step */
+void sulf_batch_destroy(sulf_batch b);             /* the handles return to their own streams */
+
+/* ---- serving: continuous batching of time-stepping jobs under an HBM budget ---- */
+typedef struct {
+    const double* levelset; /* (N+1)^dim host values, copied at submission */
+    int dim, N, coarsest_N;
+    double box_lo, box_hi;
+    sulf_model model;
+    sulf_solver solver;
+    double dt;
+    int nsteps;
+} sulf_job;
+
+typedef struct {
+    int status;               /* the job's return code */
+    double latency_ms;        /* submission to result ready */
+    double queue_ms, run_ms;  /* waiting for admission / running */
+    unsigned long long estimate_bytes, device_bytes;
+    long long newton, cycles;
+} sulf_job_result;
+
+typedef struct {
+    long long completed, failed, queued, running, max_running;
+    double p50_ms, p99_ms;    /* latency percentiles of the completed jobs */
+    double jobs_per_s;        /* completed jobs per second since creation */
+    unsigned long long budget_bytes, peak_reserved_bytes;
+} sulf_server_stats;
+
+/* Device memory a domain of this size will hold (an upper estimate used for
+   admission); 0 on invalid arguments. */
+unsigned long long sulf_estimate_device_bytes(int dim, int N, int coarsest_N, int precision);
+
+typedef struct sulf_server_s* sulf_server;
+/* nworkers host workers, each with its own CUDA stream, run admitted jobs.
+   A job is admitted (first come first served among the jobs that fit) when its
+   estimate fits in the budget left by the running jobs; its memory returns to
+   the budget when it finishes. */
+int sulf_server_create(unsigned long long budget_bytes, int nworkers, sulf_server* out);
+/* queue a job (the level set is copied; returns at once); SULF_ENOMEM if the
+   job's estimate exceeds the whole budget */
+int sulf_server_submit(sulf_server s, const sulf_job* job, long long* job_id);
+int sulf_server_poll(sulf_server s, long long job_id, int* done);
+/* block until the job is done, copy its state ((N+1)^dim host values each, may
+   be NULL) and result, and forget the job; returns the job's return code */
+int sulf_server_wait(sulf_server s, long long job_id, double* s_out, double* c_out, sulf_job_result* res);
+int sulf_server_get_stats(sulf_server s, sulf_server_stats* out);
+/* finish the queued and running jobs, then release the server */
+void sulf_server_destroy(sulf_server s);
 
 /* Message of the calling thread's last error ("" if none). */
 const char* sulf_last_error(void);

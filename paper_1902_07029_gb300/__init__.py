@@ -26,7 +26,7 @@ class SulfSolver(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("cycle", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("ghost_sweeps", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("lin_rtol", ctypes.c_double), ("tau_s", ctypes.c_double), ("precision", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("graphs", ctypes.c_int), ("fuse_below", ctypes.c_int)]
 
 
 class SulfStats(ctypes.Structure):
@@ -34,7 +34,27 @@ class SulfStats(ctypes.Structure):
                 ("newton_total", ctypes.c_longlong), ("cycles_total", ctypes.c_longlong),
                 ("steps_total", ctypes.c_longlong), ("last_rho", ctypes.c_double), ("last_fnorm", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("levels", ctypes.c_int), ("n_inside", ctypes.c_longlong),
-                ("n_ghost", ctypes.c_longlong), ("ghost_rows", ctypes.c_int * 3)]
+                ("n_ghost", ctypes.c_longlong), ("ghost_rows", ctypes.c_int * 3),
+                ("device_bytes", ctypes.c_ulonglong)]
+
+
+class SulfJob(ctypes.Structure):
+    _fields_ = [("levelset", ctypes.POINTER(ctypes.c_double)), ("dim", ctypes.c_int), ("N", ctypes.c_int),
+                ("coarsest_N", ctypes.c_int), ("box_lo", ctypes.c_double), ("box_hi", ctypes.c_double),
+                ("model", SulfModel), ("solver", SulfSolver), ("dt", ctypes.c_double), ("nsteps", ctypes.c_int)]
+
+
+class SulfJobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("estimate_bytes", ctypes.c_ulonglong),
+                ("device_bytes", ctypes.c_ulonglong), ("newton", ctypes.c_longlong), ("cycles", ctypes.c_longlong)]
+
+
+class SulfServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("queued", ctypes.c_longlong),
+                ("running", ctypes.c_longlong), ("max_running", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("jobs_per_s", ctypes.c_double), ("budget_bytes", ctypes.c_ulonglong),
+                ("peak_reserved_bytes", ctypes.c_ulonglong)]
 
 
 _lib = None
@@ -57,6 +77,17 @@ _SIGS = {
     "sulf_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
     "sulf_kernel_time": (ctypes.c_int, [P, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "sulf_newton_residual_noalloc": (ctypes.c_int, [P, ctypes.c_double, P, P, P, P]),
+    "sulf_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]),
+    "sulf_batch_step": (ctypes.c_int, [P, _dp, ctypes.POINTER(ctypes.c_int)]),
+    "sulf_batch_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
+    "sulf_batch_destroy": (None, [P]),
+    "sulf_estimate_device_bytes": (ctypes.c_ulonglong, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "sulf_server_create": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_int, ctypes.POINTER(P)]),
+    "sulf_server_submit": (ctypes.c_int, [P, ctypes.POINTER(SulfJob), ctypes.POINTER(ctypes.c_longlong)]),
+    "sulf_server_poll": (ctypes.c_int, [P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
+    "sulf_server_wait": (ctypes.c_int, [P, ctypes.c_longlong, _dp, _dp, ctypes.POINTER(SulfJobResult)]),
+    "sulf_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(SulfServerStats)]),
+    "sulf_server_destroy": (None, [P]),
     "sulf_destroy": (None, [P]),
     "sulf_last_error": (ctypes.c_char_p, []),
     "sulf_dbg_level_info": (ctypes.c_int, [P, ctypes.c_int, _i64p]),
@@ -107,7 +138,7 @@ def _chk(lib, rc):
 
 def default_solver(**kw) -> SulfSolver:
     s = SulfSolver(nu1=2, nu2=2, cycle=1, max_newton=20, max_cycles=30, ghost_sweeps=4, newton_tol=1e-10,
-                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1)
+                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1, fuse_below=1500)
     for k, v in kw.items():
         setattr(s, k, v)
     return s
@@ -276,3 +307,98 @@ class Domain:
         rn = np.zeros(ncycles)
         _chk(self.lib, self.lib.sulf_dbg_cycles(self.h, dt, _d(Wc0), _d(rhs), _d(x), ncycles, _d(rn)))
         return x, rn
+
+
+class Batch:
+    """Many domains advanced together (each keeps its own state and results)."""
+
+    def __init__(self, domains, nstreams=8):
+        self.lib = load()
+        self.domains = list(domains)
+        arr = (P * len(self.domains))(*[d.h for d in self.domains])
+        b = P()
+        _chk(self.lib, self.lib.sulf_batch_create(arr, len(self.domains), nstreams, ctypes.byref(b)))
+        self.b = b
+
+    def step(self, dt, nsteps):
+        n = len(self.domains)
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        ns = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int32), (n,)))
+        _chk(self.lib, self.lib.sulf_batch_step(self.b, _d(dts), ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+
+    def status(self):
+        st = np.zeros(len(self.domains), dtype=np.int32)
+        _chk(self.lib, self.lib.sulf_batch_status(self.b, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return st
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.sulf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_device_bytes(dim, N, coarsest_N=8, precision=0):
+    return int(load().sulf_estimate_device_bytes(dim, N, coarsest_N, precision))
+
+
+class Server:
+    """Continuous batching of time-stepping jobs under a device-memory budget."""
+
+    def __init__(self, budget_bytes, nworkers=4):
+        self.lib = load()
+        s = P()
+        _chk(self.lib, self.lib.sulf_server_create(int(budget_bytes), nworkers, ctypes.byref(s)))
+        self.s = s
+        self._shape = {}
+
+    def submit(self, levelset, dim, N, model, dt, nsteps, box=(-1.0, 1.0), coarsest_N=8, **solver):
+        phi = np.ascontiguousarray(levelset, dtype=np.float64)
+        job = SulfJob(levelset=_d(phi), dim=dim, N=N, coarsest_N=coarsest_N, box_lo=box[0], box_hi=box[1],
+                      model=SulfModel(*[float(v) for v in model]), solver=default_solver(**solver), dt=dt,
+                      nsteps=nsteps)
+        jid = ctypes.c_longlong(0)
+        _chk(self.lib, self.lib.sulf_server_submit(self.s, ctypes.byref(job), ctypes.byref(jid)))
+        self._shape[jid.value] = phi.shape
+        return jid.value
+
+    def done(self, jid):
+        d = ctypes.c_int(0)
+        _chk(self.lib, self.lib.sulf_server_poll(self.s, jid, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, jid):
+        """(s, c, result dict); raises SulfError if the job failed."""
+        shape = self._shape.pop(jid)
+        nn = int(np.prod(shape))
+        s = np.zeros(nn)
+        c = np.zeros(nn)
+        r = SulfJobResult()
+        rc = self.lib.sulf_server_wait(self.s, jid, _d(s), _d(c), ctypes.byref(r))
+        res = {f[0]: getattr(r, f[0]) for f in r._fields_}
+        if rc != OK:
+            err = SulfError(rc, self.lib.sulf_last_error().decode())
+            err.result = res
+            raise err
+        return s.reshape(shape), c.reshape(shape), res
+
+    def stats(self):
+        st = SulfServerStats()
+        _chk(self.lib, self.lib.sulf_server_get_stats(self.s, ctypes.byref(st)))
+        return {f[0]: getattr(st, f[0]) for f in st._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.sulf_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -8,21 +8,22 @@
 // JssI, JscI, JcsI, JccI as exact derivatives of F), so a relaxation sweep
 // moves 16 B of coefficients, 16 B of right-hand side and 16 B of unknowns
 // per node instead of a dozen stored matrix entries.
-#include "sulf_internal.cuh"
+#include "mg_stages.cuh"
 
 namespace sulf {
+
+using stages::abs_bits;
+using stages::coef_ptr;
+using stages::CoefPtr;
+using stages::list_node;
+using stages::Lists;
+using stages::make_lists;
 
 namespace {
 
 constexpr int kT = 256;
 
 inline unsigned nblk(long long n, int t = kT) { return (unsigned)((n + t - 1) / t); }
-
-template <typename T>
-__device__ __forceinline__ unsigned long long abs_bits(T v) {
-    double d = fabs((double)v);
-    return (unsigned long long)__double_as_longlong(d);
-}
 
 // max over the block of non-negative doubles held as bit patterns (NaN, whose
 // pattern exceeds +inf, propagates), then one atomicMax per block
@@ -63,85 +64,6 @@ __host__ __device__ inline Offs<D> make_offs(long long st1, long long st2) {
         f.o[5 % (2 * D)] = -st2;
     }
     return f;
-}
-
-// node of list position t in the concatenation (inside colour 0, inside colour
-// 1, ghosts); kind 1 inside, 2 ghost
-struct Lists {
-    const int* l0;
-    const int* l1;
-    const int* lg;
-    int n0, n1, ng;
-};
-
-__device__ __forceinline__ long long list_node(const Lists& L, int t, int& kind, int& gi) {
-    if (t < L.n0) {
-        kind = 1;
-        return L.l0[t];
-    }
-    t -= L.n0;
-    if (t < L.n1) {
-        kind = 1;
-        return L.l1[t];
-    }
-    t -= L.n1;
-    kind = 2;
-    gi = t;
-    return L.lg[t];
-}
-
-inline Lists make_lists(const LevelGeo& L, bool ghosts = true) {
-    Lists l;
-    l.l0 = L.inl[0];
-    l.l1 = L.inl[1];
-    l.lg = L.gidx;
-    l.n0 = L.nin[0];
-    l.n1 = L.nin[1];
-    l.ng = ghosts ? L.ng : 0;
-    return l;
-}
-
-// pointers of the stencil coefficients, passed by value to the kernels
-template <int D, typename T>
-struct CoefPtr {
-    typedef typename V2<T>::t T2;
-    const T2* edge[3];
-    const T2* Pa;
-    const T2* Pb;
-    const T2* Ia;
-    const T2* Ib;
-    const T2* gc;
-};
-
-template <int D, typename T>
-inline CoefPtr<D, T> coef_ptr(const LevelVec<T>& V) {
-    CoefPtr<D, T> c;
-    for (int a = 0; a < 3; a++) c.edge[a] = V.edge[a];
-    c.Pa = V.Pa;
-    c.Pb = V.Pb;
-    c.Ia = V.Ia;
-    c.Ib = V.Ib;
-    c.gc = V.gc;
-    return c;
-}
-
-// off-diagonal part of the s row of an inside node applied to x (Eq. JssI
-// and Eq. JscI as exact derivatives): sum over the axis neighbours q of
-// J^ss_pq x^s_q + J^sc_pq x^c_q with J^ss_pq = -g and J^sc_pq = +-e
-template <int D, typename T>
-__device__ __forceinline__ T offdiag_s(long long p, const CoefPtr<D, T>& cf, const typename V2<T>::t* __restrict__ x,
-                                       const long long* st) {
-    typedef typename V2<T>::t T2;
-    T acc = 0;
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        T2 ge = cf.edge[a][p];
-        T2 xe = x[p + st[a]];
-        T2 gw = cf.edge[a][p - st[a]];
-        T2 xw = x[p - st[a]];
-        acc += (ge.y * xe.y - ge.x * xe.x) - (gw.x * xw.x + gw.y * xw.y);
-    }
-    return acc;
 }
 
 // stencil coefficients of every active node from Wc: edges toward the +axis
@@ -217,71 +139,13 @@ template <int D, typename T, bool PW>
 __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
                                                       const typename V2<T>::t* __restrict__ rhs,
                                                       typename V2<T>::t* __restrict__ x, long long st1, long long st2) {
-    typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
-    long long p = list[t];
     const long long st[3] = {1, st1, st2};
-    T off = offdiag_s<D, T>(p, cf, x, st);
-    T2 b = rhs[p];
-    T2 out;
-    if (PW) {
-        // Eq. matrixPclassical: the diagonal of the 2x2 block only
-        T2 xp = x[p];
-        T2 pa = cf.Pa[p], pb = cf.Pb[p];
-        out.x = (b.x - off - pa.y * xp.y) / pa.x;
-        out.y = (b.y - pb.x * xp.x) / pb.y;
-    } else {
-        // Eq. matrixP: x_p + P^{-1} (b - J x) = P^{-1} (b - (J - P) x)
-        T2 ia = cf.Ia[p], ib = cf.Ib[p];
-        T r = b.x - off;
-        out.x = ia.x * r + ia.y * b.y;
-        out.y = ib.x * r + ib.y * b.y;
-    }
-    x[p] = out;
+    stages::relax_node<D, T, PW, false>(list[t], cf, rhs, x, st);
 }
 
-// ghost row s~(B) of ghost gi applied to the s component: sum over the upwind
-// stencil of the tensor-product weights (Eq. JssD).  Ghost members are read
-// from the previous pass's buffer (sin) unless this is the first pass.
-template <int D, typename T>
-__device__ __forceinline__ T ghost_dot(int gi, long long g, const int8_t* __restrict__ gm, const T* __restrict__ gw,
-                                       const int* __restrict__ gpos, const typename V2<T>::t* __restrict__ x,
-                                       const T* __restrict__ sin, bool from_x, long long st1, long long st2) {
-    T wa[3][3];
-    int m[3] = {1, 1, 1};
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        m[a] = gm[(long long)gi * D + a];
-#pragma unroll
-        for (int k = 0; k < 3; k++) wa[a][k] = gw[(long long)gi * 3 * D + 3 * a + k];
-    }
-    long long st[3] = {1, st1, st2};
-    const int K = D == 2 ? 9 : 27;
-    T acc = 0;
-#pragma unroll
-    for (int kk = 0; kk < K; kk++) {
-        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
-        T w = wa[0][k0] * wa[1][k1];
-        if (D == 3) w = w * wa[2][k2];
-        if (w == (T)0) continue;
-        long long node = g - m[0] * k0 * st[0] - m[1] * k1 * st[1];
-        if (D == 3) node -= m[2] * k2 * st[2];
-        T v;
-        if (from_x) {
-            v = x[node].x;
-        } else {
-            int gp = gpos[node];
-            v = gp >= 0 ? sin[gp] : x[node].x;
-        }
-        acc += w * v;
-    }
-    return acc;
-}
-
-// one Jacobi pass of the ghost relaxation of Eq. RelGhost: s_g += tau (r_g -
-// row.x) from the previous pass's values, then the ghost c row relaxed by its
-// diagonal with the fresh s_g.  Only the ghost's own thread touches its c.
+// one Jacobi pass of the ghost relaxation of Eq. RelGhost over all ghosts
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict__ gidx, const int* __restrict__ gpos,
                                                     const int8_t* __restrict__ gm, const T* __restrict__ gw,
@@ -289,23 +153,10 @@ __global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict
                                                     const typename V2<T>::t* __restrict__ rhs,
                                                     typename V2<T>::t* x, const T* sin, T* sout, long long st1,
                                                     long long st2, Coef<T> c, int first, int last) {
-    typedef typename V2<T>::t T2;
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= ng) return;
-    long long g = gidx[gi];
-    T acc = ghost_dot<D, T>(gi, g, gm, gw, gpos, x, sin, first != 0, st1, st2);
-    T2 xg = x[g];
-    T s_old = first ? xg.x : sin[gi];
-    T2 b = rhs[g];
-    T s_new = s_old + c.tau * (b.x - acc);
-    T2 q = gc[gi];  // (J^cs_gg, J^cc_gg)
-    T c_new = xg.y + (b.y - (q.x * s_new + q.y * xg.y)) / q.y;
-    T* xs = reinterpret_cast<T*>(x + g);
-    xs[1] = c_new;
-    if (last)
-        xs[0] = s_new;
-    else
-        sout[gi] = s_new;
+    stages::ghost_pass_node<D, T, false>(gi, gidx, gpos, gm, gw, gc, rhs, x, sin, sout, st1, st2, c.tau, first != 0,
+                                         last != 0);
 }
 
 template <typename T>
@@ -325,31 +176,9 @@ __global__ void __launch_bounds__(kT) k_residual(Lists ls, const int8_t* __restr
                                                   const typename V2<T>::t* __restrict__ x,
                                                   typename V2<T>::t* __restrict__ res, long long st1, long long st2,
                                                   unsigned long long* norm) {
-    typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nb = 0;
-    if (t < ls.n0 + ls.n1 + ls.ng) {
-        int kind, gi = 0;
-        long long p = list_node(ls, t, kind, gi);
-        T2 b = rhs[p];
-        T2 xp = x[p];
-        T2 r;
-        if (kind == 1) {
-            const long long st[3] = {1, st1, st2};
-            T off = offdiag_s<D, T>(p, cf, x, st);
-            T2 pa = cf.Pa[p], pb = cf.Pb[p];
-            r.x = b.x - (pa.x * xp.x + pa.y * xp.y + off);
-            r.y = b.y - (pb.x * xp.x + pb.y * xp.y);
-        } else {
-            T acc = ghost_dot<D, T>(gi, p, gm, gw, nullptr, x, nullptr, true, st1, st2);
-            T2 q = cf.gc[gi];
-            r.x = b.x - acc;
-            r.y = b.y - (q.x * xp.x + q.y * xp.y);
-        }
-        res[p] = r;
-        unsigned long long a0 = abs_bits(r.x), a1 = abs_bits(r.y);
-        nb = a0 > a1 ? a0 : a1;
-    }
+    if (t < ls.n0 + ls.n1 + ls.ng) nb = stages::residual_node<D, T, false>(t, ls, gm, gw, cf, rhs, x, res, st1, st2);
     if (norm) block_max(nb, norm);
 }
 
@@ -362,43 +191,9 @@ __global__ void k_extend_step(int nb, const int* __restrict__ bidx, const int* _
                               const T* __restrict__ ban, typename V2<T>::t* res,
                               const typename V2<T>::t* __restrict__ bin, typename V2<T>::t* __restrict__ bout, T cfl,
                               int first, int last) {
-    typedef typename V2<T>::t T2;
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
-    T2 v;
-    if (first) {
-        v.x = 0;
-        v.y = 0;
-    } else {
-        v = bin[b];
-    }
-    T ax = 0, ay = 0;
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        int ref = bref[(long long)b * D + a];
-        if (ref == -1) continue;
-        T2 u;
-        if (ref >= 0) {
-            if (first) {
-                u.x = 0;
-                u.y = 0;
-            } else {
-                u = bin[ref];
-            }
-        } else {
-            u = res[-(long long)ref - 2];
-        }
-        T an = ban[(long long)b * D + a];
-        ax += an * (v.x - u.x);
-        ay += an * (v.y - u.y);
-    }
-    T2 nv;
-    nv.x = v.x - cfl * ax;
-    nv.y = v.y - cfl * ay;
-    if (last)
-        res[bidx[b]] = nv;
-    else
-        bout[b] = nv;
+    stages::extend_node<D, T, false>(b, bidx, bref, ban, res, bin, bout, cfl, first != 0, last != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,79 +202,15 @@ __global__ void k_extend_step(int nb, const int* __restrict__ bidx, const int* _
 // ghosts; per-axis mirrored weights, invalid diagonal weight moved to the
 // centre.  Also zeroes the coarse error at the coarse active nodes.
 
-__device__ __forceinline__ bool valid_for(int8_t rule, int8_t t) {
-    return rule == T_IN ? t == T_IN : (t == T_GHOST || t == T_BAND);
-}
-
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restrict__ ctype, int cn,
                                                   const int8_t* __restrict__ ftype, int fn,
                                                   const typename V2<T>::t* __restrict__ fres,
                                                   typename V2<T>::t* __restrict__ crhs,
                                                   typename V2<T>::t* __restrict__ cx) {
-    typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
-    int kind, gi;
-    long long I = list_node(ls, t, kind, gi);
-    int8_t rule = ctype[I];
-    int ii[3] = {0, 0, 0};
-    ii[0] = (int)(I % cn);
-    ii[1] = (int)((I / cn) % cn);
-    if (D == 3) ii[2] = (int)(I / ((long long)cn * cn));
-    long long fst[3] = {1, fn, (long long)fn * fn};
-    long long f = 0;
-#pragma unroll
-    for (int a = 0; a < D; a++) f += 2LL * ii[a] * fst[a];
-    T w1[3][3];
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        bool vl = ii[a] > 0 && valid_for(rule, ftype[f - fst[a]]);
-        bool vr = 2 * ii[a] < fn - 1 && valid_for(rule, ftype[f + fst[a]]);
-        T l = 1, m = 2, r = 1;
-        if (vl && !vr) {
-            l = 2; m = 2; r = 0;
-        } else if (!vl && vr) {
-            l = 0; m = 2; r = 2;
-        } else if (!vl && !vr) {
-            l = 0; m = 4; r = 0;
-        }
-        w1[a][0] = l / (T)4;
-        w1[a][1] = m / (T)4;
-        w1[a][2] = r / (T)4;
-    }
-    const int K = D == 2 ? 9 : 27;
-    T as = 0, ac = 0, wc = 0;
-#pragma unroll
-    for (int kk = 0; kk < K; kk++) {
-        const int k0 = kk % 3 - 1, k1 = (kk / 3) % 3 - 1, k2 = kk / 9 - 1;
-        T w = w1[0][k0 + 1] * w1[1][k1 + 1];
-        if (D == 3) w = w * w1[2][k2 + 1];
-        if (w == (T)0) continue;
-        bool centre = k0 == 0 && k1 == 0 && (D == 2 || k2 == 0);
-        if (centre) {
-            wc += w;
-            continue;
-        }
-        long long node = f + k0 * fst[0] + k1 * fst[1];
-        if (D == 3) node += k2 * fst[2];
-        if (!valid_for(rule, ftype[node])) {
-            wc += w;
-            continue;
-        }
-        T2 v = fres[node];
-        as += w * v.x;
-        ac += w * v.y;
-    }
-    T2 vc = fres[f];
-    T2 out;
-    out.x = as + wc * vc.x;
-    out.y = ac + wc * vc.y;
-    crhs[I] = out;
-    T2 z;
-    z.x = 0;
-    z.y = 0;
-    cx[I] = z;  // the coarse-grid error starts from zero
+    stages::restrict_node<D, T, false>(t, ls, ctype, cn, ftype, fn, fres, crhs, cx);
 }
 
 // (bi/tri)linear interpolation of the coarse error to every fine active node,
@@ -488,49 +219,9 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_prolong(Lists ls, const int8_t* __restrict__ ctype, int cn,
                                                  const typename V2<T>::t* __restrict__ cx, int fn,
                                                  typename V2<T>::t* __restrict__ fx) {
-    typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
-    int kind, gi;
-    long long i = list_node(ls, t, kind, gi);
-    int ii[3] = {0, 0, 0};
-    ii[0] = (int)(i % fn);
-    ii[1] = (int)((i / fn) % fn);
-    if (D == 3) ii[2] = (int)(i / ((long long)fn * fn));
-    long long cst[3] = {1, cn, (long long)cn * cn};
-    T ws = 0, as = 0, ac = 0;
-    const int NC = 1 << D;
-#pragma unroll
-    for (int cc = 0; cc < NC; cc++) {
-        long long node = 0;
-        T w = 1;
-        bool dup = false;
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            int pick = (cc >> a) & 1;
-            int lo = ii[a] >> 1, hi = (ii[a] + 1) >> 1;
-            if (lo == hi) {
-                if (pick) dup = true;
-                node += lo * cst[a];
-            } else {
-                w *= (T)0.5;
-                node += (pick ? hi : lo) * cst[a];
-            }
-        }
-        if (dup) continue;
-        int8_t tc = ctype[node];
-        if (tc != T_IN && tc != T_GHOST) continue;
-        T2 v = cx[node];
-        ws += w;
-        as += w * v.x;
-        ac += w * v.y;
-    }
-    if (ws > (T)0) {
-        T2 xf = fx[i];
-        xf.x += as / ws;
-        xf.y += ac / ws;
-        fx[i] = xf;
-    }
+    stages::prolong_node<D, T, false>(t, ls, ctype, cn, cx, fn, fx);
 }
 
 // coarse Jacobian coefficients by injection of (s, c); a coarse ghost whose
@@ -584,8 +275,9 @@ __global__ void __launch_bounds__(kT) k_inject(Lists ls, int cn, const int8_t* _
 }
 
 // ---------------------------------------------------------------------------
-// coarsest level: assemble the Jacobian, factor it with partial pivoting and
-// form its inverse (one CTA); each cycle then applies the inverse
+// coarsest level: assemble the Jacobian and invert it by Gauss-Jordan
+// elimination with partial pivoting (one CTA, once per Newton iteration); each
+// cycle then applies the inverse
 
 template <int D, typename T, bool SMEM>
 __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* __restrict__ act,
@@ -597,15 +289,13 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
                                                           int* singular) {
     typedef typename V2<T>::t T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red_v[32];
-    __shared__ int red_i[32];
     const int m = 2 * nact;
     const long long mm = (long long)m * m;
     // with SMEM the work matrix and the inverse live in shared memory (small
     // coarsest levels) and the inverse is copied out at the end
     T* A = SMEM ? reinterpret_cast<T*>(smem_raw) : Ag;
     T* Ainv = SMEM ? A + mm : Ainv_g;
-    int* piv = reinterpret_cast<int*>(smem_raw + (SMEM ? 2 * mm * sizeof(T) : 0));
+    int* piv = reinterpret_cast<int*>(smem_raw + (SMEM ? 2 * mm * sizeof(T) : 0));  // scratch of m T values
     for (long long i = threadIdx.x; i < mm; i += blockDim.x) A[i] = 0;
     __syncthreads();
     for (int r = threadIdx.x; r < nact; r += blockDim.x) {
@@ -653,85 +343,73 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
         rc[2 * r + 1] += c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
     }
     __syncthreads();
-    // LU with partial pivoting (row swaps), multipliers stored below the diagonal
-    for (int k = 0; k < m; k++) {
-        T bv = -1;
-        int bi = k;
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-            T v = fabs(A[(long long)i * m + k]);
-            if (v > bv) {
-                bv = v;
-                bi = i;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            T ov = __shfl_down_sync(0xffffffffu, bv, o);
-            int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) {
-                bv = ov;
-                bi = oi;
-            }
-        }
-        int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) {
-            red_v[warp] = bv;
-            red_i[warp] = bi;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int nw = (blockDim.x + 31) >> 5;
-            T v0 = red_v[0];
-            int i0 = red_i[0];
-            for (int w = 1; w < nw; w++)
-                if (red_v[w] > v0 || (red_v[w] == v0 && red_i[w] < i0)) {
-                    v0 = red_v[w];
-                    i0 = red_i[w];
-                }
-            piv[k] = i0;
-            if (!(v0 > (T)0)) *singular = 1;
-        }
-        __syncthreads();
-        int pr = piv[k];
-        if (pr != k)
-            for (int j = threadIdx.x; j < m; j += blockDim.x) {
-                T tmp = A[(long long)k * m + j];
-                A[(long long)k * m + j] = A[(long long)pr * m + j];
-                A[(long long)pr * m + j] = tmp;
-            }
-        __syncthreads();
-        T dk = A[(long long)k * m + k];
-        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[(long long)i * m + k] /= dk;
-        __syncthreads();
-        long long rem = (long long)(m - k - 1) * (m - k - 1);
-        for (long long e = threadIdx.x; e < rem; e += blockDim.x) {
-            int i = k + 1 + (int)(e / (m - k - 1));
-            int j = k + 1 + (int)(e % (m - k - 1));
-            A[(long long)i * m + j] -= A[(long long)i * m + k] * A[(long long)k * m + j];
-        }
-        __syncthreads();
+    // Gauss-Jordan elimination with partial pivoting on [A | I]: the same pivot
+    // sequence as an LU with partial pivoting (first row of largest |a_ik|,
+    // i >= k), leaving the inverse in Ainv
+    for (long long i = threadIdx.x; i < mm; i += blockDim.x) {
+        int r = (int)(i / m), q = (int)(i % m);
+        Ainv[i] = r == q ? (T)1 : (T)0;
     }
-    // inverse, one column per thread: apply the row swaps to e_j, then solve
-    // L y = P e_j and U x = y; Ainv is stored row-major
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        for (int i = 0; i < m; i++) Ainv[(long long)i * m + j] = (i == j) ? (T)1 : (T)0;
-        for (int k = 0; k < m; k++) {
-            int pr = piv[k];
-            if (pr != k) {
-                T tmp = Ainv[(long long)k * m + j];
-                Ainv[(long long)k * m + j] = Ainv[(long long)pr * m + j];
-                Ainv[(long long)pr * m + j] = tmp;
+    T* fac = reinterpret_cast<T*>(piv);  // column factors of the current step (m values)
+    __shared__ int s_piv;
+    __syncthreads();
+    for (int k = 0; k < m; k++) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            T bv = -1;
+            int bi = k;
+            for (int i = k + lane; i < m; i += 32) {
+                T v = fabs(A[(long long)i * m + k]);
+                if (v > bv) {
+                    bv = v;
+                    bi = i;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                T ov = __shfl_down_sync(0xffffffffu, bv, o);
+                int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                s_piv = bi;
+                if (!(bv > (T)0)) *singular = 1;
             }
         }
-        for (int i = 1; i < m; i++) {
-            T acc = Ainv[(long long)i * m + j];
-            for (int k = 0; k < i; k++) acc -= A[(long long)i * m + k] * Ainv[(long long)k * m + j];
-            Ainv[(long long)i * m + j] = acc;
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != k)
+            for (int j = threadIdx.x; j < 2 * m; j += blockDim.x) {
+                T* M = j < m ? A : Ainv;
+                int q = j < m ? j : j - m;
+                T tmp = M[(long long)k * m + q];
+                M[(long long)k * m + q] = M[(long long)pr * m + q];
+                M[(long long)pr * m + q] = tmp;
+            }
+        __syncthreads();
+        const T inv = (T)1 / A[(long long)k * m + k];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) fac[i] = A[(long long)i * m + k];
+        __syncthreads();
+        for (int j = threadIdx.x; j < 2 * m; j += blockDim.x) {
+            T* M = j < m ? A : Ainv;
+            int q = j < m ? j : j - m;
+            M[(long long)k * m + q] *= inv;
         }
-        for (int i = m - 1; i >= 0; i--) {
-            T acc = Ainv[(long long)i * m + j];
-            for (int k = i + 1; k < m; k++) acc -= A[(long long)i * m + k] * Ainv[(long long)k * m + j];
-            Ainv[(long long)i * m + j] = acc / A[(long long)i * m + i];
+        __syncthreads();
+        const long long work = (long long)m * 2 * m;
+        for (long long e = threadIdx.x; e < work; e += blockDim.x) {
+            int i = (int)(e / (2 * m));
+            int j = (int)(e % (2 * m));
+            if (i == k) continue;
+            T f = fac[i];
+            if (f == (T)0) continue;
+            T* M = j < m ? A : Ainv;
+            int q = j < m ? j : j - m;
+            M[(long long)i * m + q] -= f * M[(long long)k * m + q];
         }
+        __syncthreads();
     }
     if (SMEM) {
         __syncthreads();
@@ -833,7 +511,7 @@ __global__ void __launch_bounds__(kT) k_newton_F(Lists ls, const int8_t* __restr
             double Ls = Ls_h<D>(p, W, of, f, phd);
             out.x = ph * w.x * f.idt - 0.5 * Ls + g.x;
         } else {
-            out.x = ghost_dot<D, double>(gi, p, gm, gw, nullptr, W, nullptr, true, st1, st2) - f.sb;
+            out.x = stages::ghost_dot<D, double, false>(gi, p, gm, gw, nullptr, W, nullptr, true, st1, st2) - f.sb;
         }
         F[p] = out;
         unsigned long long a0 = abs_bits(out.x), a1 = abs_bits(out.y);
@@ -1039,7 +717,7 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
     const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
     Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
     const size_t m = 2 * (size_t)L.nact;
-    const size_t piv_bytes = sizeof(int) * (m + 1);
+    const size_t piv_bytes = sizeof(T) * (m + 1);
     const size_t smem_full = 2 * m * m * sizeof(T) + piv_bytes;
     if (smem_full <= 220 * 1024) {
         auto kern = k_coarsest_factor<D, T, true>;

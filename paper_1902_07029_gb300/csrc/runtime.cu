@@ -1,0 +1,370 @@
+// Batching and serving runtime of the sulfmg library.
+//
+// Batch: many independent domains (uneven sizes) advanced together.  Each of
+// nstreams host workers owns a CUDA stream and takes the next instance (largest
+// work first); an instance's multigrid cycles are its own captured CUDA graphs,
+// so the GPU runs the kernels of several instances at once while each worker
+// waits on its instance's convergence tests.
+//
+// Server: jobs (a level set, a model, a number of CN steps) are submitted at any
+// time and admitted first-come-first-served among those whose device-memory
+// estimate fits in what the budget has left; admitted jobs run on the worker
+// streams as soon as a worker and memory are free (continuous batching), and
+// their memory returns to the budget when they finish.  Latency is measured
+// from submission to the moment the result is ready.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/sulfmg.h"
+#include "sulf_internal.cuh"
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// device-memory estimate of a domain (admission control)
+
+extern "C" unsigned long long sulf_estimate_device_bytes(int dim, int N, int coarsest_N, int precision) {
+    if ((dim != 2 && dim != 3) || N < 2 || coarsest_N < 2) return 0;
+    double nn0 = 1;
+    for (int a = 0; a < dim; a++) nn0 *= (double)(N + 1);
+    // bytes per box node: FP64 level vectors (Wc, rhs, x, res 64; edges 16 dim;
+    // 2x2 blocks and inverses 64), geometry (phi, type, maps, lists, marks ~30),
+    // the finest level's W^n, old-time part and staging (49); FP32 vectors
+    // (32 + 8 dim + 32) when mixed; coarser levels add 1/(2^dim - 1)
+    double per_level = 128.0 + 16.0 * dim + 30.0;
+    if (precision == 1) per_level += 64.0 + 8.0 * dim;
+    double geo = 1.0 / (1.0 - 1.0 / (double)(1 << dim));
+    double bytes = nn0 * (per_level * geo + 49.0);
+    // ghost and band arrays, allocation granularity, coarsest dense matrices
+    double nc = 1;
+    for (int a = 0; a < dim; a++) nc *= (double)(coarsest_N + 1);
+    double m = 2.0 * nc;
+    bytes += 2.0 * m * m * 8.0 * (precision == 1 ? 1.5 : 1.0);
+    bytes = bytes * 1.15 + 8.0 * 1024 * 1024;
+    return (unsigned long long)bytes;
+}
+
+// ---------------------------------------------------------------------------
+// batch
+
+struct sulf_batch_s {
+    std::vector<sulf_handle> h;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> status;
+    std::vector<std::string> errors;
+    int device = 0;
+};
+
+extern "C" int sulf_batch_create(const sulf_handle* handles, int n, int nstreams, sulf_batch* out) {
+    if (!out) return sulf_fail(SULF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!handles || n < 1 || nstreams < 1) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    for (int i = 0; i < n; i++)
+        if (!handles[i]) return sulf_fail(SULF_EINVAL, "NULL handle in batch");
+    sulf_batch b = new sulf_batch_s();
+    b->h.assign(handles, handles + n);
+    b->status.assign(n, SULF_OK);
+    b->errors.assign(n, std::string());
+    cudaGetDevice(&b->device);
+    int ns = std::min(nstreams, n);
+    for (int k = 0; k < ns; k++) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            sulf_batch_destroy(b);
+            return sulf_fail(SULF_EDEVICE, "cannot create a CUDA stream");
+        }
+        b->streams.push_back(s);
+    }
+    *out = b;
+    return SULF_OK;
+}
+
+extern "C" int sulf_batch_step(sulf_batch b, const double* dt, const int* nsteps) {
+    if (!b || !dt || !nsteps) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const int n = (int)b->h.size();
+    // largest work first: active nodes times steps
+    std::vector<int> order(n);
+    std::vector<double> work(n);
+    for (int i = 0; i < n; i++) {
+        sulf_stats st;
+        sulf_get_stats(b->h[i], &st);
+        work[i] = (double)(st.n_inside + st.n_ghost) * nsteps[i];
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::atomic<int> next(0);
+    auto worker = [&](int k) {
+        cudaSetDevice(b->device);
+        for (;;) {
+            int j = next.fetch_add(1);
+            if (j >= n) break;
+            int i = order[j];
+            int rc = sulf_set_stream(b->h[i], b->streams[k]);
+            if (rc == SULF_OK) rc = sulf_step(b->h[i], dt[i], nsteps[i]);
+            b->status[i] = rc;
+            b->errors[i] = rc ? sulf_last_error() : "";
+        }
+    };
+    std::vector<std::thread> th;
+    for (int k = 0; k < (int)b->streams.size(); k++) th.emplace_back(worker, k);
+    for (auto& t : th) t.join();
+    for (int i = 0; i < n; i++)
+        if (b->status[i] != SULF_OK) return sulf_fail(b->status[i], "batch instance " + std::to_string(i) + ": " + b->errors[i]);
+    return SULF_OK;
+}
+
+extern "C" int sulf_batch_status(sulf_batch b, int* status) {
+    if (!b || !status) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    for (size_t i = 0; i < b->status.size(); i++) status[i] = b->status[i];
+    return SULF_OK;
+}
+
+extern "C" void sulf_batch_destroy(sulf_batch b) {
+    if (!b) return;
+    for (sulf_handle h : b->h) sulf_set_stream(h, nullptr);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    delete b;
+}
+
+// ---------------------------------------------------------------------------
+// server
+
+namespace {
+
+struct Job {
+    long long id = 0;
+    sulf_job spec{};
+    std::vector<double> phi;
+    unsigned long long est = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int status = SULF_OK;
+    std::string err;
+    std::vector<double> s, c;
+    sulf_stats stats{};
+    unsigned long long bytes = 0;
+    bool done = false;
+};
+
+}  // namespace
+
+struct sulf_server_s {
+    unsigned long long budget = 0, reserved = 0, peak = 0;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Job*> queue;
+    std::unordered_map<long long, Job*> jobs;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    bool stopping = false;
+    long long next_id = 1, completed = 0, failed = 0, running = 0, max_running = 0;
+    std::vector<double> latencies;
+    double t_create = 0, t_last_done = 0;
+};
+
+namespace {
+
+void run_job(Job* j, cudaStream_t stream) {
+    const sulf_job& p = j->spec;
+    double box[2] = {p.box_lo, p.box_hi};
+    sulf_handle h = nullptr;
+    int rc = sulf_create_domain(j->phi.data(), p.dim, box, p.N, p.coarsest_N, &h);
+    if (rc == SULF_OK) rc = sulf_set_stream(h, stream);
+    if (rc == SULF_OK) rc = sulf_set_model(h, &p.model);
+    if (rc == SULF_OK) rc = sulf_set_solver(h, &p.solver);
+    if (rc == SULF_OK) rc = sulf_step(h, p.dt, p.nsteps);
+    if (rc == SULF_OK) {
+        size_t nn = j->phi.size();
+        j->s.resize(nn);
+        j->c.resize(nn);
+        rc = sulf_get_state(h, j->s.data(), j->c.data(), nullptr);
+    }
+    if (h) sulf_get_stats(h, &j->stats);
+    j->status = rc;
+    if (rc) j->err = sulf_last_error();
+    if (h) {
+        sulf_set_stream(h, nullptr);
+        sulf_destroy(h);
+    }
+}
+
+void server_worker(sulf_server s, int k) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        Job* pick = nullptr;
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+            if (s->reserved + (*it)->est <= s->budget) {
+                pick = *it;
+                s->queue.erase(it);
+                break;
+            }
+        if (!pick) {
+            if (s->stopping && s->queue.empty()) return;
+            s->cv_work.wait(lk);
+            continue;
+        }
+        s->reserved += pick->est;
+        s->peak = std::max(s->peak, s->reserved);
+        s->running++;
+        s->max_running = std::max(s->max_running, s->running);
+        pick->t_start = now_ms();
+        lk.unlock();
+        run_job(pick, s->streams[k]);
+        lk.lock();
+        s->reserved -= pick->est;
+        s->running--;
+        pick->t_done = now_ms();
+        s->t_last_done = pick->t_done;
+        pick->done = true;
+        if (pick->status == SULF_OK) {
+            s->completed++;
+            s->latencies.push_back(pick->t_done - pick->t_submit);
+        } else {
+            s->failed++;
+        }
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+}
+
+double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0;
+    std::sort(v.begin(), v.end());
+    double pos = q * (v.size() - 1);
+    size_t lo = (size_t)pos, hi = std::min(lo + 1, v.size() - 1);
+    return v[lo] + (pos - lo) * (v[hi] - v[lo]);
+}
+
+}  // namespace
+
+extern "C" int sulf_server_create(unsigned long long budget_bytes, int nworkers, sulf_server* out) {
+    if (!out) return sulf_fail(SULF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (budget_bytes == 0 || nworkers < 1) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    sulf_server s = new sulf_server_s();
+    s->budget = budget_bytes;
+    cudaGetDevice(&s->device);
+    for (int k = 0; k < nworkers; k++) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t t : s->streams) cudaStreamDestroy(t);
+            delete s;
+            return sulf_fail(SULF_EDEVICE, "cannot create a CUDA stream");
+        }
+        s->streams.push_back(st);
+    }
+    s->t_create = now_ms();
+    for (int k = 0; k < nworkers; k++) s->workers.emplace_back(server_worker, s, k);
+    *out = s;
+    return SULF_OK;
+}
+
+extern "C" int sulf_server_submit(sulf_server s, const sulf_job* job, long long* id) {
+    if (!s || !job || !id || !job->levelset || (job->dim != 2 && job->dim != 3) || job->N < 2 || job->nsteps < 0 ||
+        !(job->dt > 0))
+        return sulf_fail(SULF_EINVAL, "invalid job");
+    Job* j = new Job();
+    j->spec = *job;
+    size_t nn = 1;
+    for (int a = 0; a < job->dim; a++) nn *= (size_t)(job->N + 1);
+    j->phi.assign(job->levelset, job->levelset + nn);
+    j->spec.levelset = nullptr;
+    j->est = sulf_estimate_device_bytes(job->dim, job->N, job->coarsest_N, job->solver.precision);
+    if (j->est > s->budget) {
+        delete j;
+        return sulf_fail(SULF_ENOMEM, "job needs more device memory than the whole budget");
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    j->id = s->next_id++;
+    j->t_submit = now_ms();
+    s->jobs[j->id] = j;
+    s->queue.push_back(j);
+    *id = j->id;
+    s->cv_work.notify_one();
+    return SULF_OK;
+}
+
+extern "C" int sulf_server_poll(sulf_server s, long long id, int* done) {
+    if (!s || !done) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end()) return sulf_fail(SULF_EINVAL, "unknown job id");
+    *done = it->second->done ? 1 : 0;
+    return SULF_OK;
+}
+
+extern "C" int sulf_server_wait(sulf_server s, long long id, double* s_out, double* c_out, sulf_job_result* res) {
+    if (!s) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end()) return sulf_fail(SULF_EINVAL, "unknown job id");
+    Job* j = it->second;
+    s->cv_done.wait(lk, [&] { return j->done; });
+    s->jobs.erase(it);
+    lk.unlock();
+    if (res) {
+        res->status = j->status;
+        res->latency_ms = j->t_done - j->t_submit;
+        res->queue_ms = j->t_start - j->t_submit;
+        res->run_ms = j->t_done - j->t_start;
+        res->estimate_bytes = j->est;
+        res->device_bytes = j->stats.device_bytes;
+        res->newton = j->stats.newton_total;
+        res->cycles = j->stats.cycles_total;
+    }
+    int rc = j->status;
+    if (rc == SULF_OK) {
+        if (s_out) std::copy(j->s.begin(), j->s.end(), s_out);
+        if (c_out) std::copy(j->c.begin(), j->c.end(), c_out);
+    }
+    std::string err = j->err;
+    delete j;
+    if (rc) return sulf_fail(rc, err);
+    return SULF_OK;
+}
+
+extern "C" int sulf_server_get_stats(sulf_server s, sulf_server_stats* out) {
+    if (!s || !out) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->completed = s->completed;
+    out->failed = s->failed;
+    out->queued = (long long)s->queue.size();
+    out->running = s->running;
+    out->max_running = s->max_running;
+    out->p50_ms = percentile(s->latencies, 0.50);
+    out->p99_ms = percentile(s->latencies, 0.99);
+    out->budget_bytes = s->budget;
+    out->peak_reserved_bytes = s->peak;
+    double span = (s->t_last_done - s->t_create) / 1e3;
+    out->jobs_per_s = span > 0 ? s->completed / span : 0;
+    return SULF_OK;
+}
+
+extern "C" void sulf_server_destroy(sulf_server s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    for (auto& kv : s->jobs) delete kv.second;
+    for (cudaStream_t t : s->streams) cudaStreamDestroy(t);
+    delete s;
+}

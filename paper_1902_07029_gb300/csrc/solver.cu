@@ -27,18 +27,41 @@ int sulf_fail_cuda(cudaError_t e, const char* what) {
 
 namespace sulf {
 
+namespace {
+// keep freed blocks in the device pool instead of returning them at each
+// synchronisation (set once per device)
+void retain_pool_memory() {
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+}  // namespace
+
 void* DevMem::get(size_t n) {
     void* p = nullptr;
     size_t sz = (n + 255) & ~size_t(255);
     if (sz == 0) sz = 256;
-    if (cudaMalloc(&p, sz) != cudaSuccess) return nullptr;
+    retain_pool_memory();
+    if (cudaMallocAsync(&p, sz, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    // set-up only: make the block usable from any stream right away
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return nullptr;
     ptrs.push_back(p);
     bytes += sz;
     return p;
 }
 
 void DevMem::release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, stream);
+    if (stream) cudaStreamSynchronize(stream);
     ptrs.clear();
     bytes = 0;
 }
@@ -87,6 +110,9 @@ struct sulf_domain {
         size_t ev0 = 0, ev1 = 0;
     } graph[2];
     bool capturing = false;
+    // fused coarsest levels: device descriptors per precision
+    void* tail_desc[2] = {nullptr, nullptr};
+    bool tail_ready[2] = {false, false};
 };
 
 namespace {
@@ -105,6 +131,7 @@ sulf_solver default_solver() {
     s.precision = 0;
     s.smoother = 0;
     s.graphs = 1;
+    s.fuse_below = 1500;
     return s;
 }
 
@@ -222,6 +249,30 @@ int read_norms(sulf_domain* d, int n) {
     return SULF_OK;
 }
 
+// first level handled by the fused coarse-level cycle (-1: none)
+int tail_level(const sulf_domain* d) {
+    if (d->solver.fuse_below <= 0 || d->solver.cycle != 1) return -1;
+    for (int l = 0; l < d->L - 1; l++)
+        if ((long long)d->geo[l].nin[0] + d->geo[l].nin[1] + d->geo[l].ng <= d->solver.fuse_below) return l;
+    return -1;
+}
+
+// device descriptors of the levels for the fused cycle (pointers are fixed once
+// the vectors exist); must run outside stream capture
+template <int D, typename T>
+int ensure_tail(sulf_domain* d, const LevelVec<T>* V) {
+    int p = std::is_same<T, float>::value ? 1 : 0;
+    if (d->tail_ready[p]) return SULF_OK;
+    if (!d->tail_desc[p]) {
+        d->tail_desc[p] = d->mem.get(tail_desc_bytes(d->L));
+        if (!d->tail_desc[p]) return sulf_fail(SULF_ENOMEM, "out of device memory");
+    }
+    int rc = upload_tail_desc<T>(d->geo, V, d->L, d->tail_desc[p], d->stream);
+    if (rc) return rc;
+    d->tail_ready[p] = true;
+    return SULF_OK;
+}
+
 // ---- multigrid on precision T ----
 template <int D, typename T>
 struct MG {
@@ -252,19 +303,32 @@ struct MG {
         return SULF_OK;
     }
 
-    void cycle(int l) {
+    int cycle(int l) {
         if (l == d->L - 1) {
             d->launches += launch_coarsest_solve<D, T>(d->geo[l], V[l], d->stream);
-            return;
+            return SULF_OK;
         }
-        for (int k = 0; k < d->solver.nu1; k++) relax(l);
+        int p = std::is_same<T, float>::value ? 1 : 0;
+        int rc;
+        if (l == tail_level(d) && d->tail_ready[p] && d->solver.cycle == 1) {
+            // this level and all coarser ones in one single-CTA launch
+            rc = launch_tail<D, T>(d->tail_desc[p], l, d->L, d->solver, d->stream);
+            if (rc) return rc;
+            d->launches += 1;
+            return SULF_OK;
+        }
+        for (int k = 0; k < d->solver.nu1; k++)
+            if ((rc = relax(l))) return rc;
         d->launches += launch_residual<D, T>(d->geo[l], V[l], make_coef<T>(d, l), nullptr, d->stream);
         d->launches += launch_extend<D, T>(d->geo[l], V[l], 4, d->stream);
         d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
         int gam = d->solver.cycle == 2 ? 2 : 1;
-        for (int g = 0; g < gam; g++) cycle(l + 1);
+        for (int g = 0; g < gam; g++)
+            if ((rc = cycle(l + 1))) return rc;
         d->launches += launch_prolong<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
-        for (int k = 0; k < d->solver.nu2; k++) relax(l);
+        for (int k = 0; k < d->solver.nu2; k++)
+            if ((rc = relax(l))) return rc;
+        return SULF_OK;
     }
 
     // coarse coefficients from V[0].Wc, the stencil coefficients of every
@@ -303,15 +367,15 @@ int cycle_body(sulf_domain* d) {
     if (d->solver.precision == 0) {
         if (d->L == 1)
             d->launches += launch_coarsest_solve<D, double>(G0, V0, d->stream);
-        else
-            MG<D, double>{d, d->v64}.cycle(0);
+        else if (int rc = MG<D, double>{d, d->v64}.cycle(0))
+            return rc;
     } else {
         LevelVec<float>& U0 = d->v32[0];
         SULF_CUDA_TRY(cudaMemsetAsync(U0.x, 0, sizeof(float2) * G0.nn, d->stream));
         if (d->L == 1)
             d->launches += launch_coarsest_solve<D, float>(G0, U0, d->stream);
-        else
-            MG<D, float>{d, d->v32}.cycle(0);
+        else if (int rc = MG<D, float>{d, d->v32}.cycle(0))
+            return rc;
         d->launches += launch_accumulate(G0, V0.x, U0.x, d->stream);
     }
     SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
@@ -383,9 +447,13 @@ int linear_solve(sulf_domain* d, double fnorm, int max_cycles, double rtol, doub
     SULF_CUDA_TRY(cudaMemsetAsync(d->v64[0].x, 0, sizeof(double2) * G0.nn, d->stream));
     int rc;
     if (d->solver.precision == 0) {
+        rc = ensure_tail<D, double>(d, d->v64);
+        if (rc) return rc;
         rc = MG<D, double>{d, d->v64}.prepare();
     } else {
         rc = ensure32(d);
+        if (rc) return rc;
+        rc = ensure_tail<D, float>(d, d->v32);
         if (rc) return rc;
         d->launches += launch_to_float(G0, d->W, d->v32[0].Wc, d->stream);
         // the FP64 defect of the outer iteration needs the FP64 finest-level coefficients
@@ -524,6 +592,7 @@ int sulf_create_domain(const double* levelset, int dim, const double* box, int N
         return sulf_fail(SULF_EDEVICE, "cannot create a CUDA stream");
     }
     d->stream = d->own_stream;
+    d->mem.stream = d->own_stream;
     std::string err;
     int rc = SULF_OK;
     for (int l = 0; l < nl && rc == SULF_OK; l++) {
@@ -599,7 +668,7 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
     sulf_solver v = s ? *s : default_solver();
     if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || (v.cycle != 1 && v.cycle != 2) || v.max_newton < 1 ||
         v.max_cycles < 1 || v.ghost_sweeps < 1 || !(v.tau_s > 0 && v.tau_s < 1) || !(v.newton_tol > 0) ||
-        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1))
+        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1) || v.fuse_below < 0)
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
     if (v.precision == 1) return ensure32(h);
@@ -677,6 +746,7 @@ int sulf_get_stats(sulf_handle h, sulf_stats* o) {
     o->n_inside = h->geo[0].nin[0] + (long long)h->geo[0].nin[1];
     o->n_ghost = h->geo[0].ng;
     for (int k = 0; k < 3; k++) o->ghost_rows[k] = h->geo[0].kinds[k];
+    o->device_bytes = h->mem.bytes;
     return SULF_OK;
 }
 

@@ -108,10 +108,13 @@ struct FConst {
     double sb;                     // Dirichlet value
 };
 
-// Device memory owned by one handle.
+// Device memory owned by one handle, from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync on the handle's stream), so creating and
+// destroying domains does not synchronise the work of other streams.
 struct DevMem {
     std::vector<void*> ptrs;
     size_t bytes = 0;
+    cudaStream_t stream = nullptr;
     void* get(size_t n);
     void release();
 };
@@ -165,6 +168,13 @@ int launch_accumulate(const LevelGeo& L, double2* x, const float2* e, cudaStream
 int launch_reset_state(const LevelGeo& L, double2* W, double s0, double c0, cudaStream_t s);
 int launch_import_state(const LevelGeo& L, double2* W, const double* sv, const double* cv, cudaStream_t s);
 int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double* cv, int8_t* tv, cudaStream_t s);
+
+// fused coarsest levels of the V-cycle, one CTA (tail.cu)
+size_t tail_desc_bytes(int L);
+template <typename T>
+int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, cudaStream_t s);
+template <int D, typename T>
+int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, cudaStream_t s);
 
 // read-only views of a handle (solver.cu)
 const LevelGeo* handle_fine_geo(sulf_handle h);

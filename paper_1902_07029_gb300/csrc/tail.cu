@@ -1,0 +1,240 @@
+// The coarsest levels of a multigrid V-cycle (arXiv:1902.07029, Sec. 3.5) as
+// one kernel launch.
+//
+// On the smallest levels (a few hundred to a few thousand active nodes) every
+// phase -- two colours, the ghost passes, residual, band extension,
+// restriction, prolongation -- is a chain of dependent loads over a handful of
+// nodes: as separate graph nodes each costs a few microseconds of launch and
+// latency, ~31 per level and cycle.  Here one CTA walks the levels l0 .. L-1
+// down and back up with __syncthreads between phases, on L1-resident data.
+// Each phase calls the same per-node stage functions as the per-level kernels
+// (mg_stages.cuh), in the same order, so the result is the same.
+#include "mg_stages.cuh"
+
+namespace sulf {
+
+namespace {
+
+constexpr int kTailThreads = 512;
+
+using stages::Lists;
+
+// one level as seen by the fused cycle
+template <typename T>
+struct TailLevel {
+    typedef typename V2<T>::t T2;
+    Lists ls;
+    int n;
+    long long st1, st2;
+    const int8_t* type;
+    const int* gpos;
+    const int8_t* gm;
+    const T* gw;
+    int nb;
+    const int* bidx;
+    const int* bref;
+    const T* ban;
+    int nact;
+    const int* act;
+    const T* Ainv;
+    T2* rhs;
+    T2* x;
+    T2* res;
+    T* gbuf[2];
+    T2* bbuf[2];
+    const T2* edge[3];
+    const T2* Pa;
+    const T2* Pb;
+    const T2* Ia;
+    const T2* Ib;
+    const T2* gc;
+};
+
+struct TailParams {
+    int l0, L, nu1, nu2, passes, ext, pointwise;
+    double tau, cfl;
+};
+
+template <int D, typename T>
+__device__ __forceinline__ stages::CoefPtr<D, T> coefs_of(const TailLevel<T>& v) {
+    stages::CoefPtr<D, T> c;
+    for (int a = 0; a < 3; a++) c.edge[a] = v.edge[a];
+    c.Pa = v.Pa;
+    c.Pb = v.Pb;
+    c.Ia = v.Ia;
+    c.Ib = v.Ib;
+    c.gc = v.gc;
+    return c;
+}
+
+// one relaxation sweep of Sec. 3.5.1 on level v: red, black, ghost passes
+template <int D, typename T>
+__device__ void tail_relax(const TailLevel<T>& v, const TailParams& pr, int tid, int nthr) {
+    const long long st[3] = {1, v.st1, v.st2};
+    stages::CoefPtr<D, T> cf = coefs_of<D, T>(v);
+    for (int colour = 0; colour < 2; colour++) {
+        const int* list = colour ? v.ls.l1 : v.ls.l0;
+        int cnt = colour ? v.ls.n1 : v.ls.n0;
+        for (int t = tid; t < cnt; t += nthr) {
+            if (pr.pointwise)
+                stages::relax_node<D, T, true, false>(list[t], cf, v.rhs, v.x, st);
+            else
+                stages::relax_node<D, T, false, false>(list[t], cf, v.rhs, v.x, st);
+        }
+        __syncthreads();
+    }
+    for (int p = 0; p < pr.passes; p++) {
+        bool first = p == 0, last = p == pr.passes - 1 && pr.passes > 1;
+        const T* sin = first ? nullptr : v.gbuf[(p - 1) & 1];
+        T* sout = v.gbuf[p & 1];
+        for (int gi = tid; gi < v.ls.ng; gi += nthr)
+            stages::ghost_pass_node<D, T, false>(gi, v.ls.lg, v.gpos, v.gm, v.gw, v.gc, v.rhs, v.x, sin, sout, v.st1,
+                                                v.st2, (T)pr.tau, first, last);
+        __syncthreads();
+    }
+    if (pr.passes == 1) {
+        for (int gi = tid; gi < v.ls.ng; gi += nthr)
+            reinterpret_cast<T*>(v.x + v.ls.lg[gi])[0] = v.gbuf[0][gi];
+        __syncthreads();
+    }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T>* __restrict__ lv, TailParams pr) {
+    typedef typename V2<T>::t T2;
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    // descent
+    for (int l = pr.l0; l < pr.L - 1; l++) {
+        const TailLevel<T>& f = lv[l];
+        const TailLevel<T>& c = lv[l + 1];
+        for (int k = 0; k < pr.nu1; k++) tail_relax<D, T>(f, pr, tid, nthr);
+        stages::CoefPtr<D, T> cf = coefs_of<D, T>(f);
+        int tot = f.ls.n0 + f.ls.n1 + f.ls.ng;
+        for (int t = tid; t < tot; t += nthr)
+            stages::residual_node<D, T, false>(t, f.ls, f.gm, f.gw, cf, f.rhs, f.x, f.res, f.st1, f.st2);
+        __syncthreads();
+        for (int k = 0; k < pr.ext; k++) {
+            bool first = k == 0, last = k == pr.ext - 1;
+            for (int b = tid; b < f.nb; b += nthr)
+                stages::extend_node<D, T, false>(b, f.bidx, f.bref, f.ban, f.res, f.bbuf[(k + 1) & 1], f.bbuf[k & 1],
+                                                (T)pr.cfl, first, last);
+            __syncthreads();
+        }
+        int ctot = c.ls.n0 + c.ls.n1 + c.ls.ng;
+        for (int t = tid; t < ctot; t += nthr)
+            stages::restrict_node<D, T, false>(t, c.ls, c.type, c.n, f.type, f.n, f.res, c.rhs, c.x);
+        __syncthreads();
+    }
+    // coarsest level: x = A^{-1} rhs, one warp per row of the inverse
+    {
+        const TailLevel<T>& c = lv[pr.L - 1];
+        const int m = 2 * c.nact;
+        const int lane = threadIdx.x & 31;
+        const int warp = tid >> 5, nwarp = nthr >> 5;
+        for (int r = warp; r < m; r += nwarp) {
+            const T* row = c.Ainv + (long long)r * m;
+            T acc = 0;
+            for (int j = lane; j < m; j += 32) {
+                T2 b = c.rhs[c.act[j >> 1]];
+                acc += row[j] * ((j & 1) ? b.y : b.x);
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) reinterpret_cast<T*>(c.x + c.act[r >> 1])[r & 1] = acc;
+        }
+        __syncthreads();
+    }
+    // ascent
+    for (int l = pr.L - 2; l >= pr.l0; l--) {
+        const TailLevel<T>& f = lv[l];
+        const TailLevel<T>& c = lv[l + 1];
+        int tot = f.ls.n0 + f.ls.n1 + f.ls.ng;
+        for (int t = tid; t < tot; t += nthr) stages::prolong_node<D, T, false>(t, f.ls, c.type, c.n, c.x, f.n, f.x);
+        __syncthreads();
+        for (int k = 0; k < pr.nu2; k++) tail_relax<D, T>(f, pr, tid, nthr);
+    }
+}
+
+template <typename T>
+TailLevel<T> describe(const LevelGeo& G, const LevelVec<T>& V) {
+    TailLevel<T> t;
+    t.ls = stages::make_lists(G);
+    t.n = G.n;
+    t.st1 = G.st[1];
+    t.st2 = G.st[2];
+    t.type = G.type;
+    t.gpos = G.gpos;
+    t.gm = G.gm;
+    t.gw = std::is_same<T, float>::value ? (const T*)G.gw32 : (const T*)G.gw;
+    t.nb = G.nb;
+    t.bidx = G.bidx;
+    t.bref = G.bref;
+    t.ban = std::is_same<T, float>::value ? (const T*)G.ban32 : (const T*)G.ban;
+    t.nact = G.nact;
+    t.act = G.act;
+    t.Ainv = V.Ainv;
+    t.rhs = V.rhs;
+    t.x = V.x;
+    t.res = V.res;
+    for (int k = 0; k < 2; k++) {
+        t.gbuf[k] = V.gbuf[k];
+        t.bbuf[k] = V.bbuf[k];
+    }
+    for (int a = 0; a < 3; a++) t.edge[a] = V.edge[a];
+    t.Pa = V.Pa;
+    t.Pb = V.Pb;
+    t.Ia = V.Ia;
+    t.Ib = V.Ib;
+    t.gc = V.gc;
+    return t;
+}
+
+}  // namespace
+
+size_t tail_desc_bytes(int L) { return sizeof(TailLevel<double>) * (size_t)L; }
+
+template <typename T>
+int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, cudaStream_t s) {
+    std::vector<TailLevel<T>> h(L);
+    for (int l = 0; l < L; l++) h[l] = describe<T>(G[l], V[l]);
+    cudaError_t e = cudaMemcpyAsync(dev, h.data(), sizeof(TailLevel<T>) * L, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return sulf_fail_cuda(e, "tail descriptor upload");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return sulf_fail_cuda(e, "tail descriptor upload");
+    return SULF_OK;
+}
+
+namespace {
+
+TailParams make_params(int l0, int L, const sulf_solver& sv, int D) {
+    TailParams pr;
+    pr.l0 = l0;
+    pr.L = L;
+    pr.nu1 = sv.nu1;
+    pr.nu2 = sv.nu2;
+    pr.passes = sv.ghost_sweeps;
+    pr.ext = 4;
+    pr.pointwise = sv.smoother == 1;
+    pr.tau = sv.tau_s;
+    pr.cfl = D == 2 ? 0.5 : 1.0 / 3.0;
+    return pr;
+}
+
+}  // namespace
+
+template <int D, typename T>
+int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, cudaStream_t s) {
+    k_tail<D, T><<<1, kTailThreads, 0, s>>>((const TailLevel<T>*)dev_desc, make_params(l0, L, sv, D));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sulf_fail_cuda(e, "fused coarse-level cycle launch");
+    return SULF_OK;
+}
+
+template int upload_tail_desc<double>(const LevelGeo*, const LevelVec<double>*, int, void*, cudaStream_t);
+template int upload_tail_desc<float>(const LevelGeo*, const LevelVec<float>*, int, void*, cudaStream_t);
+template int launch_tail<2, double>(const void*, int, int, const sulf_solver&, cudaStream_t);
+template int launch_tail<2, float>(const void*, int, int, const sulf_solver&, cudaStream_t);
+template int launch_tail<3, double>(const void*, int, int, const sulf_solver&, cudaStream_t);
+template int launch_tail<3, float>(const void*, int, int, const sulf_solver&, cudaStream_t);
+
+}  // namespace sulf

@@ -54,3 +54,11 @@ def test_headers_cite_the_paper():
     for h in ("sulfmg.h", "sulfmg_debug.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         assert "arXiv:1902.07029" in src or "Sec. 3" in src
+
+
+def test_memory_estimate_host_logic(sulfmg):
+    est = sulfmg.estimate_device_bytes
+    assert est(2, 0, 8, 0) == 0 and est(4, 64, 8, 0) == 0
+    assert est(2, 128, 8, 0) < est(2, 256, 8, 0) < est(2, 512, 8, 0)
+    assert est(2, 256, 8, 0) < est(2, 256, 8, 1)
+    assert est(3, 64, 8, 0) > est(2, 64, 8, 0)

@@ -101,10 +101,14 @@ def test_stages(sulfmg, oracle_mod, name, mk):
         _close(dom.inject(W0, l), ref.inject(W0, l), STAGE_TOL)
 
 
+@pytest.mark.parametrize("fuse_below", [100000, 0], ids=["fused_coarse", "per_level"])
 @pytest.mark.parametrize("name,mk", GEOMS, ids=[g[0] for g in GEOMS])
-def test_cycles(sulfmg, oracle_mod, name, mk):
+def test_cycles(sulfmg, oracle_mod, name, mk, fuse_below):
+    """cycles with the coarse levels fused into one single-CTA kernel and with
+    every level as separate kernels"""
     phi, dim, N, cN = mk()
     dom, ref = _pair(sulfmg, oracle_mod, phi, dim, N, cN)
+    dom.set_solver(fuse_below=fuse_below)
     rng = np.random.default_rng(11)
     dt = 2.0 / N
     t0 = ref.level_type(0)
@@ -133,6 +137,7 @@ RUNS = [
 def test_steps_fp64(sulfmg, oracle_mod, name, mk):
     phi, dim, N, cN, dt, nsteps = mk()
     dom, ref = _pair(sulfmg, oracle_mod, phi, dim, N, cN)
+    dom.set_solver(fuse_below=4000)  # level 0 (and 1) as separate kernels, the coarser levels fused
     dom.step(dt, nsteps)
     ref.step(dt, nsteps)
     s, c, t = dom.get_state()
@@ -143,6 +148,23 @@ def test_steps_fp64(sulfmg, oracle_mod, name, mk):
     _close(c[act], rc[act], RUN_TOL)
     sd, so = dom.stats(), ref.stats()
     assert sd["steps_total"] == nsteps
+
+
+@pytest.mark.parametrize("name,mk", RUNS[1:3], ids=[r[0] for r in RUNS[1:3]])
+def test_steps_unfused_and_w_cycle(sulfmg, oracle_mod, name, mk):
+    """every level as separate kernels without graphs, and the paper's W-cycle"""
+    phi, dim, N, cN, dt, nsteps = mk()
+    for kw in (dict(fuse_below=0, graphs=0), dict(cycle=2, nu1=2, nu2=1)):
+        dom, ref = _pair(sulfmg, oracle_mod, phi, dim, N, cN)
+        dom.set_solver(**kw)
+        ref.set_solver(**{k: v for k, v in kw.items() if k in ("cycle", "nu1", "nu2")})
+        dom.step(dt, nsteps)
+        ref.step(dt, nsteps)
+        s, c, t = dom.get_state()
+        rs, rc, rt = ref.get_state()
+        act = (rt == 1) | (rt == 2)
+        _close(s[act], rs[act], RUN_TOL)
+        _close(c[act], rc[act], RUN_TOL)
 
 
 @pytest.mark.parametrize("name,mk", RUNS[:3], ids=[r[0] for r in RUNS[:3]])
