@@ -43,9 +43,17 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # stencil coefficients precomputed per Newton iteration, 2-D: rhs 16, inverse
 # of the 2x2 block 32, own edge coefficients 2*16, the other colour's edge
 # coefficients 2*16 and x 16 (each read once per sweep), x written 16 -- in
-# FP64; half in FP32.  About 23 flops per update: memory-bound (HBM or L2).
+# FP64; half in FP32.  22 flops per update (8 + 2 fused multiply-adds, 2
+# multiplies): the minimum HBM time and the FP64-pipe time are both ~3 us per
+# launch at 1025^2.
 RELAX_BYTES_2D = {"fp64": 144, "mixed": 72}
-RELAX_FLOPS_2D = 23
+RELAX_FLOPS_2D = 22
+# 3-D: rhs 16, inverse 32, own edges 3*16, the other colour's edges 3*16, x 16
+# read and 16 written (FP64); half in FP32
+RELAX_BYTES_3D = {"fp64": 176, "mixed": 88}
+RELAX_FLOPS_3D = 30
+RELAX_BYTES = {2: RELAX_BYTES_2D, 3: RELAX_BYTES_3D}
+RELAX_FLOPS = {2: RELAX_FLOPS_2D, 3: RELAX_FLOPS_3D}
 
 
 def whole_job_value(elapsed_ms_local: float, units_local: int, device=None) -> tuple[float, float]:
@@ -148,7 +156,7 @@ def cpu_baseline(name, budget_s=20.0, precision="fp64"):
     import oracle
 
     w, N, dim, phi, dt = workload_setup(name)
-    ref = oracle.Oracle(phi, dim, -1.0, 1.0, N)
+    ref = oracle.Oracle(phi, dim, -1.0, 1.0, N, w["coarsest"])
     ref.set_model(workloads.PAPER_MODEL)
     ref.set_solver()
     info = ref.level_info(0)
@@ -179,7 +187,7 @@ def run_reference(args):
     import oracle
 
     w, N, dim, phi, dt = workload_setup(args.workload)
-    ref = oracle.Oracle(phi, dim, -1.0, 1.0, N)
+    ref = oracle.Oracle(phi, dim, -1.0, 1.0, N, w["coarsest"])
     ref.set_model(workloads.PAPER_MODEL)
     ref.set_solver()
     t = ref.level_type(0)
@@ -225,7 +233,7 @@ def run_gpu(args):
     dev = torch.device("cuda", lr)
     pkg.build()
     w, N, dim, phi, dt = workload_setup(args.workload)
-    dom = pkg.Domain(phi, dim, (-1.0, 1.0), N)
+    dom = pkg.Domain(phi, dim, (-1.0, 1.0), N, w["coarsest"])
     dom.set_model(workloads.PAPER_MODEL)
     prec = 1 if args.precision == "mixed" else 0
     dom.set_solver(precision=prec)
@@ -247,7 +255,7 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    dom.set_profiling(True)
+    dom.set_profiling(1)  # the first finest-level sweep of every cycle
     launches0 = dom.stats()["kernel_launches"]
     newton0, cyc0 = dom.stats()["newton_total"], dom.stats()["cycles_total"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -294,15 +302,16 @@ def run_gpu(args):
         peaks = measured_peaks()
         avg_us = 1e3 * relax_ms / max(relax_n, 1)
         nodes_per_launch = st0["n_inside"] / 2.0
-        nbytes = RELAX_BYTES_2D[args.precision] * nodes_per_launch
-        achieved = nbytes / (avg_us * 1e-6) / 1e9 if dim == 2 and relax_n else None
+        nbytes = RELAX_BYTES[dim][args.precision] * nodes_per_launch
+        achieved = nbytes / (avg_us * 1e-6) / 1e9 if relax_n else None
         hbm = peaks.get("hbm_gbs")
         roofline = {"kernel": "k_relax_inside (finest level, one colour)", "bound": "hbm",
                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": None,
                     "avg_launch_us": avg_us, "launches": relax_n,
-                    "algorithmic": f"{RELAX_BYTES_2D[args.precision]} B and {RELAX_FLOPS_2D} flop per inside-node "
-                                   f"update; {nodes_per_launch:.0f} nodes per launch",
+                    "algorithmic": f"{RELAX_BYTES[dim][args.precision]} B and {RELAX_FLOPS[dim]} flop per "
+                                   f"inside-node update; {nodes_per_launch:.0f} nodes per launch",
+                    "sample": "the two colour launches of the first finest-level sweep of every cycle",
                     "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); the finest level's working "
                                  "set is partly L2-resident, so the fraction can exceed what HBM alone allows"}
         if prec == 1:
@@ -430,14 +439,14 @@ def run_serve(args):
     for (phi, dim, N, cN, m, dt, nsteps), gap in zip(jobs, gaps):
         time.sleep(gap)
         ids.append(srv.submit(phi, dim, N, m, dt, nsteps, coarsest_N=cN, precision=1))
-    failed = 0
+    failed = []
     nodes = 0.0
     for i, (phi, dim, N, cN, m, dt, nsteps) in zip(ids, jobs):
         try:
             s, c, res = srv.wait(i)
             nodes += float(np.count_nonzero(phi < 0)) * nsteps
-        except pkg.SulfError:
-            failed += 1
+        except pkg.SulfError as e:
+            failed.append({"dim": dim, "N": N, "nsteps": nsteps, "error": str(e)[:160]})
     el = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
@@ -446,7 +455,8 @@ def run_serve(args):
             "data": "synthetic",
             "config": {"workload": "Poisson-arrival serving of random star / rounded-box jobs", "jobs": len(jobs),
                        "arrival_rate_per_s": rate, "workers": args.streams, "budget_GB": 150},
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"], "failed": failed,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"], "failed": len(failed),
+            "failures": failed,
             "max_running": st["max_running"], "peak_reserved_GB": st["peak_reserved_bytes"] / 2 ** 30,
             "inside_node_updates_per_s": nodes / el, "wall_s": el}
     print(json.dumps(line), flush=True)

@@ -70,11 +70,15 @@ typedef struct {
    fuse_below    the first level with at most this many active nodes and all
                  coarser ones run as one single-CTA kernel per V-cycle;
                  0 = every level as separate kernels (W-cycles always are)
-                                                                         default 1500 */
+                                                                         default 1500
+   pdl           1 = kernels of a step are launched as programmatic dependent
+                 launches (each may be scheduled while its predecessor runs and
+                 waits on the device for its completion); 0 = plain stream
+                 order.  Results are the same either way.                default 1 */
 typedef struct {
     int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;
-    int precision, smoother, graphs, fuse_below;
+    int precision, smoother, graphs, fuse_below, pdl;
 } sulf_solver;
 
 /* Counters and timings of the handle. */
@@ -138,10 +142,12 @@ int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_de
 
 int sulf_get_stats(sulf_handle h, sulf_stats* out);
 
-/* Kernel timing for measurement: when on, the library brackets every launch of
-   the finest-level inside relaxation (the dominant kernel) with CUDA events on
-   its stream.  sulf_kernel_time returns the summed device time in ms and the
-   number of bracketed launches since the last reset (synchronises). */
+/* Kernel timing for measurement: the library brackets launches of the
+   finest-level inside relaxation (the dominant kernel) with CUDA events on its
+   stream.  on = 0 off; 1 the two colour launches of the first finest-level
+   sweep of every cycle (a sample that keeps the event overhead small); 2 every
+   finest-level launch.  sulf_kernel_time returns the summed device time in ms
+   and the number of bracketed launches since the last reset (synchronises). */
 int sulf_set_profiling(sulf_handle h, int on);
 int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
 

@@ -26,7 +26,8 @@ class SulfSolver(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("cycle", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("ghost_sweeps", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("lin_rtol", ctypes.c_double), ("tau_s", ctypes.c_double), ("precision", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("graphs", ctypes.c_int), ("fuse_below", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("graphs", ctypes.c_int), ("fuse_below", ctypes.c_int),
+                ("pdl", ctypes.c_int)]
 
 
 class SulfStats(ctypes.Structure):
@@ -138,7 +139,7 @@ def _chk(lib, rc):
 
 def default_solver(**kw) -> SulfSolver:
     s = SulfSolver(nu1=2, nu2=2, cycle=1, max_newton=20, max_cycles=30, ghost_sweeps=4, newton_tol=1e-10,
-                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1, fuse_below=1500)
+                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1, fuse_below=1500, pdl=1)
     for k, v in kw.items():
         setattr(s, k, v)
     return s
@@ -218,8 +219,10 @@ class Domain:
         _chk(self.lib, self.lib.sulf_newton_residual_noalloc(self.h, dt, P(W_ptr), P(Wn_ptr), P(F_ptr),
                                                              P(fnorm_ptr)))
 
-    def set_profiling(self, on: bool):
-        _chk(self.lib, self.lib.sulf_set_profiling(self.h, 1 if on else 0))
+    def set_profiling(self, on):
+        """0/False off; 1/True the first finest-level sweep of every cycle; 2
+        every finest-level sweep."""
+        _chk(self.lib, self.lib.sulf_set_profiling(self.h, int(on)))
 
     def kernel_time(self):
         ms = ctypes.c_double(0)

@@ -3,11 +3,11 @@
 // T of the multigrid arithmetic (double, or float inside FP64 defect
 // correction).  The Newton residual F and the update always run in FP64.
 //
-// The Jacobian is never stored: every kernel recomputes the coefficients of
-// its rows from the (s, c) pair of the node and its axis neighbours (Eqs.
-// JssI, JscI, JcsI, JccI as exact derivatives of F), so a relaxation sweep
-// moves 16 B of coefficients, 16 B of right-hand side and 16 B of unknowns
-// per node instead of a dozen stored matrix entries.
+// The Jacobian is stored as stencil coefficients (Eqs. JssI, JscI, JcsI, JccI
+// as exact derivatives of F), refreshed once per Newton iteration by k_coefs:
+// per node the edge pair (g, e) toward each +axis neighbour and the inverse of
+// the 2x2 diagonal block, per ghost its c row.  Each relaxation is then a
+// handful of loads and fused multiply-adds per node.
 #include "mg_stages.cuh"
 
 namespace sulf {
@@ -18,6 +18,13 @@ using stages::CoefPtr;
 using stages::list_node;
 using stages::Lists;
 using stages::make_lists;
+
+namespace {
+thread_local bool t_pdl = false;
+}  // namespace
+
+void set_launch_pdl(bool on) { t_pdl = on; }
+bool launch_pdl() { return t_pdl; }
 
 namespace {
 
@@ -76,6 +83,7 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
                                                typename V2<T>::t* e0, typename V2<T>::t* e1, typename V2<T>::t* e2,
                                                typename V2<T>::t* Pa, typename V2<T>::t* Pb, typename V2<T>::t* Ia,
                                                typename V2<T>::t* Ib, typename V2<T>::t* gc, Coef<T> c) {
+    pdl_enter();
     typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
@@ -140,9 +148,18 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
                                                       const typename V2<T>::t* __restrict__ rhs,
                                                       typename V2<T>::t* __restrict__ x, long long st1, long long st2) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
     const long long st[3] = {1, st1, st2};
-    stages::relax_node<D, T, PW, false>(list[t], cf, rhs, x, st);
+    // the list and the stencil coefficients are fixed during the linear solve:
+    // fetch them while the previous kernel is still running
+    long long p = 0;
+    stages::InsideCoef<D, T> k;
+    if (t < cnt) {
+        p = list[t];
+        k = stages::fetch_inside<D, T, PW>(p, cf, st);
+    }
+    pdl_enter();
+    if (t >= cnt) return;
+    stages::relax_apply<D, T, PW, false>(p, k, rhs, x, st);
 }
 
 // one Jacobi pass of the ghost relaxation of Eq. RelGhost over all ghosts
@@ -154,14 +171,29 @@ __global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict
                                                     typename V2<T>::t* x, const T* sin, T* sout, long long st1,
                                                     long long st2, Coef<T> c, int first, int last) {
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    // the boundary rows and the ghost c-row coefficients are fixed during the
+    // linear solve: fetch them (and, in 2-D, the members' ghost indices) while
+    // the previous kernel is still running
+    stages::GhostRow<D, T> row;
+    typename V2<T>::t q;
+    int src[stages::kGhostSrc];
+    const bool hoist = D == 2 && !first;
+    if (gi < ng) {
+        row = stages::fetch_ghost_row<D, T>(gi, gidx[gi], gm, gw);
+        q = gc[gi];
+        if constexpr (D == 2)
+            if (hoist) stages::fetch_ghost_src<D, T>(row, gpos, st1, src);
+    }
+    pdl_enter();
     if (gi >= ng) return;
-    stages::ghost_pass_node<D, T, false>(gi, gidx, gpos, gm, gw, gc, rhs, x, sin, sout, st1, st2, c.tau, first != 0,
-                                         last != 0);
+    stages::ghost_pass_apply<D, T, false>(gi, row, hoist ? src : nullptr, q, gpos, rhs, x, sin, sout, st1, st2,
+                                          c.tau, first != 0, last != 0);
 }
 
 template <typename T>
 __global__ void k_ghost_scatter(int ng, const int* __restrict__ gidx, const T* __restrict__ sin,
                                 typename V2<T>::t* x) {
+    pdl_enter();
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= ng) return;
     reinterpret_cast<T*>(x + gidx[gi])[0] = sin[gi];
@@ -177,8 +209,17 @@ __global__ void __launch_bounds__(kT) k_residual(Lists ls, const int8_t* __restr
                                                   typename V2<T>::t* __restrict__ res, long long st1, long long st2,
                                                   unsigned long long* norm) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = t < ls.n0 + ls.n1 + ls.ng;
+    // lists and coefficients are fixed during the linear solve: fetched ahead
+    int kind = 0;
+    long long p = 0;
+    stages::InsideCoef<D, T> k;
+    stages::GhostRow<D, T> row;
+    typename V2<T>::t q;
+    if (on) p = stages::fetch_residual<D, T>(t, ls, gm, gw, cf, st1, st2, kind, k, row, q);
+    pdl_enter();
     unsigned long long nb = 0;
-    if (t < ls.n0 + ls.n1 + ls.ng) nb = stages::residual_node<D, T, false>(t, ls, gm, gw, cf, rhs, x, res, st1, st2);
+    if (on) nb = stages::residual_apply<D, T, false>(p, kind, k, row, q, rhs, x, res, st1, st2);
     if (norm) block_max(nb, norm);
 }
 
@@ -192,8 +233,11 @@ __global__ void k_extend_step(int nb, const int* __restrict__ bidx, const int* _
                               const typename V2<T>::t* __restrict__ bin, typename V2<T>::t* __restrict__ bout, T cfl,
                               int first, int last) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
+    stages::BandRef<D, T> br;
+    if (b < nb) br = stages::fetch_band<D, T>(b, bref, ban);  // fixed geometry, fetched ahead
+    pdl_enter();
     if (b >= nb) return;
-    stages::extend_node<D, T, false>(b, bidx, bref, ban, res, bin, bout, cfl, first != 0, last != 0);
+    stages::extend_apply<D, T, false>(b, br, bidx, res, bin, bout, cfl, first != 0, last != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -209,8 +253,12 @@ __global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restr
                                                   typename V2<T>::t* __restrict__ crhs,
                                                   typename V2<T>::t* __restrict__ cx) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ls.n0 + ls.n1 + ls.ng) return;
-    stages::restrict_node<D, T, false>(t, ls, ctype, cn, ftype, fn, fres, crhs, cx);
+    const bool on = t < ls.n0 + ls.n1 + ls.ng;
+    stages::RestrictGeo<D, T> g;
+    if (on) g = stages::fetch_restrict<D, T>(t, ls, ctype, cn, ftype, fn);  // fixed geometry, fetched ahead
+    pdl_enter();
+    if (!on) return;
+    stages::restrict_apply<D, T, false>(g, fn, fres, crhs, cx);
 }
 
 // (bi/tri)linear interpolation of the coarse error to every fine active node,
@@ -220,8 +268,12 @@ __global__ void __launch_bounds__(kT) k_prolong(Lists ls, const int8_t* __restri
                                                  const typename V2<T>::t* __restrict__ cx, int fn,
                                                  typename V2<T>::t* __restrict__ fx) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ls.n0 + ls.n1 + ls.ng) return;
-    stages::prolong_node<D, T, false>(t, ls, ctype, cn, cx, fn, fx);
+    const bool on = t < ls.n0 + ls.n1 + ls.ng;
+    stages::ProlongGeo<D, T> g;
+    if (on) g = stages::fetch_prolong<D, T>(t, ls, ctype, cn, fn);  // fixed geometry, fetched ahead
+    pdl_enter();
+    if (!on) return;
+    stages::prolong_apply<D, T, false>(g, fn, cx, fx);
 }
 
 // coarse Jacobian coefficients by injection of (s, c); a coarse ghost whose
@@ -230,6 +282,7 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_inject(Lists ls, int cn, const int8_t* __restrict__ ftype, int fn,
                                                 const typename V2<T>::t* __restrict__ fW,
                                                 typename V2<T>::t* __restrict__ cW) {
+    pdl_enter();
     typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
@@ -287,6 +340,7 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
                                                           const typename V2<T>::t* __restrict__ Wc, Offs<D> of,
                                                           long long st1, long long st2, Coef<T> c, T* Ag, T* Ainv_g,
                                                           int* singular) {
+    pdl_enter();
     typedef typename V2<T>::t T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = 2 * nact;
@@ -421,6 +475,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_coarsest_solve(int nact, const int* __restrict__ act, const T* __restrict__ Ainv,
                                                          const typename V2<T>::t* __restrict__ rhs,
                                                          typename V2<T>::t* __restrict__ x) {
+    pdl_enter();
     typedef typename V2<T>::t T2;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* b = reinterpret_cast<T*>(smraw);
@@ -472,6 +527,7 @@ __device__ __forceinline__ double Ls_h(long long p, const double2* __restrict__ 
 template <int D>
 __global__ void __launch_bounds__(kT) k_old_time(Lists ls, const double2* __restrict__ Wn, double2* __restrict__ G,
                                                   Offs<D> of, FConst f) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
     int kind, gi;
@@ -495,6 +551,7 @@ __global__ void __launch_bounds__(kT) k_newton_F(Lists ls, const int8_t* __restr
                                                   const double2* __restrict__ W, const double2* __restrict__ G,
                                                   double2* __restrict__ F, Offs<D> of, long long st1, long long st2,
                                                   FConst f, unsigned long long* norm) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nb = 0;
     if (t < ls.n0 + ls.n1 + ls.ng) {
@@ -523,6 +580,7 @@ __global__ void __launch_bounds__(kT) k_newton_F(Lists ls, const int8_t* __restr
 // W -= x on active nodes; norms[0] = |x|_inf, norms[1] = |W_old|_inf
 __global__ void __launch_bounds__(kT) k_newton_update(Lists ls, double2* __restrict__ W, const double2* __restrict__ x,
                                                       unsigned long long* norms) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nx = 0, nw = 0;
     if (t < ls.n0 + ls.n1 + ls.ng) {
@@ -544,6 +602,7 @@ __global__ void __launch_bounds__(kT) k_newton_update(Lists ls, double2* __restr
 }
 
 __global__ void __launch_bounds__(kT) k_norm_active(Lists ls, const double2* __restrict__ v, unsigned long long* norm) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nb = 0;
     if (t < ls.n0 + ls.n1 + ls.ng) {
@@ -558,6 +617,7 @@ __global__ void __launch_bounds__(kT) k_norm_active(Lists ls, const double2* __r
 
 // mixed precision: FP64 values to FP32 on active nodes
 __global__ void k_to_float2(Lists ls, const double2* __restrict__ a, float2* __restrict__ b) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
     int kind, gi;
@@ -568,6 +628,7 @@ __global__ void k_to_float2(Lists ls, const double2* __restrict__ a, float2* __r
 
 // x64 += e32 on active nodes
 __global__ void k_accumulate(Lists ls, double2* __restrict__ x, const float2* __restrict__ e) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
     int kind, gi;
@@ -581,6 +642,7 @@ __global__ void k_accumulate(Lists ls, double2* __restrict__ x, const float2* __
 
 // state import / export over the box
 __global__ void k_reset_state(const int8_t* __restrict__ type, long long nn, double2* W, double s0, double c0) {
+    pdl_enter();
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= nn) return;
     int8_t t = type[i];
@@ -590,6 +652,7 @@ __global__ void k_reset_state(const int8_t* __restrict__ type, long long nn, dou
 
 __global__ void k_import_state(const int8_t* __restrict__ type, long long nn, double2* W, const double* __restrict__ sv,
                                const double* __restrict__ cv) {
+    pdl_enter();
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= nn) return;
     int8_t t = type[i];
@@ -599,6 +662,7 @@ __global__ void k_import_state(const int8_t* __restrict__ type, long long nn, do
 
 __global__ void k_export_state(const int8_t* __restrict__ type, long long nn, const double2* __restrict__ W,
                                double* sv, double* cv, int8_t* tv) {
+    pdl_enter();
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= nn) return;
     int8_t t = type[i];
@@ -619,7 +683,7 @@ int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cuda
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
-    k_coefs<D, T><<<nblk(tot), kT, 0, s>>>(ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa, V.Pb, V.Ia, V.Ib,
+    launch_k(k_coefs<D, T>, nblk(tot), kT, 0, s, ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa, V.Pb, V.Ia, V.Ib,
                                             V.gc, c);
     return 1;
 }
@@ -632,9 +696,9 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
     (void)c;
     CoefPtr<D, T> cf = coef_ptr<D, T>(V);
     if (pointwise)
-        k_relax_inside<D, T, true><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, true>, nblk(cnt), kT, 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
     else
-        k_relax_inside<D, T, false><<<nblk(cnt), kT, 0, s>>>(L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, false>, nblk(cnt), kT, 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
     return 1;
 }
 
@@ -647,12 +711,12 @@ int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
         bool first = p == 0, last = p == passes - 1 && passes > 1;
         const T* sin = first ? nullptr : V.gbuf[(p - 1) & 1];
         T* sout = V.gbuf[p & 1];
-        k_ghost_pass<D, T><<<nblk(L.ng), kT, 0, s>>>(L.ng, L.gidx, L.gpos, L.gm, gw, V.gc, V.rhs, V.x, sin, sout,
+        launch_k(k_ghost_pass<D, T>, nblk(L.ng), kT, 0, s, L.ng, L.gidx, L.gpos, L.gm, gw, V.gc, V.rhs, V.x, sin, sout,
                                                       L.st[1], L.st[2], c, first, last);
         n++;
     }
     if (passes == 1) {
-        k_ghost_scatter<T><<<nblk(L.ng), kT, 0, s>>>(L.ng, L.gidx, V.gbuf[0], V.x);
+        launch_k(k_ghost_scatter<T>, nblk(L.ng), kT, 0, s, L.ng, L.gidx, V.gbuf[0], V.x);
         n++;
     }
     return n;
@@ -666,7 +730,7 @@ int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, u
     if (tot == 0) return 0;
     (void)c;
     const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
-    k_residual<D, T><<<nblk(tot), kT, 0, s>>>(ls, L.gm, gw, coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2],
+    launch_k(k_residual<D, T>, nblk(tot), kT, 0, s, ls, L.gm, gw, coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2],
                                                norm);
     return 1;
 }
@@ -678,7 +742,7 @@ int launch_extend(const LevelGeo& L, const LevelVec<T>& V, int steps, cudaStream
     T cfl = D == 2 ? (T)0.5 : (T)(1.0 / 3.0);
     for (int k = 0; k < steps; k++) {
         bool first = k == 0, last = k == steps - 1;
-        k_extend_step<D, T><<<nblk(L.nb), kT, 0, s>>>(L.nb, L.bidx, L.bref, an, V.res, V.bbuf[(k + 1) & 1],
+        launch_k(k_extend_step<D, T>, nblk(L.nb), kT, 0, s, L.nb, L.bidx, L.bref, an, V.res, V.bbuf[(k + 1) & 1],
                                                        V.bbuf[k & 1], cfl, first, last);
     }
     return steps;
@@ -689,7 +753,7 @@ int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C,
                     cudaStream_t s) {
     Lists ls = make_lists(C);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_restrict<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs, CV.x);
+    launch_k(k_restrict<D, T>, nblk(tot), kT, 0, s, ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs, CV.x);
     return 1;
 }
 
@@ -698,7 +762,7 @@ int launch_prolong(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, 
                    cudaStream_t s) {
     Lists ls = make_lists(F);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_prolong<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.type, C.n, CV.x, F.n, FV.x);
+    launch_k(k_prolong<D, T>, nblk(tot), kT, 0, s, ls, C.type, C.n, CV.x, F.n, FV.x);
     return 1;
 }
 
@@ -707,7 +771,7 @@ int launch_inject(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, c
                   cudaStream_t s) {
     Lists ls = make_lists(C);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_inject<D, T><<<nblk(tot), kT, 0, s>>>(ls, C.n, F.type, F.n, FV.Wc, CV.Wc);
+    launch_k(k_inject<D, T>, nblk(tot), kT, 0, s, ls, C.n, F.type, F.n, FV.Wc, CV.Wc);
     return 1;
 }
 
@@ -722,10 +786,10 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
     if (smem_full <= 220 * 1024) {
         auto kern = k_coarsest_factor<D, T, true>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_full);
-        kern<<<1, 1024, smem_full, s>>>(L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw, V.Wc, of, L.st[1], L.st[2],
+        launch_k(kern, 1, 1024, smem_full, s, L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw, V.Wc, of, L.st[1], L.st[2],
                                         c, V.A, V.Ainv, singular);
     } else {
-        k_coarsest_factor<D, T, false><<<1, 1024, piv_bytes, s>>>(L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw,
+        launch_k(k_coarsest_factor<D, T, false>, 1, 1024, piv_bytes, s, L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw,
                                                                   V.Wc, of, L.st[1], L.st[2], c, V.A, V.Ainv,
                                                                   singular);
     }
@@ -735,7 +799,7 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
 template <int D, typename T>
 int launch_coarsest_solve(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s) {
     size_t shm = sizeof(T) * (4 * (size_t)L.nact + 2);
-    k_coarsest_solve<T><<<1, 1024, shm, s>>>(L.nact, L.act, V.Ainv, V.rhs, V.x);
+    launch_k(k_coarsest_solve<T>, 1, 1024, shm, s, L.nact, L.act, V.Ainv, V.rhs, V.x);
     return 1;
 }
 
@@ -743,7 +807,7 @@ template <int D>
 int launch_old_time(const LevelGeo& L, const double2* Wn, double2* G, const FConst& fc, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_old_time<D><<<nblk(tot), kT, 0, s>>>(ls, Wn, G, make_offs<D>(L.st[1], L.st[2]), fc);
+    launch_k(k_old_time<D>, nblk(tot), kT, 0, s, ls, Wn, G, make_offs<D>(L.st[1], L.st[2]), fc);
     return 1;
 }
 
@@ -752,7 +816,7 @@ int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, doubl
                     unsigned long long* norm, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_newton_F<D><<<nblk(tot), kT, 0, s>>>(ls, L.gm, L.gw, W, G, F, make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2],
+    launch_k(k_newton_F<D>, nblk(tot), kT, 0, s, ls, L.gm, L.gw, W, G, F, make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2],
                                             fc, norm);
     return 1;
 }
@@ -760,43 +824,43 @@ int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, doubl
 int launch_newton_update(const LevelGeo& L, double2* W, const double2* x, unsigned long long* norms, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_newton_update<<<nblk(tot), kT, 0, s>>>(ls, W, x, norms);
+    launch_k(k_newton_update, nblk(tot), kT, 0, s, ls, W, x, norms);
     return 1;
 }
 
 int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* norm, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_norm_active<<<nblk(tot), kT, 0, s>>>(ls, v, norm);
+    launch_k(k_norm_active, nblk(tot), kT, 0, s, ls, v, norm);
     return 1;
 }
 
 int launch_to_float(const LevelGeo& L, const double2* src, float2* dst, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_to_float2<<<nblk(tot), kT, 0, s>>>(ls, src, dst);
+    launch_k(k_to_float2, nblk(tot), kT, 0, s, ls, src, dst);
     return 1;
 }
 
 int launch_accumulate(const LevelGeo& L, double2* x, const float2* e, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    k_accumulate<<<nblk(tot), kT, 0, s>>>(ls, x, e);
+    launch_k(k_accumulate, nblk(tot), kT, 0, s, ls, x, e);
     return 1;
 }
 
 int launch_reset_state(const LevelGeo& L, double2* W, double s0, double c0, cudaStream_t s) {
-    k_reset_state<<<nblk(L.nn), kT, 0, s>>>(L.type, L.nn, W, s0, c0);
+    launch_k(k_reset_state, nblk(L.nn), kT, 0, s, L.type, L.nn, W, s0, c0);
     return 1;
 }
 
 int launch_import_state(const LevelGeo& L, double2* W, const double* sv, const double* cv, cudaStream_t s) {
-    k_import_state<<<nblk(L.nn), kT, 0, s>>>(L.type, L.nn, W, sv, cv);
+    launch_k(k_import_state, nblk(L.nn), kT, 0, s, L.type, L.nn, W, sv, cv);
     return 1;
 }
 
 int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double* cv, int8_t* tv, cudaStream_t s) {
-    k_export_state<<<nblk(L.nn), kT, 0, s>>>(L.type, L.nn, W, sv, cv, tv);
+    launch_k(k_export_state, nblk(L.nn), kT, 0, s, L.type, L.nn, W, sv, cv, tv);
     return 1;
 }
 

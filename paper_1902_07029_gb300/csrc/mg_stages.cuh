@@ -85,103 +85,189 @@ inline CoefPtr<D, T> coef_ptr(const LevelVec<T>& V) {
     return c;
 }
 
-// off-diagonal part of the s row of an inside node applied to x (Eq. JssI and
-// Eq. JscI as exact derivatives): sum over the axis neighbours q of
-// J^ss_pq x^s_q + J^sc_pq x^c_q with J^ss_pq = -g and J^sc_pq = +-e
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// b_s minus the off-diagonal part of the s row of inside node p applied to x
+// (Eq. JssI and Eq. JscI as exact derivatives): over the axis neighbours q,
+// J^ss_pq = -g and J^sc_pq = +-e, so b_s - sum_q (J^ss_pq x^s_q + J^sc_pq x^c_q)
+// is one chain of 4 fused multiply-adds per axis.  FP64 issue rate is the
+// scarce resource on this GPU, so the chain is written out explicitly.
 template <int D, typename T, bool CG>
-__device__ __forceinline__ T offdiag_s(long long p, const CoefPtr<D, T>& cf, const typename V2<T>::t* x,
-                                       const long long* st) {
+__device__ __forceinline__ T s_defect(T bs, long long p, const typename V2<T>::t* ge, const typename V2<T>::t* gw,
+                                      const typename V2<T>::t* x, const long long* st) {
     typedef typename V2<T>::t T2;
-    T acc = 0;
+    T r = bs;
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        T2 ge = cf.edge[a][p];
         T2 xe = ldx<CG>(x + p + st[a]);
-        T2 gw = cf.edge[a][p - st[a]];
         T2 xw = ldx<CG>(x + p - st[a]);
-        acc += (ge.y * xe.y - ge.x * xe.x) - (gw.x * xw.x + gw.y * xw.y);
+        r = fmadd(ge[a].x, xe.x, r);
+        r = fmadd(-ge[a].y, xe.y, r);
+        r = fmadd(gw[a].x, xw.x, r);
+        r = fmadd(gw[a].y, xw.y, r);
     }
-    return acc;
+    return r;
+}
+
+// The coefficients an inside-node update needs, all fixed during a linear
+// solve: the edge pairs toward the +axis neighbours (ge) and from the -axis
+// neighbours (gw), and the rows of P^{-1} (collective) or of P (pointwise).
+template <int D, typename T>
+struct InsideCoef {
+    typedef typename V2<T>::t T2;
+    T2 ge[D], gw[D];
+    T2 m0, m1;
+};
+
+template <int D, typename T, bool PW>
+__device__ __forceinline__ InsideCoef<D, T> fetch_inside(long long p, const CoefPtr<D, T>& cf, const long long* st) {
+    InsideCoef<D, T> k;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        k.ge[a] = cf.edge[a][p];
+        k.gw[a] = cf.edge[a][p - st[a]];
+    }
+    k.m0 = PW ? cf.Pa[p] : cf.Ia[p];
+    k.m1 = PW ? cf.Pb[p] : cf.Ib[p];
+    return k;
 }
 
 // collective (Eq. matrixP) or pointwise (Eq. matrixPclassical) update of the
-// inside node p: x_p <- P^{-1} (b - (J - P) x), resp. the diagonal of P
+// inside node p from its fetched coefficients: x_p <- P^{-1} (b - (J - P) x),
+// resp. the diagonal of P
 template <int D, typename T, bool PW, bool CG>
-__device__ __forceinline__ void relax_node(long long p, const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
-                                           typename V2<T>::t* x, const long long* st) {
+__device__ __forceinline__ void relax_apply(long long p, const InsideCoef<D, T>& k, const typename V2<T>::t* rhs,
+                                            typename V2<T>::t* x, const long long* st) {
     typedef typename V2<T>::t T2;
-    T off = offdiag_s<D, T, CG>(p, cf, x, st);
     T2 b = ldx<CG>(rhs + p);
+    T r = s_defect<D, T, CG>(b.x, p, k.ge, k.gw, x, st);
     T2 out;
     if (PW) {
         T2 xp = ldx<CG>(x + p);
-        T2 pa = cf.Pa[p], pb = cf.Pb[p];
-        out.x = (b.x - off - pa.y * xp.y) / pa.x;
-        out.y = (b.y - pb.x * xp.x) / pb.y;
+        out.x = fmadd(-k.m0.y, xp.y, r) / k.m0.x;
+        out.y = fmadd(-k.m1.x, xp.x, b.y) / k.m1.y;
     } else {
-        T2 ia = cf.Ia[p], ib = cf.Ib[p];
-        T r = b.x - off;
-        out.x = ia.x * r + ia.y * b.y;
-        out.y = ib.x * r + ib.y * b.y;
+        out.x = fmadd(k.m0.x, r, k.m0.y * b.y);
+        out.y = fmadd(k.m1.x, r, k.m1.y * b.y);
     }
     x[p] = out;
 }
 
-// boundary row s~(B) of ghost gi applied to the s component: tensor-product
-// weights on the upwind stencil (Eq. JssD).  Ghost members come from the
-// previous relaxation pass (sin) unless from_x.
-template <int D, typename T, bool CG>
-__device__ __forceinline__ T ghost_dot(int gi, long long g, const int8_t* gm, const T* gw, const int* gpos,
-                                       const typename V2<T>::t* x, const T* sin, bool from_x, long long st1,
-                                       long long st2) {
+template <int D, typename T, bool PW, bool CG>
+__device__ __forceinline__ void relax_node(long long p, const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
+                                           typename V2<T>::t* x, const long long* st) {
+    InsideCoef<D, T> k = fetch_inside<D, T, PW>(p, cf, st);
+    relax_apply<D, T, PW, CG>(p, k, rhs, x, st);
+}
+
+// The fixed part of ghost gi's boundary row s~(B) (Eq. JssD): the ghost node,
+// the upwind signs and the 1-D weights at offsets 0, 1, 2 per axis.
+template <int D, typename T>
+struct GhostRow {
+    long long g;
+    int m[3];
     T wa[3][3];
-    int m[3] = {1, 1, 1};
+};
+
+template <int D, typename T>
+__device__ __forceinline__ GhostRow<D, T> fetch_ghost_row(int gi, long long g, const int8_t* gm, const T* gw) {
+    GhostRow<D, T> r;
+    r.g = g;
+    r.m[0] = r.m[1] = r.m[2] = 1;
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        m[a] = gm[(long long)gi * D + a];
+        r.m[a] = gm[(long long)gi * D + a];
 #pragma unroll
-        for (int k = 0; k < 3; k++) wa[a][k] = gw[(long long)gi * 3 * D + 3 * a + k];
+        for (int k = 0; k < 3; k++) r.wa[a][k] = gw[(long long)gi * 3 * D + 3 * a + k];
     }
-    const long long st[3] = {1, st1, st2};
-    const int K = D == 2 ? 9 : 27;
+    return r;
+}
+
+// tensor weight and node of member kk of the upwind 3^D stencil
+template <int D, typename T>
+__device__ __forceinline__ T row_member(const GhostRow<D, T>& r, int kk, long long st1, long long st2,
+                                        long long& node) {
+    const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+    T w = r.wa[0][k0] * r.wa[1][k1];
+    if (D == 3) w = w * r.wa[2][k2];
+    node = r.g - r.m[0] * k0 - r.m[1] * k1 * st1;
+    if (D == 3) node -= r.m[2] * k2 * st2;
+    return w;
+}
+
+constexpr int kGhostSrc = 9;  // 2-D stencil members whose ghost index is fetched ahead
+
+// ghost index (or -1) of every stencil member with a nonzero weight (2-D)
+template <int D, typename T>
+__device__ __forceinline__ void fetch_ghost_src(const GhostRow<D, T>& r, const int* gpos, long long st1,
+                                                int* src) {
+    static_assert(D == 2, "member ghost indices are fetched ahead in 2-D only");
+#pragma unroll
+    for (int kk = 0; kk < kGhostSrc; kk++) {
+        long long node;
+        T w = row_member<D, T>(r, kk, st1, 0, node);
+        src[kk] = w == (T)0 ? -1 : gpos[node];
+    }
+}
+
+// the row applied to the s component.  Ghost members come from the previous
+// relaxation pass (sin) unless from_x; their ghost indices from src when given
+// (2-D), else from gpos.  The member values are gathered nine at a time with
+// every load issued before any is used (one memory latency per nine members,
+// not one per member), then summed in member order.
+template <int D, typename T, bool CG>
+__device__ __forceinline__ T row_dot(const GhostRow<D, T>& r, const int* src, const int* gpos,
+                                     const typename V2<T>::t* x, const T* sin, bool from_x, long long st1,
+                                     long long st2) {
+    constexpr int K = D == 2 ? 9 : 27;
     T acc = 0;
 #pragma unroll
-    for (int kk = 0; kk < K; kk++) {
-        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
-        T w = wa[0][k0] * wa[1][k1];
-        if (D == 3) w = w * wa[2][k2];
-        if (w == (T)0) continue;
-        long long node = g - m[0] * k0 * st[0] - m[1] * k1 * st[1];
-        if (D == 3) node -= m[2] * k2 * st[2];
-        T v;
-        if (from_x) {
-            v = ldx<CG>(x + node).x;
-        } else {
-            int gp = gpos[node];
-            v = gp >= 0 ? ldx<CG>(sin + gp) : ldx<CG>(x + node).x;
+    for (int c0 = 0; c0 < K; c0 += 9) {
+        T w[9], v[9];
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            long long node;
+            w[j] = row_member<D, T>(r, c0 + j, st1, st2, node);
+            const T* a = reinterpret_cast<const T*>(x + node);
+            if (!from_x) {
+                int gp = (D == 2 && src) ? src[j] : (w[j] != (T)0 ? gpos[node] : -1);
+                if (gp >= 0) a = sin + gp;
+            }
+            v[j] = w[j] != (T)0 ? ldx<CG>(a) : (T)0;
         }
-        acc += w * v;
+#pragma unroll
+        for (int j = 0; j < 9; j++)
+            if (w[j] != (T)0) acc += w[j] * v[j];
     }
     return acc;
 }
 
-// one Jacobi pass of the ghost relaxation (Eq. RelGhost) for ghost gi:
-// s_g += tau (r_g - row . x) from the previous pass's values, then the ghost c
-// row relaxed by its diagonal with the fresh s_g
 template <int D, typename T, bool CG>
-__device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const int* gpos, const int8_t* gm,
-                                                const T* gw, const typename V2<T>::t* gc,
-                                                const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* sin,
-                                                T* sout, long long st1, long long st2, T tau, bool first,
-                                                bool last) {
+__device__ __forceinline__ T ghost_dot(int gi, long long g, const int8_t* gm, const T* gw, const int* gpos,
+                                       const typename V2<T>::t* x, const T* sin, bool from_x, long long st1,
+                                       long long st2) {
+    GhostRow<D, T> r = fetch_ghost_row<D, T>(gi, g, gm, gw);
+    return row_dot<D, T, CG>(r, nullptr, gpos, x, sin, from_x, st1, st2);
+}
+
+// one Jacobi pass of the ghost relaxation (Eq. RelGhost) for ghost gi from its
+// fetched row: s_g += tau (r_g - row . x) from the previous pass's values,
+// then the ghost c row relaxed by its diagonal with the fresh s_g
+template <int D, typename T, bool CG>
+__device__ __forceinline__ void ghost_pass_apply(int gi, const GhostRow<D, T>& row, const int* src,
+                                                 typename V2<T>::t q, const int* gpos,
+                                                 const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* sin,
+                                                 T* sout, long long st1, long long st2, T tau, bool first,
+                                                 bool last) {
     typedef typename V2<T>::t T2;
-    long long g = gidx[gi];
-    T acc = ghost_dot<D, T, CG>(gi, g, gm, gw, gpos, x, sin, first, st1, st2);
+    const long long g = row.g;
+    T acc = row_dot<D, T, CG>(row, src, gpos, x, sin, first, st1, st2);
     T2 xg = ldx<CG>(x + g);
     T s_old = first ? xg.x : ldx<CG>(sin + gi);
     T2 b = ldx<CG>(rhs + g);
     T s_new = s_old + tau * (b.x - acc);
-    T2 q = gc[gi];  // (J^cs_gg, J^cc_gg)
+    // q = (J^cs_gg, J^cc_gg)
     T c_new = xg.y + (b.y - (q.x * s_new + q.y * xg.y)) / q.y;
     T* xs = reinterpret_cast<T*>(x + g);
     xs[1] = c_new;
@@ -191,27 +277,35 @@ __device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const i
         sout[gi] = s_new;
 }
 
-// defect r = rhs - J x at list position t; returns max(|r_s|, |r_c|) as bits
 template <int D, typename T, bool CG>
-__device__ __forceinline__ unsigned long long residual_node(int t, const Lists& ls, const int8_t* gm, const T* gw,
-                                                            const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
-                                                            const typename V2<T>::t* x, typename V2<T>::t* res,
-                                                            long long st1, long long st2) {
+__device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const int* gpos, const int8_t* gm,
+                                                const T* gw, const typename V2<T>::t* gc,
+                                                const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* sin,
+                                                T* sout, long long st1, long long st2, T tau, bool first,
+                                                bool last) {
+    GhostRow<D, T> row = fetch_ghost_row<D, T>(gi, gidx[gi], gm, gw);
+    ghost_pass_apply<D, T, CG>(gi, row, nullptr, gc[gi], gpos, rhs, x, sin, sout, st1, st2, tau, first, last);
+}
+
+// defect r = rhs - J x at node p of kind 1 (inside, coefficients k) or 2
+// (ghost, boundary row and c-row q); returns max(|r_s|, |r_c|) as bits
+template <int D, typename T, bool CG>
+__device__ __forceinline__ unsigned long long residual_apply(long long p, int kind, const InsideCoef<D, T>& k,
+                                                             const GhostRow<D, T>& row, typename V2<T>::t q,
+                                                             const typename V2<T>::t* rhs,
+                                                             const typename V2<T>::t* x, typename V2<T>::t* res,
+                                                             long long st1, long long st2) {
     typedef typename V2<T>::t T2;
-    int kind, gi = 0;
-    long long p = list_node(ls, t, kind, gi);
     T2 b = ldx<CG>(rhs + p);
     T2 xp = ldx<CG>(x + p);
     T2 r;
     if (kind == 1) {
         const long long st[3] = {1, st1, st2};
-        T off = offdiag_s<D, T, CG>(p, cf, x, st);
-        T2 pa = cf.Pa[p], pb = cf.Pb[p];
-        r.x = b.x - (pa.x * xp.x + pa.y * xp.y + off);
-        r.y = b.y - (pb.x * xp.x + pb.y * xp.y);
+        T rs = s_defect<D, T, CG>(b.x, p, k.ge, k.gw, x, st);
+        r.x = fmadd(-k.m0.y, xp.y, fmadd(-k.m0.x, xp.x, rs));
+        r.y = fmadd(-k.m1.y, xp.y, fmadd(-k.m1.x, xp.x, b.y));
     } else {
-        T acc = ghost_dot<D, T, CG>(gi, p, gm, gw, nullptr, x, nullptr, true, st1, st2);
-        T2 q = cf.gc[gi];
+        T acc = row_dot<D, T, CG>(row, nullptr, nullptr, x, nullptr, true, st1, st2);
         r.x = b.x - acc;
         r.y = b.y - (q.x * xp.x + q.y * xp.y);
     }
@@ -220,39 +314,83 @@ __device__ __forceinline__ unsigned long long residual_node(int t, const Lists& 
     return a0 > a1 ? a0 : a1;
 }
 
-// one explicit upwind Euler step of dr/dtau + n.grad r = 0 at band node b
-// (Sec. 3.5.2); band values start at 0
-template <int D, typename T, bool CG>
-__device__ __forceinline__ void extend_node(int b, const int* bidx, const int* bref, const T* ban,
-                                            typename V2<T>::t* res, const typename V2<T>::t* bin,
-                                            typename V2<T>::t* bout, T cfl, bool first, bool last) {
-    typedef typename V2<T>::t T2;
-    T2 v;
-    if (first) {
-        v.x = 0;
-        v.y = 0;
+// the fixed data of the defect at list position t
+template <int D, typename T>
+__device__ __forceinline__ long long fetch_residual(int t, const Lists& ls, const int8_t* gm, const T* gw,
+                                                   const CoefPtr<D, T>& cf, long long st1, long long st2, int& kind,
+                                                   InsideCoef<D, T>& k, GhostRow<D, T>& row,
+                                                   typename V2<T>::t& q) {
+    int gi = 0;
+    long long p = list_node(ls, t, kind, gi);
+    if (kind == 1) {
+        const long long st[3] = {1, st1, st2};
+        k = fetch_inside<D, T, true>(p, cf, st);
     } else {
-        v = ldx<CG>(bin + b);
+        row = fetch_ghost_row<D, T>(gi, p, gm, gw);
+        q = cf.gc[gi];
+    }
+    return p;
+}
+
+template <int D, typename T, bool CG>
+__device__ __forceinline__ unsigned long long residual_node(int t, const Lists& ls, const int8_t* gm, const T* gw,
+                                                            const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
+                                                            const typename V2<T>::t* x, typename V2<T>::t* res,
+                                                            long long st1, long long st2) {
+    int kind;
+    InsideCoef<D, T> k;
+    GhostRow<D, T> row;
+    typename V2<T>::t q;
+    long long p = fetch_residual<D, T>(t, ls, gm, gw, cf, st1, st2, kind, k, row, q);
+    return residual_apply<D, T, CG>(p, kind, k, row, q, rhs, x, res, st1, st2);
+}
+
+// one explicit upwind Euler step of dr/dtau + n.grad r = 0 at band node b
+// (Sec. 3.5.2); band values start at 0.  The upwind references and |n_a| are
+// fixed geometry (BandRef, fetched ahead by the per-level kernel).
+template <int D, typename T>
+struct BandRef {
+    int ref[D];
+    T an[D];
+};
+
+template <int D, typename T>
+__device__ __forceinline__ BandRef<D, T> fetch_band(int b, const int* bref, const T* ban) {
+    BandRef<D, T> r;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        r.ref[a] = bref[(long long)b * D + a];
+        r.an[a] = ban[(long long)b * D + a];
+    }
+    return r;
+}
+
+template <int D, typename T, bool CG>
+__device__ __forceinline__ void extend_apply(int b, const BandRef<D, T>& br, const int* bidx,
+                                             typename V2<T>::t* res, const typename V2<T>::t* bin,
+                                             typename V2<T>::t* bout, T cfl, bool first, bool last) {
+    typedef typename V2<T>::t T2;
+    T2 v, u[D];
+    v.x = 0;
+    v.y = 0;
+    if (!first) v = ldx<CG>(bin + b);
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        u[a].x = 0;
+        u[a].y = 0;
+        int ref = br.ref[a];
+        if (ref >= 0) {
+            if (!first) u[a] = ldx<CG>(bin + ref);
+        } else if (ref <= -2) {
+            u[a] = ldx<CG>(res + (-(long long)ref - 2));
+        }
     }
     T ax = 0, ay = 0;
 #pragma unroll
     for (int a = 0; a < D; a++) {
-        int ref = bref[(long long)b * D + a];
-        if (ref == -1) continue;
-        T2 u;
-        if (ref >= 0) {
-            if (first) {
-                u.x = 0;
-                u.y = 0;
-            } else {
-                u = ldx<CG>(bin + ref);
-            }
-        } else {
-            u = ldx<CG>(res + (-(long long)ref - 2));
-        }
-        T an = ban[(long long)b * D + a];
-        ax += an * (v.x - u.x);
-        ay += an * (v.y - u.y);
+        if (br.ref[a] == -1) continue;
+        ax += br.an[a] * (v.x - u[a].x);
+        ay += br.an[a] * (v.y - u[a].y);
     }
     T2 nv;
     nv.x = v.x - cfl * ax;
@@ -263,19 +401,38 @@ __device__ __forceinline__ void extend_node(int b, const int* bidx, const int* b
         bout[b] = nv;
 }
 
+template <int D, typename T, bool CG>
+__device__ __forceinline__ void extend_node(int b, const int* bidx, const int* bref, const T* ban,
+                                            typename V2<T>::t* res, const typename V2<T>::t* bin,
+                                            typename V2<T>::t* bout, T cfl, bool first, bool last) {
+    BandRef<D, T> br = fetch_band<D, T>(b, bref, ban);
+    extend_apply<D, T, CG>(b, br, bidx, res, bin, bout, cfl, first, last);
+}
+
 __device__ __forceinline__ bool valid_for(int8_t rule, int8_t t) {
     return rule == T_IN ? t == T_IN : (t == T_GHOST || t == T_BAND);
 }
 
-// boundary-aware full weighting at the coarse node of list position t (Eqs.
-// Fstencil, Fstencilgen, Fig. Neigh); also zeroes the coarse error there
-template <int D, typename T, bool CG>
-__device__ __forceinline__ void restrict_node(int t, const Lists& ls, const int8_t* ctype, int cn,
-                                              const int8_t* ftype, int fn, const typename V2<T>::t* fres,
-                                              typename V2<T>::t* crhs, typename V2<T>::t* cx) {
-    typedef typename V2<T>::t T2;
+// The fixed part of the boundary-aware full weighting (Eqs. Fstencil,
+// Fstencilgen, Fig. Neigh) at coarse node I: the fine twin f, the per-axis
+// mirrored 1-D weights, the members that hold a value of the rule's kind
+// (bit kk), and the weight moved to the centre (the centre's own plus that of
+// every member without a value), summed in member order.
+template <int D, typename T>
+struct RestrictGeo {
+    long long I, f;
+    T w1[3][3];
+    unsigned valid;
+    T wc;
+};
+
+template <int D, typename T>
+__device__ __forceinline__ RestrictGeo<D, T> fetch_restrict(int t, const Lists& ls, const int8_t* ctype, int cn,
+                                                            const int8_t* ftype, int fn) {
+    RestrictGeo<D, T> g;
     int kind, gi;
-    long long I = list_node(ls, t, kind, gi);
+    g.I = list_node(ls, t, kind, gi);
+    const long long I = g.I;
     int8_t rule = ctype[I];
     int ii[3] = {0, 0, 0};
     ii[0] = (int)(I % cn);
@@ -285,7 +442,7 @@ __device__ __forceinline__ void restrict_node(int t, const Lists& ls, const int8
     long long f = 0;
 #pragma unroll
     for (int a = 0; a < D; a++) f += 2LL * ii[a] * fst[a];
-    T w1[3][3];
+    g.f = f;
 #pragma unroll
     for (int a = 0; a < D; a++) {
         bool vl = ii[a] > 0 && valid_for(rule, ftype[f - fst[a]]);
@@ -298,90 +455,179 @@ __device__ __forceinline__ void restrict_node(int t, const Lists& ls, const int8
         } else if (!vl && !vr) {
             l = 0; m = 4; r = 0;
         }
-        w1[a][0] = l / (T)4;
-        w1[a][1] = m / (T)4;
-        w1[a][2] = r / (T)4;
+        g.w1[a][0] = l / (T)4;
+        g.w1[a][1] = m / (T)4;
+        g.w1[a][2] = r / (T)4;
     }
     const int K = D == 2 ? 9 : 27;
-    T as = 0, ac = 0, wc = 0;
+    g.valid = 0;
+    g.wc = 0;
 #pragma unroll
     for (int kk = 0; kk < K; kk++) {
         const int k0 = kk % 3 - 1, k1 = (kk / 3) % 3 - 1, k2 = kk / 9 - 1;
-        T w = w1[0][k0 + 1] * w1[1][k1 + 1];
-        if (D == 3) w = w * w1[2][k2 + 1];
+        T w = g.w1[0][k0 + 1] * g.w1[1][k1 + 1];
+        if (D == 3) w = w * g.w1[2][k2 + 1];
         if (w == (T)0) continue;
         bool centre = k0 == 0 && k1 == 0 && (D == 2 || k2 == 0);
-        if (centre) {
-            wc += w;
-            continue;
-        }
         long long node = f + k0 * fst[0] + k1 * fst[1];
         if (D == 3) node += k2 * fst[2];
-        if (!valid_for(rule, ftype[node])) {
-            wc += w;
-            continue;
-        }
-        T2 v = ldx<CG>(fres + node);
-        as += w * v.x;
-        ac += w * v.y;
+        if (centre || !valid_for(rule, ftype[node]))
+            g.wc += w;
+        else
+            g.valid |= 1u << kk;
     }
-    T2 vc = ldx<CG>(fres + f);
+    return g;
+}
+
+// the weighting applied to the fine defect; also zeroes the coarse error
+template <int D, typename T, bool CG>
+__device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int fn, const typename V2<T>::t* fres,
+                                               typename V2<T>::t* crhs, typename V2<T>::t* cx) {
+    typedef typename V2<T>::t T2;
+    const long long fst[3] = {1, fn, (long long)fn * fn};
+    const int K = D == 2 ? 9 : 27;
+    T as = 0, ac = 0;
+    T2 vc = ldx<CG>(fres + g.f);
+#pragma unroll
+    for (int c0 = 0; c0 < K; c0 += 9) {
+        T2 v[9];
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            const int kk = c0 + j;
+            const int k0 = kk % 3 - 1, k1 = (kk / 3) % 3 - 1, k2 = kk / 9 - 1;
+            long long node = g.f + k0 * fst[0] + k1 * fst[1];
+            if (D == 3) node += k2 * fst[2];
+            v[j].x = 0;
+            v[j].y = 0;
+            if ((g.valid >> kk) & 1u) v[j] = ldx<CG>(fres + node);
+        }
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            const int kk = c0 + j;
+            if (!((g.valid >> kk) & 1u)) continue;
+            const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+            T w = g.w1[0][k0] * g.w1[1][k1];
+            if (D == 3) w = w * g.w1[2][k2];
+            as += w * v[j].x;
+            ac += w * v[j].y;
+        }
+    }
     T2 out;
-    out.x = as + wc * vc.x;
-    out.y = ac + wc * vc.y;
-    crhs[I] = out;
+    out.x = as + g.wc * vc.x;
+    out.y = ac + g.wc * vc.y;
+    crhs[g.I] = out;
     T2 z;
     z.x = 0;
     z.y = 0;
-    cx[I] = z;  // the coarse-grid error starts from zero
+    cx[g.I] = z;  // the coarse-grid error starts from zero
 }
 
-// (bi/tri)linear interpolation of the coarse error to the fine active node of
-// list position t, renormalised over the coarse active nodes (Sec. 3.5.3)
 template <int D, typename T, bool CG>
-__device__ __forceinline__ void prolong_node(int t, const Lists& ls, const int8_t* ctype, int cn,
-                                             const typename V2<T>::t* cx, int fn, typename V2<T>::t* fx) {
-    typedef typename V2<T>::t T2;
+__device__ __forceinline__ void restrict_node(int t, const Lists& ls, const int8_t* ctype, int cn,
+                                              const int8_t* ftype, int fn, const typename V2<T>::t* fres,
+                                              typename V2<T>::t* crhs, typename V2<T>::t* cx) {
+    RestrictGeo<D, T> g = fetch_restrict<D, T>(t, ls, ctype, cn, ftype, fn);
+    restrict_apply<D, T, CG>(g, fn, fres, crhs, cx);
+}
+
+// The fixed part of the (bi/tri)linear interpolation to fine active node i
+// (Sec. 3.5.3): the coarse corners that are active (bit cc) with their nodes,
+// and the sum of their weights, renormalising over the active corners.
+template <int D, typename T>
+struct ProlongGeo {
+    long long i;
+    long long node[1 << D];
+    unsigned use;
+    T ws;
+};
+
+template <int D, typename T>
+__device__ __forceinline__ T corner(const int* ii, int cc, const long long* cst, long long& node, bool& dup) {
+    node = 0;
+    T w = 1;
+    dup = false;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        int pick = (cc >> a) & 1;
+        int lo = ii[a] >> 1, hi = (ii[a] + 1) >> 1;
+        if (lo == hi) {
+            if (pick) dup = true;
+            node += lo * cst[a];
+        } else {
+            w *= (T)0.5;
+            node += (pick ? hi : lo) * cst[a];
+        }
+    }
+    return w;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ ProlongGeo<D, T> fetch_prolong(int t, const Lists& ls, const int8_t* ctype, int cn,
+                                                          int fn) {
+    ProlongGeo<D, T> g;
     int kind, gi;
-    long long i = list_node(ls, t, kind, gi);
+    g.i = list_node(ls, t, kind, gi);
+    const long long i = g.i;
     int ii[3] = {0, 0, 0};
     ii[0] = (int)(i % fn);
     ii[1] = (int)((i / fn) % fn);
     if (D == 3) ii[2] = (int)(i / ((long long)fn * fn));
     const long long cst[3] = {1, cn, (long long)cn * cn};
-    T ws = 0, as = 0, ac = 0;
+    g.use = 0;
+    g.ws = 0;
     const int NC = 1 << D;
 #pragma unroll
     for (int cc = 0; cc < NC; cc++) {
-        long long node = 0;
-        T w = 1;
-        bool dup = false;
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            int pick = (cc >> a) & 1;
-            int lo = ii[a] >> 1, hi = (ii[a] + 1) >> 1;
-            if (lo == hi) {
-                if (pick) dup = true;
-                node += lo * cst[a];
-            } else {
-                w *= (T)0.5;
-                node += (pick ? hi : lo) * cst[a];
-            }
-        }
+        bool dup;
+        T w = corner<D, T>(ii, cc, cst, g.node[cc], dup);
         if (dup) continue;
-        int8_t tc = ctype[node];
+        int8_t tc = ctype[g.node[cc]];
         if (tc != T_IN && tc != T_GHOST) continue;
-        T2 v = ldx<CG>(cx + node);
-        ws += w;
-        as += w * v.x;
-        ac += w * v.y;
+        g.use |= 1u << cc;
+        g.ws += w;
     }
-    if (ws > (T)0) {
-        T2 xf = ldx<CG>(fx + i);
-        xf.x += as / ws;
-        xf.y += ac / ws;
-        fx[i] = xf;
+    return g;
+}
+
+template <int D, typename T, bool CG>
+__device__ __forceinline__ void prolong_apply(const ProlongGeo<D, T>& g, int fn, const typename V2<T>::t* cx,
+                                              typename V2<T>::t* fx) {
+    typedef typename V2<T>::t T2;
+    if (!(g.ws > (T)0)) return;
+    const int NC = 1 << D;
+    int ii[3] = {0, 0, 0};
+    ii[0] = (int)(g.i % fn);
+    ii[1] = (int)((g.i / fn) % fn);
+    if (D == 3) ii[2] = (int)(g.i / ((long long)fn * fn));
+    T2 v[1 << D];
+#pragma unroll
+    for (int cc = 0; cc < NC; cc++) {
+        v[cc].x = 0;
+        v[cc].y = 0;
+        if ((g.use >> cc) & 1u) v[cc] = ldx<CG>(cx + g.node[cc]);
     }
+    T2 xf = ldx<CG>(fx + g.i);
+    T as = 0, ac = 0;
+    const long long cst0[3] = {0, 0, 0};
+#pragma unroll
+    for (int cc = 0; cc < NC; cc++) {
+        if (!((g.use >> cc) & 1u)) continue;
+        long long unused;
+        bool dup;
+        T w = corner<D, T>(ii, cc, cst0, unused, dup);
+        as += w * v[cc].x;
+        ac += w * v[cc].y;
+    }
+    xf.x += as / g.ws;
+    xf.y += ac / g.ws;
+    fx[g.i] = xf;
+}
+
+template <int D, typename T, bool CG>
+__device__ __forceinline__ void prolong_node(int t, const Lists& ls, const int8_t* ctype, int cn,
+                                             const typename V2<T>::t* cx, int fn, typename V2<T>::t* fx) {
+    ProlongGeo<D, T> g = fetch_prolong<D, T>(t, ls, ctype, cn, fn);
+    prolong_apply<D, T, CG>(g, fn, cx, fx);
 }
 
 }  // namespace stages

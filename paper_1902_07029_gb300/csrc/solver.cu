@@ -92,8 +92,9 @@ struct sulf_domain {
     int newton_last = 0, cycles_last = 0;
     long long newton_total = 0, cycles_total = 0, steps_total = 0, launches = 0;
     double last_rho = 0, last_fnorm = 0;
-    // profiling of the finest-level inside relaxation
-    bool prof = false;
+    // profiling of the finest-level inside relaxation: 0 off, 1 the first
+    // finest-level sweep of every cycle, 2 every finest-level sweep
+    int prof = 0;
     std::vector<cudaEvent_t> evpool;
     size_t evused = 0;
     double prof_ms = 0;
@@ -104,7 +105,7 @@ struct sulf_domain {
         cudaGraphExec_t exec = nullptr;
         double dt = 0;
         sulf_solver sv{};
-        bool prof = false;
+        int prof = 0;
         cudaStream_t stream = nullptr;
         long long kernels = 0;
         size_t ev0 = 0, ev1 = 0;
@@ -132,6 +133,7 @@ sulf_solver default_solver() {
     s.smoother = 0;
     s.graphs = 1;
     s.fuse_below = 1500;
+    s.pdl = 1;
     return s;
 }
 
@@ -278,13 +280,16 @@ template <int D, typename T>
 struct MG {
     sulf_domain* d;
     LevelVec<T>* V;
+    int fine_sweeps = 0;  // finest-level sweeps issued so far in this cycle
 
     int relax(int l) {
         const LevelGeo& G = d->geo[l];
         Coef<T> c = make_coef<T>(d, l);
         bool pw = d->solver.smoother == 1;
+        const bool timed_sweep = l == 0 && (d->prof == 2 || (d->prof == 1 && fine_sweeps == 0));
+        if (l == 0) fine_sweeps++;
         for (int colour = 0; colour < 2; colour++) {
-            bool timed = d->prof && l == 0;
+            bool timed = timed_sweep;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             // inside stream capture a plain record only adds a dependency; the
             // external flag makes it an event-record node of the graph
@@ -386,7 +391,20 @@ int cycle_body(sulf_domain* d) {
     return SULF_OK;
 }
 
-bool same_solver(const sulf_solver& a, const sulf_solver& b) { return memcmp(&a, &b, sizeof a) == 0; }
+bool same_solver(const sulf_solver& a, const sulf_solver& b) {
+    return a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.cycle == b.cycle && a.max_newton == b.max_newton &&
+           a.max_cycles == b.max_cycles && a.ghost_sweeps == b.ghost_sweeps && a.newton_tol == b.newton_tol &&
+           a.lin_rtol == b.lin_rtol && a.tau_s == b.tau_s && a.precision == b.precision && a.smoother == b.smoother &&
+           a.graphs == b.graphs && a.fuse_below == b.fuse_below && a.pdl == b.pdl;
+}
+
+// launches of the calling thread use programmatic dependent launch while the
+// scope lives
+struct PdlScope {
+    bool old;
+    explicit PdlScope(bool on) : old(launch_pdl()) { set_launch_pdl(on); }
+    ~PdlScope() { set_launch_pdl(old); }
+};
 
 // run one cycle: replay the captured graph (capturing it first if needed), or
 // launch the kernels directly
@@ -668,7 +686,8 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
     sulf_solver v = s ? *s : default_solver();
     if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || (v.cycle != 1 && v.cycle != 2) || v.max_newton < 1 ||
         v.max_cycles < 1 || v.ghost_sweeps < 1 || !(v.tau_s > 0 && v.tau_s < 1) || !(v.newton_tol > 0) ||
-        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1) || v.fuse_below < 0)
+        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1) || v.fuse_below < 0 ||
+        (v.pdl != 0 && v.pdl != 1))
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
     if (v.precision == 1) return ensure32(h);
@@ -685,6 +704,7 @@ int sulf_set_stream(sulf_handle h, void* stream) {
 int sulf_step(sulf_handle h, double dt, int nsteps) {
     if (!valid(h) || !(dt > 0) || nsteps < 0) return sulf_fail(SULF_EINVAL, "invalid arguments");
     h->dt = dt;
+    PdlScope pdl(h->solver.pdl != 0);
     for (int k = 0; k < nsteps; k++) {
         int rc = h->dim == 2 ? cn_step<2>(h) : cn_step<3>(h);
         if (rc) return rc;
@@ -753,7 +773,8 @@ int sulf_get_stats(sulf_handle h, sulf_stats* o) {
 int sulf_set_profiling(sulf_handle h, int on) {
     if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
     SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    h->prof = on != 0;
+    if (on < 0 || on > 2) return sulf_fail(SULF_EINVAL, "profiling mode must be 0, 1 or 2");
+    h->prof = on;
     h->prof_ms = 0;
     h->prof_n = 0;
     return SULF_OK;
@@ -961,6 +982,7 @@ int sulf_dbg_cycles(sulf_handle h, double dt, const double* Wc0, const double* r
     bool nonzero = false;
     for (double v : x0) nonzero |= v != 0.0;
     if (nonzero) return sulf_fail(SULF_EINVAL, "sulf_dbg_cycles starts from x = 0");
+    PdlScope pdl(h->solver.pdl != 0);
     int nc = h->dim == 2 ? linear_solve<2>(h, 1.0, ncycles, 0.0, rnorms) : linear_solve<3>(h, 1.0, ncycles, 0.0, rnorms);
     if (nc < 0) return nc;
     return dbg_copy_out(h, 0, h->v64[0].x, x, false);

@@ -17,6 +17,7 @@
 
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/sulfmg.h"
@@ -175,6 +176,39 @@ template <typename T>
 int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, cudaStream_t s);
 template <int D, typename T>
 int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, cudaStream_t s);
+
+// Programmatic dependent launch.  Every kernel of the Newton and multigrid
+// path starts with pdl_enter(): griddepcontrol.wait blocks until the previous
+// kernel on the stream has completed and its writes are visible (a no-op when
+// the kernel was launched without the attribute), then launch_dependents lets
+// the next kernel's CTAs be scheduled while this one runs.  The next grid
+// therefore waits, resident, for this one instead of paying its launch latency
+// after it; at most two grids of a stream are in flight.  All threads pass the
+// wait before any global access.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launches made by the calling thread use the attribute while on (solver.cu
+// switches it per call from sulf_solver::pdl)
+void set_launch_pdl(bool on);
+bool launch_pdl();
+
+template <typename... P, typename... A>
+inline void launch_k(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = launch_pdl() ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // read-only views of a handle (solver.cu)
 const LevelGeo* handle_fine_geo(sulf_handle h);

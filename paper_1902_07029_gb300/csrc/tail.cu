@@ -101,6 +101,7 @@ __device__ void tail_relax(const TailLevel<T>& v, const TailParams& pr, int tid,
 
 template <int D, typename T>
 __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T>* __restrict__ lv, TailParams pr) {
+    pdl_enter();
     typedef typename V2<T>::t T2;
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -224,7 +225,7 @@ TailParams make_params(int l0, int L, const sulf_solver& sv, int D) {
 
 template <int D, typename T>
 int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, cudaStream_t s) {
-    k_tail<D, T><<<1, kTailThreads, 0, s>>>((const TailLevel<T>*)dev_desc, make_params(l0, L, sv, D));
+    launch_k(k_tail<D, T>, 1, kTailThreads, 0, s, (const TailLevel<T>*)dev_desc, make_params(l0, L, sv, D));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sulf_fail_cuda(e, "fused coarse-level cycle launch");
     return SULF_OK;

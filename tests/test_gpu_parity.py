@@ -154,7 +154,7 @@ def test_steps_fp64(sulfmg, oracle_mod, name, mk):
 def test_steps_unfused_and_w_cycle(sulfmg, oracle_mod, name, mk):
     """every level as separate kernels without graphs, and the paper's W-cycle"""
     phi, dim, N, cN, dt, nsteps = mk()
-    for kw in (dict(fuse_below=0, graphs=0), dict(cycle=2, nu1=2, nu2=1)):
+    for kw in (dict(fuse_below=0, graphs=0), dict(cycle=2, nu1=2, nu2=1), dict(pdl=0)):
         dom, ref = _pair(sulfmg, oracle_mod, phi, dim, N, cN)
         dom.set_solver(**kw)
         ref.set_solver(**{k: v for k, v in kw.items() if k in ("cycle", "nu1", "nu2")})
@@ -179,3 +179,25 @@ def test_steps_mixed(sulfmg, oracle_mod, name, mk):
     act = (rt == 1) | (rt == 2)
     _close(s[act], rs[act], MIXED_TOL)
     _close(c[act], rc[act], MIXED_TOL)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name,mk", [RUNS[2], RUNS[4]], ids=[RUNS[2][0], RUNS[4][0]])
+def test_dependent_launch_is_bitwise_neutral(sulfmg, name, mk, precision):
+    """programmatic dependent launch only changes when a kernel is scheduled,
+    never what it computes: the state after a few steps is bit for bit the
+    same with it on and off, with and without graphs"""
+    phi, dim, N, cN, dt, nsteps = mk()
+    out = []
+    for kw in (dict(pdl=1), dict(pdl=0), dict(pdl=1, graphs=0, fuse_below=0)):
+        dom = sulfmg.Domain(phi, dim, (-1.0, 1.0), N, coarsest_N=cN)
+        dom.set_model(workloads.PAPER_MODEL)
+        dom.set_solver(precision=precision, **kw)
+        dom.step(dt, nsteps)
+        out.append(dom.get_state()[:2])
+        dom.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    # launched one by one, every level as separate kernels: same up to the
+    # summation order of the coarsest solve
+    for a, b in zip(out[0], out[2]):
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(b)), 1.0)

@@ -94,11 +94,15 @@ def paper_test2(N: int, lo: float = -2.0, hi: float = 2.0) -> np.ndarray:
 
 
 # The workloads the library is measured on.  N counts intervals per axis, so
-# "1025^2 nodes" is N = 1024.  dt = h on [-1, 1] means dt = 2 / N.
+# "1025^2 nodes" is N = 1024.  dt = h on [-1, 1] means dt = 2 / N.  coarsest is
+# the N of the coarsest multigrid level: 4 in 3-D keeps the dense direct solve
+# there at 2 x 81 unknowns (a 9^3 coarsest box of the rounded box has ~600
+# active nodes, whose dense FP64 factorisation per Newton iteration costs more
+# than the cycles).
 WORKLOADS = {
-    "disk65": dict(dim=2, N=64, geometry="disk", steps=10, precision="fp64"),
-    "star1025": dict(dim=2, N=1024, geometry="star", steps=200, precision="fp64"),
-    "rbox257": dict(dim=3, N=256, geometry="rounded_box", steps=50, precision="fp64"),
+    "disk65": dict(dim=2, N=64, coarsest=8, geometry="disk", steps=10, precision="fp64"),
+    "star1025": dict(dim=2, N=1024, coarsest=8, geometry="star", steps=200, precision="fp64"),
+    "rbox257": dict(dim=3, N=256, coarsest=4, geometry="rounded_box", steps=50, precision="fp64"),
 }
 
 
