@@ -53,6 +53,9 @@ RELAX_FLOPS_2D = 22
 RELAX_BYTES_3D = {"fp64": 176, "mixed": 88}
 RELAX_FLOPS_3D = 30
 RELAX_BYTES = {2: RELAX_BYTES_2D, 3: RELAX_BYTES_3D}
+# DRAM bytes (read + write) of one finest-level relaxation launch from an ncu
+# capture of the current kernel (cold cache), per workload and precision
+RELAX_TRAFFIC = {("star1025", "fp64"): (31.31e6 + 10.5e3, "profiles/relax_inside_fp64_star1025.md")}
 RELAX_FLOPS = {2: RELAX_FLOPS_2D, 3: RELAX_FLOPS_3D}
 
 
@@ -307,7 +310,9 @@ def run_gpu(args):
         hbm = peaks.get("hbm_gbs")
         roofline = {"kernel": "k_relax_inside (finest level, one colour)", "bound": "hbm",
                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": None,
+                    "frac": (achieved / hbm) if (achieved and hbm) else None,
+                    "traffic": RELAX_TRAFFIC.get((args.workload, args.precision), (None,))[0],
+                    "traffic_source": RELAX_TRAFFIC.get((args.workload, args.precision), (None, None))[1],
                     "avg_launch_us": avg_us, "launches": relax_n,
                     "algorithmic": f"{RELAX_BYTES[dim][args.precision]} B and {RELAX_FLOPS[dim]} flop per "
                                    f"inside-node update; {nodes_per_launch:.0f} nodes per launch",
@@ -409,7 +414,8 @@ def d_model(d, doms, sizes, params):
 def run_serve(args):
     """Poisson arrivals (seed 5) of jobs: 70% 2-D random stars with
     N in {256, 512, 1024, 2048}, 30% 3-D random rounded boxes with N in
-    {64, 128}; 20-100 CN steps each, mixed precision, HBM budget 150 GB."""
+    {64, 128}; 20-100 CN steps each (dt = h in 2-D, h/2 at 129^3, h/4 at
+    65^3), mixed precision, HBM budget 150 GB."""
     import paper_1902_07029_gb300 as pkg
 
     pkg.build()
@@ -429,7 +435,9 @@ def run_serve(args):
             dim, cN = 3, 4
             m = list(workloads.PAPER_MODEL)
         nsteps = int(rng.integers(20, 101))
-        dt = 2.0 / N if dim == 2 else 0.5 * 2.0 / N
+        # 3-D: dt = h/2 at 129^3; at 65^3 some rounded boxes have no discrete
+        # solution at dt = h/2 (as the 65^2 disk at dt = h), so dt = h/4 there
+        dt = 2.0 / N if dim == 2 else (0.5 if N >= 128 else 0.25) * 2.0 / N
         jobs.append((phi, dim, N, cN, m, dt, nsteps))
     rate = args.rate
     gaps = rng.exponential(1.0 / rate, size=len(jobs))

@@ -20,8 +20,9 @@
  *   - Every int-returning call returns SULF_OK (0) or a negative error code and
  *     records a message readable with sulf_last_error() (per thread).
  *   - Calls on one handle must not overlap; different handles are independent.
- *   - Device work is issued on the handle's stream (sulf_set_stream); calls
- *     that return host data synchronise that stream.
+ *   - Device work is issued on the handle's stream (sulf_set_stream).  Every
+ *     call returns with the handle's device work complete (also on error), so
+ *     a handle may move to another stream between calls without waiting.
  */
 #ifndef SULFMG_H
 #define SULFMG_H
@@ -69,8 +70,9 @@ typedef struct {
                  replayed; 0 = kernels launched one by one               default 1
    fuse_below    the first level with at most this many active nodes and all
                  coarser ones run as one single-CTA kernel per V-cycle;
-                 0 = every level as separate kernels (W-cycles always are)
-                                                                         default 1500
+                 0 = every level as separate kernels (W-cycles always are);
+                 -1 = automatic: 600 for FP64, 2000 for mixed precision
+                 (the fused kernel runs on one SM)                       default -1
    pdl           1 = kernels of a step are launched as programmatic dependent
                  launches (each may be scheduled while its predecessor runs and
                  waits on the device for its completion); 0 = plain stream

@@ -8,6 +8,9 @@
 // per node the edge pair (g, e) toward each +axis neighbour and the inverse of
 // the 2x2 diagonal block, per ghost its c row.  Each relaxation is then a
 // handful of loads and fused multiply-adds per node.
+#include <atomic>
+#include <mutex>
+
 #include "mg_stages.cuh"
 
 namespace sulf {
@@ -21,16 +24,54 @@ using stages::make_lists;
 
 namespace {
 thread_local bool t_pdl = false;
+thread_local std::string t_launch_err;
 }  // namespace
 
 void set_launch_pdl(bool on) { t_pdl = on; }
 bool launch_pdl() { return t_pdl; }
 
+void note_launch_error(cudaError_t e, unsigned grid, unsigned block, size_t smem) {
+    if (!t_launch_err.empty()) return;
+    t_launch_err = std::string(cudaGetErrorString(e)) + " (grid " + std::to_string(grid) + ", block " +
+                   std::to_string(block) + ", smem " + std::to_string(smem) + (t_pdl ? ", dependent launch)" : ")");
+}
+
+std::string take_launch_error() {
+    std::string m;
+    m.swap(t_launch_err);
+    return m;
+}
+
 namespace {
 
 constexpr int kT = 256;
 
-inline unsigned nblk(long long n, int t = kT) { return (unsigned)((n + t - 1) / t); }
+// Launch shape of a one-thread-per-node kernel over n nodes.  On this GPU one
+// SM issues two FP64 lanes per clock, so a short list in 256-thread CTAs would
+// run on a few SMs at their FP64 rate: CTAs shrink (down to one warp) until the
+// list covers every SM, and grow to kT threads only for long lists.
+int sm_count() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int v = (dev >= 0 && dev < 64) ? cached[dev].load(std::memory_order_relaxed) : 0;
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    if (dev >= 0 && dev < 64) cached[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
+inline unsigned block_for(long long n) {
+    const long long sms = sm_count();
+    long long per = (n + sms - 1) / sms;
+    long long b = (per + 31) / 32 * 32;
+    return (unsigned)(b < 32 ? 32 : (b > kT ? kT : b));
+}
+
+inline unsigned grid_for(long long n) {
+    const unsigned b = block_for(n);
+    return (unsigned)((n + b - 1) / b);
+}
 
 // max over the block of non-negative doubles held as bit patterns (NaN, whose
 // pattern exceeds +inf, propagates), then one atomicMax per block
@@ -176,18 +217,20 @@ __global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict
     // the previous kernel is still running
     stages::GhostRow<D, T> row;
     typename V2<T>::t q;
+    T qinv;
     int src[stages::kGhostSrc];
     const bool hoist = D == 2 && !first;
     if (gi < ng) {
         row = stages::fetch_ghost_row<D, T>(gi, gidx[gi], gm, gw);
         q = gc[gi];
+        qinv = (T)1 / q.y;
         if constexpr (D == 2)
             if (hoist) stages::fetch_ghost_src<D, T>(row, gpos, st1, src);
     }
     pdl_enter();
     if (gi >= ng) return;
-    stages::ghost_pass_apply<D, T, false>(gi, row, hoist ? src : nullptr, q, gpos, rhs, x, sin, sout, st1, st2,
-                                          c.tau, first != 0, last != 0);
+    stages::ghost_pass_apply<D, T, false>(gi, row, hoist ? src : nullptr, q, qinv, gpos, rhs, x, sin, sout, st1,
+                                          st2, c.tau, first != 0, last != 0);
 }
 
 template <typename T>
@@ -683,7 +726,7 @@ int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cuda
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
-    launch_k(k_coefs<D, T>, nblk(tot), kT, 0, s, ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa, V.Pb, V.Ia, V.Ib,
+    launch_k(k_coefs<D, T>, grid_for(tot), block_for(tot), 0, s, ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa, V.Pb, V.Ia, V.Ib,
                                             V.gc, c);
     return 1;
 }
@@ -696,9 +739,9 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
     (void)c;
     CoefPtr<D, T> cf = coef_ptr<D, T>(V);
     if (pointwise)
-        launch_k(k_relax_inside<D, T, true>, nblk(cnt), kT, 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, true>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
     else
-        launch_k(k_relax_inside<D, T, false>, nblk(cnt), kT, 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, false>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
     return 1;
 }
 
@@ -711,12 +754,12 @@ int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
         bool first = p == 0, last = p == passes - 1 && passes > 1;
         const T* sin = first ? nullptr : V.gbuf[(p - 1) & 1];
         T* sout = V.gbuf[p & 1];
-        launch_k(k_ghost_pass<D, T>, nblk(L.ng), kT, 0, s, L.ng, L.gidx, L.gpos, L.gm, gw, V.gc, V.rhs, V.x, sin, sout,
+        launch_k(k_ghost_pass<D, T>, grid_for(L.ng), block_for(L.ng), 0, s, L.ng, L.gidx, L.gpos, L.gm, gw, V.gc, V.rhs, V.x, sin, sout,
                                                       L.st[1], L.st[2], c, first, last);
         n++;
     }
     if (passes == 1) {
-        launch_k(k_ghost_scatter<T>, nblk(L.ng), kT, 0, s, L.ng, L.gidx, V.gbuf[0], V.x);
+        launch_k(k_ghost_scatter<T>, grid_for(L.ng), block_for(L.ng), 0, s, L.ng, L.gidx, V.gbuf[0], V.x);
         n++;
     }
     return n;
@@ -730,7 +773,7 @@ int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, u
     if (tot == 0) return 0;
     (void)c;
     const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
-    launch_k(k_residual<D, T>, nblk(tot), kT, 0, s, ls, L.gm, gw, coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2],
+    launch_k(k_residual<D, T>, grid_for(tot), block_for(tot), 0, s, ls, L.gm, gw, coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2],
                                                norm);
     return 1;
 }
@@ -742,7 +785,7 @@ int launch_extend(const LevelGeo& L, const LevelVec<T>& V, int steps, cudaStream
     T cfl = D == 2 ? (T)0.5 : (T)(1.0 / 3.0);
     for (int k = 0; k < steps; k++) {
         bool first = k == 0, last = k == steps - 1;
-        launch_k(k_extend_step<D, T>, nblk(L.nb), kT, 0, s, L.nb, L.bidx, L.bref, an, V.res, V.bbuf[(k + 1) & 1],
+        launch_k(k_extend_step<D, T>, grid_for(L.nb), block_for(L.nb), 0, s, L.nb, L.bidx, L.bref, an, V.res, V.bbuf[(k + 1) & 1],
                                                        V.bbuf[k & 1], cfl, first, last);
     }
     return steps;
@@ -753,7 +796,7 @@ int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C,
                     cudaStream_t s) {
     Lists ls = make_lists(C);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_restrict<D, T>, nblk(tot), kT, 0, s, ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs, CV.x);
+    launch_k(k_restrict<D, T>, grid_for(tot), block_for(tot), 0, s, ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs, CV.x);
     return 1;
 }
 
@@ -762,7 +805,7 @@ int launch_prolong(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, 
                    cudaStream_t s) {
     Lists ls = make_lists(F);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_prolong<D, T>, nblk(tot), kT, 0, s, ls, C.type, C.n, CV.x, F.n, FV.x);
+    launch_k(k_prolong<D, T>, grid_for(tot), block_for(tot), 0, s, ls, C.type, C.n, CV.x, F.n, FV.x);
     return 1;
 }
 
@@ -771,7 +814,7 @@ int launch_inject(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, c
                   cudaStream_t s) {
     Lists ls = make_lists(C);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_inject<D, T>, nblk(tot), kT, 0, s, ls, C.n, F.type, F.n, FV.Wc, CV.Wc);
+    launch_k(k_inject<D, T>, grid_for(tot), block_for(tot), 0, s, ls, C.n, F.type, F.n, FV.Wc, CV.Wc);
     return 1;
 }
 
@@ -783,9 +826,23 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
     const size_t m = 2 * (size_t)L.nact;
     const size_t piv_bytes = sizeof(T) * (m + 1);
     const size_t smem_full = 2 * m * m * sizeof(T) + piv_bytes;
-    if (smem_full <= 220 * 1024) {
+    constexpr size_t kMaxSmem = 220 * 1024;
+    if (smem_full <= kMaxSmem) {
         auto kern = k_coarsest_factor<D, T, true>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_full);
+        // The limit is a per-function attribute shared by every thread: set it
+        // once to the largest size ever used (a per-launch value would race
+        // with other threads' launches of different sizes).
+        static std::mutex mu;
+        static bool raised[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            if (dev < 0 || dev >= 64 || !raised[dev]) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+                if (dev >= 0 && dev < 64) raised[dev] = true;
+            }
+        }
         launch_k(kern, 1, 1024, smem_full, s, L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw, V.Wc, of, L.st[1], L.st[2],
                                         c, V.A, V.Ainv, singular);
     } else {
@@ -807,7 +864,7 @@ template <int D>
 int launch_old_time(const LevelGeo& L, const double2* Wn, double2* G, const FConst& fc, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_old_time<D>, nblk(tot), kT, 0, s, ls, Wn, G, make_offs<D>(L.st[1], L.st[2]), fc);
+    launch_k(k_old_time<D>, grid_for(tot), block_for(tot), 0, s, ls, Wn, G, make_offs<D>(L.st[1], L.st[2]), fc);
     return 1;
 }
 
@@ -816,7 +873,7 @@ int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, doubl
                     unsigned long long* norm, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_newton_F<D>, nblk(tot), kT, 0, s, ls, L.gm, L.gw, W, G, F, make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2],
+    launch_k(k_newton_F<D>, grid_for(tot), block_for(tot), 0, s, ls, L.gm, L.gw, W, G, F, make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2],
                                             fc, norm);
     return 1;
 }
@@ -824,43 +881,43 @@ int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, doubl
 int launch_newton_update(const LevelGeo& L, double2* W, const double2* x, unsigned long long* norms, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_newton_update, nblk(tot), kT, 0, s, ls, W, x, norms);
+    launch_k(k_newton_update, grid_for(tot), block_for(tot), 0, s, ls, W, x, norms);
     return 1;
 }
 
 int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* norm, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_norm_active, nblk(tot), kT, 0, s, ls, v, norm);
+    launch_k(k_norm_active, grid_for(tot), block_for(tot), 0, s, ls, v, norm);
     return 1;
 }
 
 int launch_to_float(const LevelGeo& L, const double2* src, float2* dst, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_to_float2, nblk(tot), kT, 0, s, ls, src, dst);
+    launch_k(k_to_float2, grid_for(tot), block_for(tot), 0, s, ls, src, dst);
     return 1;
 }
 
 int launch_accumulate(const LevelGeo& L, double2* x, const float2* e, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_accumulate, nblk(tot), kT, 0, s, ls, x, e);
+    launch_k(k_accumulate, grid_for(tot), block_for(tot), 0, s, ls, x, e);
     return 1;
 }
 
 int launch_reset_state(const LevelGeo& L, double2* W, double s0, double c0, cudaStream_t s) {
-    launch_k(k_reset_state, nblk(L.nn), kT, 0, s, L.type, L.nn, W, s0, c0);
+    launch_k(k_reset_state, grid_for(L.nn), block_for(L.nn), 0, s, L.type, L.nn, W, s0, c0);
     return 1;
 }
 
 int launch_import_state(const LevelGeo& L, double2* W, const double* sv, const double* cv, cudaStream_t s) {
-    launch_k(k_import_state, nblk(L.nn), kT, 0, s, L.type, L.nn, W, sv, cv);
+    launch_k(k_import_state, grid_for(L.nn), block_for(L.nn), 0, s, L.type, L.nn, W, sv, cv);
     return 1;
 }
 
 int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double* cv, int8_t* tv, cudaStream_t s) {
-    launch_k(k_export_state, nblk(L.nn), kT, 0, s, L.type, L.nn, W, sv, cv, tv);
+    launch_k(k_export_state, grid_for(L.nn), block_for(L.nn), 0, s, L.type, L.nn, W, sv, cv, tv);
     return 1;
 }
 

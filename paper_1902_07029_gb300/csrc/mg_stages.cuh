@@ -253,10 +253,11 @@ __device__ __forceinline__ T ghost_dot(int gi, long long g, const int8_t* gm, co
 
 // one Jacobi pass of the ghost relaxation (Eq. RelGhost) for ghost gi from its
 // fetched row: s_g += tau (r_g - row . x) from the previous pass's values,
-// then the ghost c row relaxed by its diagonal with the fresh s_g
+// then the ghost c row J^cs_gg s_g + J^cc_gg c_g = r^c_g solved for c_g with
+// the fresh s_g (q = (J^cs_gg, J^cc_gg), qinv = 1 / J^cc_gg)
 template <int D, typename T, bool CG>
 __device__ __forceinline__ void ghost_pass_apply(int gi, const GhostRow<D, T>& row, const int* src,
-                                                 typename V2<T>::t q, const int* gpos,
+                                                 typename V2<T>::t q, T qinv, const int* gpos,
                                                  const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* sin,
                                                  T* sout, long long st1, long long st2, T tau, bool first,
                                                  bool last) {
@@ -267,8 +268,7 @@ __device__ __forceinline__ void ghost_pass_apply(int gi, const GhostRow<D, T>& r
     T s_old = first ? xg.x : ldx<CG>(sin + gi);
     T2 b = ldx<CG>(rhs + g);
     T s_new = s_old + tau * (b.x - acc);
-    // q = (J^cs_gg, J^cc_gg)
-    T c_new = xg.y + (b.y - (q.x * s_new + q.y * xg.y)) / q.y;
+    T c_new = fmadd(-q.x, s_new, b.y) * qinv;
     T* xs = reinterpret_cast<T*>(x + g);
     xs[1] = c_new;
     if (last)
@@ -284,7 +284,9 @@ __device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const i
                                                 T* sout, long long st1, long long st2, T tau, bool first,
                                                 bool last) {
     GhostRow<D, T> row = fetch_ghost_row<D, T>(gi, gidx[gi], gm, gw);
-    ghost_pass_apply<D, T, CG>(gi, row, nullptr, gc[gi], gpos, rhs, x, sin, sout, st1, st2, tau, first, last);
+    typename V2<T>::t q = gc[gi];
+    ghost_pass_apply<D, T, CG>(gi, row, nullptr, q, (T)1 / q.y, gpos, rhs, x, sin, sout, st1, st2, tau, first,
+                               last);
 }
 
 // defect r = rhs - J x at node p of kind 1 (inside, coefficients k) or 2
@@ -538,7 +540,7 @@ struct ProlongGeo {
     long long i;
     long long node[1 << D];
     unsigned use;
-    T ws;
+    T ws, iws;  // sum of the active corners' weights and its reciprocal
 };
 
 template <int D, typename T>
@@ -586,6 +588,7 @@ __device__ __forceinline__ ProlongGeo<D, T> fetch_prolong(int t, const Lists& ls
         g.use |= 1u << cc;
         g.ws += w;
     }
+    g.iws = g.ws > (T)0 ? (T)1 / g.ws : (T)0;
     return g;
 }
 
@@ -618,8 +621,8 @@ __device__ __forceinline__ void prolong_apply(const ProlongGeo<D, T>& g, int fn,
         as += w * v[cc].x;
         ac += w * v[cc].y;
     }
-    xf.x += as / g.ws;
-    xf.y += ac / g.ws;
+    xf.x = fmadd(as, g.iws, xf.x);
+    xf.y = fmadd(ac, g.iws, xf.y);
     fx[g.i] = xf;
 }
 

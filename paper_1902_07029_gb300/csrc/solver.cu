@@ -22,6 +22,8 @@ int sulf_fail(int code, const std::string& msg) {
 
 int sulf_fail_cuda(cudaError_t e, const char* what) {
     g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    std::string first = sulf::take_launch_error();
+    if (!first.empty()) g_err += "; first failed launch: " + first;
     return e == cudaErrorMemoryAllocation ? SULF_ENOMEM : SULF_EDEVICE;
 }
 
@@ -106,7 +108,6 @@ struct sulf_domain {
         double dt = 0;
         sulf_solver sv{};
         int prof = 0;
-        cudaStream_t stream = nullptr;
         long long kernels = 0;
         size_t ev0 = 0, ev1 = 0;
     } graph[2];
@@ -132,7 +133,7 @@ sulf_solver default_solver() {
     s.precision = 0;
     s.smoother = 0;
     s.graphs = 1;
-    s.fuse_below = 1500;
+    s.fuse_below = -1;
     s.pdl = 1;
     return s;
 }
@@ -253,9 +254,12 @@ int read_norms(sulf_domain* d, int n) {
 
 // first level handled by the fused coarse-level cycle (-1: none)
 int tail_level(const sulf_domain* d) {
-    if (d->solver.fuse_below <= 0 || d->solver.cycle != 1) return -1;
+    // automatic threshold: the fused kernel runs on one SM, whose FP64 rate is
+    // two lanes per clock, so FP64 cycles fuse only the smallest levels
+    const int fb = d->solver.fuse_below >= 0 ? d->solver.fuse_below : (d->solver.precision == 0 ? 600 : 2000);
+    if (fb <= 0 || d->solver.cycle != 1) return -1;
     for (int l = 0; l < d->L - 1; l++)
-        if ((long long)d->geo[l].nin[0] + d->geo[l].nin[1] + d->geo[l].ng <= d->solver.fuse_below) return l;
+        if ((long long)d->geo[l].nin[0] + d->geo[l].nin[1] + d->geo[l].ng <= fb) return l;
     return -1;
 }
 
@@ -421,7 +425,9 @@ int run_cycle(sulf_domain* d) {
         return rc;
     }
     sulf_domain::CycleGraph& g = d->graph[p];
-    if (!g.exec || g.dt != d->dt || !same_solver(g.sv, d->solver) || g.prof != d->prof || g.stream != d->stream) {
+    // an instantiated graph may be launched on any stream: a new stream alone
+    // needs no recapture
+    if (!g.exec || g.dt != d->dt || !same_solver(g.sv, d->solver) || g.prof != d->prof) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
         d->evused = 0;
@@ -447,7 +453,6 @@ int run_cycle(sulf_domain* d) {
         g.dt = d->dt;
         g.sv = d->solver;
         g.prof = d->prof;
-        g.stream = d->stream;
     }
     SULF_CUDA_TRY(cudaGraphLaunch(g.exec, d->stream));
     d->launches += g.kernels;
@@ -686,7 +691,7 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
     sulf_solver v = s ? *s : default_solver();
     if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || (v.cycle != 1 && v.cycle != 2) || v.max_newton < 1 ||
         v.max_cycles < 1 || v.ghost_sweeps < 1 || !(v.tau_s > 0 && v.tau_s < 1) || !(v.newton_tol > 0) ||
-        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1) || v.fuse_below < 0 ||
+        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1) || v.fuse_below < -1 ||
         (v.pdl != 0 && v.pdl != 1))
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
@@ -696,7 +701,9 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
 
 int sulf_set_stream(sulf_handle h, void* stream) {
     if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
-    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    // every call returns with the handle's device work complete, so the old
+    // stream needs no synchronisation (it may belong to another thread that is
+    // capturing a graph on it right now)
     h->stream = stream ? (cudaStream_t)stream : h->own_stream;
     return SULF_OK;
 }
@@ -707,7 +714,10 @@ int sulf_step(sulf_handle h, double dt, int nsteps) {
     PdlScope pdl(h->solver.pdl != 0);
     for (int k = 0; k < nsteps; k++) {
         int rc = h->dim == 2 ? cn_step<2>(h) : cn_step<3>(h);
-        if (rc) return rc;
+        if (rc) {
+            cudaStreamSynchronize(h->stream);  // leave no work in flight
+            return rc;
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sulf_fail_cuda(e, "kernel launch");

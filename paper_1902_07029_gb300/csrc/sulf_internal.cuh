@@ -195,6 +195,12 @@ __device__ __forceinline__ void pdl_enter() {
 void set_launch_pdl(bool on);
 bool launch_pdl();
 
+// the first failed launch of the calling thread is remembered (a failed launch
+// inside stream capture only surfaces later, as an invalidated capture) and
+// reported with the next CUDA error
+void note_launch_error(cudaError_t e, unsigned grid, unsigned block, size_t smem);
+std::string take_launch_error();
+
 template <typename... P, typename... A>
 inline void launch_k(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A&&... args) {
     cudaLaunchConfig_t cfg = {};
@@ -207,7 +213,8 @@ inline void launch_k(void (*k)(P...), unsigned grid, unsigned block, size_t smem
     at[0].val.programmaticStreamSerializationAllowed = launch_pdl() ? 1 : 0;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+    if (e != cudaSuccess) note_launch_error(e, grid, block, smem);
 }
 
 // read-only views of a handle (solver.cu)
