@@ -317,6 +317,118 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
     if (i < cnt) b[i] = (float)a[i];
 }
 
+// member table of the ghost rows: the tensor weights of Eq. JssD multiplied
+// out per stencil member (the same products, in the same order, the row
+// evaluation used to form on the fly), the member's box node and ghost index
+template <int D>
+__global__ void k_ghost_members(int ng, const int* __restrict__ gidx, const int8_t* __restrict__ gm,
+                                const double* __restrict__ gw, const float* __restrict__ gw32,
+                                const int* __restrict__ gpos, long long st1, long long st2, double* wk, float* wk32,
+                                int* node, int* src) {
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ng) return;
+    const int K = D == 2 ? 9 : 27;
+    const long long g = gidx[gi];
+    int m[3] = {1, 1, 1};
+    for (int a = 0; a < D; a++) m[a] = gm[(long long)gi * D + a];
+    for (int kk = 0; kk < K; kk++) {
+        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+        const double* w = gw + (long long)gi * 3 * D;
+        const float* w32 = gw32 + (long long)gi * 3 * D;
+        double wd = w[k0] * w[3 + k1];
+        float wf = w32[k0] * w32[3 + k1];
+        if (D == 3) {
+            wd = wd * w[6 + k2];
+            wf = wf * w32[6 + k2];
+        }
+        long long nd = g - m[0] * k0 - m[1] * k1 * st1;
+        if (D == 3) nd -= m[2] * k2 * st2;
+        const long long o = (long long)kk * ng + gi;
+        wk[o] = wd;
+        wk32[o] = wf;
+        const bool on = wd != 0.0 || wf != 0.0f;
+        node[o] = on ? (int)nd : (int)g;
+        src[o] = on ? gpos[nd] : -1;
+    }
+}
+
+// ---- band extension operator (Sec. 3.5.2) ----
+// kExtSteps explicit upwind Euler steps of dr/dtau + n.grad r = 0 from zero
+// band values are linear in the ghost defects with coefficients fixed by the
+// geometry: with S_b the sum of |n_a| over b's upwind references,
+//   v_{k+1}(b) = (1 - cfl S_b) v_k(b) + cfl sum_a |n_a| u_k(ref_a),
+// u the band value (v_k) or the ghost defect at the reference.  Expanding the
+// recursion, each band node's final value is a short weighted sum of ghost
+// defects; the weights are accumulated over the paths of the recursion.
+constexpr int kExtSteps = 4;
+constexpr int kExtCap = 32;
+
+template <int D>
+__device__ int ext_row(int b, const int* __restrict__ bref, const double* __restrict__ ban, double cfl, int* gnode,
+                       double* coef) {
+    struct Item {
+        int node, k;
+        double scale;
+    };
+    Item st[1 + kExtSteps * (D + 1)];
+    int sp = 0, n = 0;
+    st[sp++] = Item{b, kExtSteps, 1.0};
+    while (sp > 0) {
+        Item e = st[--sp];
+        if (e.k == 0) continue;  // band values start at zero
+        double S = 0.0;
+        for (int a = 0; a < D; a++)
+            if (bref[(long long)e.node * D + a] != -1) S += ban[(long long)e.node * D + a];
+        st[sp++] = Item{e.node, e.k - 1, e.scale * (1.0 - cfl * S)};
+        for (int a = 0; a < D; a++) {
+            const int r = bref[(long long)e.node * D + a];
+            if (r == -1) continue;
+            const double w = e.scale * (cfl * ban[(long long)e.node * D + a]);
+            if (r >= 0) {
+                st[sp++] = Item{r, e.k - 1, w};
+            } else {
+                const int g = -r - 2;
+                int j = 0;
+                while (j < n && gnode[j] != g) j++;
+                if (j == n) {
+                    if (n == kExtCap) return -1;
+                    gnode[n] = g;
+                    coef[n] = 0.0;
+                    n++;
+                }
+                coef[j] += w;
+            }
+        }
+    }
+    return n;
+}
+
+template <int D>
+__global__ void k_ext_count(int nb, const int* __restrict__ bref, const double* __restrict__ ban, double cfl,
+                            int* cnt) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int gnode[kExtCap];
+    double coef[kExtCap];
+    cnt[b] = ext_row<D>(b, bref, ban, cfl, gnode, coef);
+}
+
+template <int D>
+__global__ void k_ext_fill(int nb, const int* __restrict__ bref, const double* __restrict__ ban, double cfl,
+                           const int* __restrict__ eptr, int* eidx, double* eval, float* eval32) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int gnode[kExtCap];
+    double coef[kExtCap];
+    int n = ext_row<D>(b, bref, ban, cfl, gnode, coef);
+    const int o = eptr[b];
+    for (int j = 0; j < n; j++) {
+        eidx[o + j] = gnode[j];
+        eval[o + j] = coef[j];
+        eval32[o + j] = (float)coef[j];
+    }
+}
+
 // ---- band of inactive nodes near the ghosts ----
 
 __global__ void k_band_mark(const int8_t* __restrict__ type, int8_t* __restrict__ mark, int n, int dim, long long nn,
@@ -482,7 +594,12 @@ int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool c
     L.gw = (double*)mem.get(sizeof(double) * ng1 * D * 3);
     L.gw32 = (float*)mem.get(sizeof(float) * ng1 * D * 3);
     L.gB = (double*)mem.get(sizeof(double) * ng1 * D);
-    if (!L.gpos || !L.gkind || !L.gm || !L.gw || !L.gw32 || !L.gB) {
+    const long long K = D == 2 ? 9 : 27;
+    L.gwk = (double*)mem.get(sizeof(double) * ng1 * K);
+    L.gwk32 = (float*)mem.get(sizeof(float) * ng1 * K);
+    L.gnode = (int*)mem.get(sizeof(int) * ng1 * K);
+    L.gsrc = (int*)mem.get(sizeof(int) * ng1 * K);
+    if (!L.gpos || !L.gkind || !L.gm || !L.gw || !L.gw32 || !L.gB || !L.gwk || !L.gwk32 || !L.gnode || !L.gsrc) {
         err = "out of device memory";
         return SULF_ENOMEM;
     }
@@ -496,7 +613,13 @@ int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool c
             k_ghost_geom<3><<<nblk(L.ng, 128), 128, 0, s>>>(L.phi, L.type, L.n, L.lo, L.h, L.gidx, L.ng, L.gkind,
                                                             L.gm, L.gw, L.gB);
         k_to_float<<<nblk(L.ng * 3LL * D), kThreads, 0, s>>>(L.gw, L.gw32, L.ng * 3LL * D);
-        launches += 3;
+        if (D == 2)
+            k_ghost_members<2><<<nblk(L.ng, 128), 128, 0, s>>>(L.ng, L.gidx, L.gm, L.gw, L.gw32, L.gpos, L.st[1],
+                                                               L.st[2], L.gwk, L.gwk32, L.gnode, L.gsrc);
+        else
+            k_ghost_members<3><<<nblk(L.ng, 128), 128, 0, s>>>(L.ng, L.gidx, L.gm, L.gw, L.gw32, L.gpos, L.st[1],
+                                                               L.st[2], L.gwk, L.gwk32, L.gnode, L.gsrc);
+        launches += 4;
         std::vector<int8_t> kinds(L.ng);
         cudaMemcpyAsync(kinds.data(), L.gkind, L.ng, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -545,6 +668,64 @@ int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool c
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         err = "band construction failed";
         return SULF_EDEVICE;
+    }
+    // the band extension operator: per-node entry counts, host scan, fill
+    {
+        const double cfl = D == 2 ? 0.5 : 1.0 / 3.0;
+        L.eptr = (int*)mem.get(sizeof(int) * nb1);
+        if (!L.eptr) {
+            err = "out of device memory";
+            return SULF_ENOMEM;
+        }
+        std::vector<int> cnt(L.nb + 1, 0);
+        if (L.nb > 0) {
+            if (D == 2)
+                k_ext_count<2><<<nblk(L.nb, 128), 128, 0, s>>>(L.nb, L.bref, L.ban, cfl, L.eptr);
+            else
+                k_ext_count<3><<<nblk(L.nb, 128), 128, 0, s>>>(L.nb, L.bref, L.ban, cfl, L.eptr);
+            launches++;
+            if (cudaMemcpyAsync(cnt.data(), L.eptr, sizeof(int) * L.nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                err = "band extension operator failed";
+                return SULF_EDEVICE;
+            }
+        }
+        std::vector<int> ptr(L.nb + 1, 0);
+        long long tot = 0;
+        for (int b = 0; b < L.nb; b++) {
+            if (cnt[b] < 0) {
+                err = "band extension reaches more ghosts than supported";
+                return SULF_EGEOM;
+            }
+            ptr[b] = (int)tot;
+            tot += cnt[b];
+        }
+        ptr[L.nb] = (int)tot;
+        L.ne = tot;
+        L.eidx = (int*)mem.get(sizeof(int) * (tot + 1));
+        L.eval = (double*)mem.get(sizeof(double) * (tot + 1));
+        L.eval32 = (float*)mem.get(sizeof(float) * (tot + 1));
+        if (!L.eidx || !L.eval || !L.eval32) {
+            err = "out of device memory";
+            return SULF_ENOMEM;
+        }
+        if (cudaMemcpyAsync(L.eptr, ptr.data(), sizeof(int) * (L.nb + 1), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            err = "band extension operator failed";
+            return SULF_EDEVICE;
+        }
+        if (L.nb > 0) {
+            if (D == 2)
+                k_ext_fill<2><<<nblk(L.nb, 128), 128, 0, s>>>(L.nb, L.bref, L.ban, cfl, L.eptr, L.eidx, L.eval,
+                                                              L.eval32);
+            else
+                k_ext_fill<3><<<nblk(L.nb, 128), 128, 0, s>>>(L.nb, L.bref, L.ban, cfl, L.eptr, L.eidx, L.eval,
+                                                              L.eval32);
+            launches++;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            err = "band extension operator failed";
+            return SULF_EDEVICE;
+        }
     }
     if (coarsest) {
         L.nact = compact(P_ACTIVE, L, L.act, mem, s, err, launches);

@@ -18,6 +18,7 @@ namespace sulf {
 using stages::abs_bits;
 using stages::coef_ptr;
 using stages::CoefPtr;
+using stages::GhostTab;
 using stages::list_node;
 using stages::Lists;
 using stages::make_lists;
@@ -205,32 +206,30 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
 
 // one Jacobi pass of the ghost relaxation of Eq. RelGhost over all ghosts
 template <int D, typename T>
-__global__ void __launch_bounds__(kT) k_ghost_pass(int ng, const int* __restrict__ gidx, const int* __restrict__ gpos,
-                                                    const int8_t* __restrict__ gm, const T* __restrict__ gw,
+__global__ void __launch_bounds__(kT) k_ghost_pass(const int* __restrict__ gidx, GhostTab<T> tb,
                                                     const typename V2<T>::t* __restrict__ gc,
                                                     const typename V2<T>::t* __restrict__ rhs,
-                                                    typename V2<T>::t* x, const T* sin, T* sout, long long st1,
-                                                    long long st2, Coef<T> c, int first, int last) {
+                                                    typename V2<T>::t* x, const T* sin, T* sout, Coef<T> c, int first,
+                                                    int last) {
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = gi < tb.ng;
     // the boundary rows and the ghost c-row coefficients are fixed during the
-    // linear solve: fetch them (and, in 2-D, the members' ghost indices) while
+    // linear solve: fetch them (in 2-D the whole member table of the row) while
     // the previous kernel is still running
-    stages::GhostRow<D, T> row;
+    long long g = 0;
     typename V2<T>::t q;
     T qinv;
-    int src[stages::kGhostSrc];
-    const bool hoist = D == 2 && !first;
-    if (gi < ng) {
-        row = stages::fetch_ghost_row<D, T>(gi, gidx[gi], gm, gw);
+    stages::Members<T> m;
+    if (on) {
+        g = gidx[gi];
         q = gc[gi];
         qinv = (T)1 / q.y;
-        if constexpr (D == 2)
-            if (hoist) stages::fetch_ghost_src<D, T>(row, gpos, st1, src);
+        if (D == 2) stages::fetch_members<T>(tb, gi, 0, m);
     }
     pdl_enter();
-    if (gi >= ng) return;
-    stages::ghost_pass_apply<D, T, false>(gi, row, hoist ? src : nullptr, q, qinv, gpos, rhs, x, sin, sout, st1,
-                                          st2, c.tau, first != 0, last != 0);
+    if (!on) return;
+    stages::ghost_pass_apply<D, T, false>(gi, g, tb, D == 2 ? &m : nullptr, q, qinv, rhs, x, sin, sout, c.tau,
+                                          first != 0, last != 0);
 }
 
 template <typename T>
@@ -246,41 +245,42 @@ __global__ void k_ghost_scatter(int ng, const int* __restrict__ gidx, const T* _
 // defect r = rhs - J x on every active node, with its max-norm
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kT) k_residual(Lists ls, const int8_t* __restrict__ gm, const T* __restrict__ gw,
-                                                  CoefPtr<D, T> cf, const typename V2<T>::t* __restrict__ rhs,
+__global__ void __launch_bounds__(kT) k_residual(Lists ls, GhostTab<T> tb, CoefPtr<D, T> cf,
+                                                  const typename V2<T>::t* __restrict__ rhs,
                                                   const typename V2<T>::t* __restrict__ x,
                                                   typename V2<T>::t* __restrict__ res, long long st1, long long st2,
                                                   unsigned long long* norm) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool on = t < ls.n0 + ls.n1 + ls.ng;
-    // lists and coefficients are fixed during the linear solve: fetched ahead
-    int kind = 0;
+    // lists, coefficients and ghost rows are fixed during the linear solve:
+    // fetched ahead
+    int kind = 0, gi = 0;
     long long p = 0;
     stages::InsideCoef<D, T> k;
-    stages::GhostRow<D, T> row;
+    stages::Members<T> m;
     typename V2<T>::t q;
-    if (on) p = stages::fetch_residual<D, T>(t, ls, gm, gw, cf, st1, st2, kind, k, row, q);
+    if (on) p = stages::fetch_residual<D, T>(t, ls, tb, cf, st1, st2, kind, gi, k, m, q);
     pdl_enter();
     unsigned long long nb = 0;
-    if (on) nb = stages::residual_apply<D, T, false>(p, kind, k, row, q, rhs, x, res, st1, st2);
+    if (on)
+        nb = stages::residual_apply<D, T, false>(p, kind, gi, k, tb, D == 2 ? &m : nullptr, q, rhs, x, res, st1,
+                                                 st2);
     if (norm) block_max(nb, norm);
 }
 
 // ---------------------------------------------------------------------------
-// extension of the ghost defect into the band along the normal (Sec. 3.5.2):
-// explicit upwind Euler steps of dr/dtau + n.grad r = 0, band values start at 0
+// extension of the ghost defect into the band along the normal (Sec. 3.5.2),
+// the explicit upwind steps applied as one precomputed linear operator
 
-template <int D, typename T>
-__global__ void k_extend_step(int nb, const int* __restrict__ bidx, const int* __restrict__ bref,
-                              const T* __restrict__ ban, typename V2<T>::t* res,
-                              const typename V2<T>::t* __restrict__ bin, typename V2<T>::t* __restrict__ bout, T cfl,
-                              int first, int last) {
+template <typename T>
+__global__ void k_extend(int nb, const int* __restrict__ eptr, const int* __restrict__ eidx,
+                         const T* __restrict__ eval, const int* __restrict__ bidx, typename V2<T>::t* res) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    stages::BandRef<D, T> br;
-    if (b < nb) br = stages::fetch_band<D, T>(b, bref, ban);  // fixed geometry, fetched ahead
+    stages::ExtRow<T> r;
+    if (b < nb) r = stages::fetch_ext<T>(b, eptr, eidx, eval, bidx);  // fixed operator, fetched ahead
     pdl_enter();
     if (b >= nb) return;
-    stages::extend_apply<D, T, false>(b, br, bidx, res, bin, bout, cfl, first != 0, last != 0);
+    stages::extend_apply<T, false>(r, eidx, eval, res);
 }
 
 // ---------------------------------------------------------------------------
@@ -388,11 +388,11 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = 2 * nact;
     const long long mm = (long long)m * m;
-    // with SMEM the work matrix and the inverse live in shared memory (small
-    // coarsest levels) and the inverse is copied out at the end
+    // with SMEM the matrix is inverted in shared memory (small coarsest
+    // levels) and copied out at the end; otherwise in place in Ag
     T* A = SMEM ? reinterpret_cast<T*>(smem_raw) : Ag;
-    T* Ainv = SMEM ? A + mm : Ainv_g;
-    int* piv = reinterpret_cast<int*>(smem_raw + (SMEM ? 2 * mm * sizeof(T) : 0));  // scratch of m T values
+    T* fac = reinterpret_cast<T*>(smem_raw + (SMEM ? mm * sizeof(T) : 0));  // column k of the current step
+    int* piv = reinterpret_cast<int*>(fac + m + 1);                        // row interchanges
     for (long long i = threadIdx.x; i < mm; i += blockDim.x) A[i] = 0;
     __syncthreads();
     for (int r = threadIdx.x; r < nact; r += blockDim.x) {
@@ -440,15 +440,18 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
         rc[2 * r + 1] += c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
     }
     __syncthreads();
-    // Gauss-Jordan elimination with partial pivoting on [A | I]: the same pivot
-    // sequence as an LU with partial pivoting (first row of largest |a_ik|,
-    // i >= k), leaving the inverse in Ainv
-    for (long long i = threadIdx.x; i < mm; i += blockDim.x) {
-        int r = (int)(i / m), q = (int)(i % m);
-        Ainv[i] = r == q ? (T)1 : (T)0;
-    }
-    T* fac = reinterpret_cast<T*>(piv);  // column factors of the current step (m values)
+    // In-place Gauss-Jordan inversion with partial pivoting (first row of
+    // largest |a_ik|, i >= k, as an LU with partial pivoting would choose):
+    // step k scales the pivot row by 1/a_kk and eliminates column k from every
+    // other row, storing -a_ik/a_kk in column k; this inverts P A, and the
+    // column interchanges applied in reverse order at the end give A^{-1}.
+    // About m^3 fused multiply-adds (half of eliminating on [A | I]); threads
+    // own fixed columns and stride over rows, so the inner loop carries no
+    // index division.
     __shared__ int s_piv;
+    const int W = m < (int)blockDim.x ? m : (int)blockDim.x;
+    const int R = (int)blockDim.x / W;
+    const int jt = (int)threadIdx.x % W, rt = (int)threadIdx.x / W;
     __syncthreads();
     for (int k = 0; k < m; k++) {
         if (threadIdx.x < 32) {
@@ -472,46 +475,51 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
             }
             if (lane == 0) {
                 s_piv = bi;
+                piv[k] = bi;
                 if (!(bv > (T)0)) *singular = 1;
             }
         }
         __syncthreads();
         const int pr = s_piv;
         if (pr != k)
-            for (int j = threadIdx.x; j < 2 * m; j += blockDim.x) {
-                T* M = j < m ? A : Ainv;
-                int q = j < m ? j : j - m;
-                T tmp = M[(long long)k * m + q];
-                M[(long long)k * m + q] = M[(long long)pr * m + q];
-                M[(long long)pr * m + q] = tmp;
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                T tmp = A[(long long)k * m + j];
+                A[(long long)k * m + j] = A[(long long)pr * m + j];
+                A[(long long)pr * m + j] = tmp;
             }
         __syncthreads();
         const T inv = (T)1 / A[(long long)k * m + k];
         for (int i = threadIdx.x; i < m; i += blockDim.x) fac[i] = A[(long long)i * m + k];
         __syncthreads();
-        for (int j = threadIdx.x; j < 2 * m; j += blockDim.x) {
-            T* M = j < m ? A : Ainv;
-            int q = j < m ? j : j - m;
-            M[(long long)k * m + q] *= inv;
-        }
+        for (int j = threadIdx.x; j < m; j += blockDim.x)
+            A[(long long)k * m + j] = j == k ? inv : A[(long long)k * m + j] * inv;
         __syncthreads();
-        const long long work = (long long)m * 2 * m;
-        for (long long e = threadIdx.x; e < work; e += blockDim.x) {
-            int i = (int)(e / (2 * m));
-            int j = (int)(e % (2 * m));
-            if (i == k) continue;
-            T f = fac[i];
-            if (f == (T)0) continue;
-            T* M = j < m ? A : Ainv;
-            int q = j < m ? j : j - m;
-            M[(long long)i * m + q] -= f * M[(long long)k * m + q];
-        }
+        if (rt < R)
+            for (int j = jt; j < m; j += W) {
+                if (j == k) continue;
+                const T akj = A[(long long)k * m + j];
+                for (int i = rt; i < m; i += R) {
+                    if (i == k) continue;
+                    A[(long long)i * m + j] -= fac[i] * akj;
+                }
+            }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            if (i != k) A[(long long)i * m + k] = -fac[i] * inv;
         __syncthreads();
     }
-    if (SMEM) {
+    // undo the row interchanges as column interchanges, last first
+    for (int k = m - 1; k >= 0; k--) {
+        const int pr = piv[k];
+        if (pr != k)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                T tmp = A[(long long)i * m + k];
+                A[(long long)i * m + k] = A[(long long)i * m + pr];
+                A[(long long)i * m + pr] = tmp;
+            }
         __syncthreads();
-        for (long long i = threadIdx.x; i < mm; i += blockDim.x) Ainv_g[i] = Ainv[i];
     }
+    for (long long i = threadIdx.x; i < mm; i += blockDim.x) Ainv_g[i] = A[i];
 }
 
 template <typename T>
@@ -590,8 +598,7 @@ __global__ void __launch_bounds__(kT) k_old_time(Lists ls, const double2* __rest
 }
 
 template <int D>
-__global__ void __launch_bounds__(kT) k_newton_F(Lists ls, const int8_t* __restrict__ gm, const double* __restrict__ gw,
-                                                  const double2* __restrict__ W, const double2* __restrict__ G,
+__global__ void __launch_bounds__(kT) k_newton_F(Lists ls, GhostTab<double> tb, const double2* __restrict__ W, const double2* __restrict__ G,
                                                   double2* __restrict__ F, Offs<D> of, long long st1, long long st2,
                                                   FConst f, unsigned long long* norm) {
     pdl_enter();
@@ -611,7 +618,7 @@ __global__ void __launch_bounds__(kT) k_newton_F(Lists ls, const int8_t* __restr
             double Ls = Ls_h<D>(p, W, of, f, phd);
             out.x = ph * w.x * f.idt - 0.5 * Ls + g.x;
         } else {
-            out.x = stages::ghost_dot<D, double, false>(gi, p, gm, gw, nullptr, W, nullptr, true, st1, st2) - f.sb;
+            out.x = stages::row_dot<D, double, false>(tb, gi, nullptr, W, nullptr, true) - f.sb;
         }
         F[p] = out;
         unsigned long long a0 = abs_bits(out.x), a1 = abs_bits(out.y);
@@ -739,23 +746,24 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
     (void)c;
     CoefPtr<D, T> cf = coef_ptr<D, T>(V);
     if (pointwise)
-        launch_k(k_relax_inside<D, T, true>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, true>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf,
+                 V.rhs, V.x, L.st[1], L.st[2]);
     else
-        launch_k(k_relax_inside<D, T, false>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf, V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, false>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf,
+                 V.rhs, V.x, L.st[1], L.st[2]);
     return 1;
 }
 
 template <int D, typename T>
 int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, cudaStream_t s) {
     if (L.ng == 0 || passes < 1) return 0;
-    const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
     int n = 0;
     for (int p = 0; p < passes; p++) {
         bool first = p == 0, last = p == passes - 1 && passes > 1;
         const T* sin = first ? nullptr : V.gbuf[(p - 1) & 1];
         T* sout = V.gbuf[p & 1];
-        launch_k(k_ghost_pass<D, T>, grid_for(L.ng), block_for(L.ng), 0, s, L.ng, L.gidx, L.gpos, L.gm, gw, V.gc, V.rhs, V.x, sin, sout,
-                                                      L.st[1], L.st[2], c, first, last);
+        launch_k(k_ghost_pass<D, T>, grid_for(L.ng), block_for(L.ng), 0, s, L.gidx, stages::ghost_tab<T>(L), V.gc,
+                 V.rhs, V.x, sin, sout, c, first, last);
         n++;
     }
     if (passes == 1) {
@@ -772,23 +780,17 @@ int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, u
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
     (void)c;
-    const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
-    launch_k(k_residual<D, T>, grid_for(tot), block_for(tot), 0, s, ls, L.gm, gw, coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2],
-                                               norm);
+    launch_k(k_residual<D, T>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<T>(L), coef_ptr<D, T>(V),
+             V.rhs, V.x, V.res, L.st[1], L.st[2], norm);
     return 1;
 }
 
 template <int D, typename T>
-int launch_extend(const LevelGeo& L, const LevelVec<T>& V, int steps, cudaStream_t s) {
-    if (L.nb == 0 || steps < 1) return 0;
-    const T* an = std::is_same<T, float>::value ? (const T*)L.ban32 : (const T*)L.ban;
-    T cfl = D == 2 ? (T)0.5 : (T)(1.0 / 3.0);
-    for (int k = 0; k < steps; k++) {
-        bool first = k == 0, last = k == steps - 1;
-        launch_k(k_extend_step<D, T>, grid_for(L.nb), block_for(L.nb), 0, s, L.nb, L.bidx, L.bref, an, V.res, V.bbuf[(k + 1) & 1],
-                                                       V.bbuf[k & 1], cfl, first, last);
-    }
-    return steps;
+int launch_extend(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s) {
+    if (L.nb == 0) return 0;
+    const T* ev = std::is_same<T, float>::value ? (const T*)L.eval32 : (const T*)L.eval;
+    launch_k(k_extend<T>, grid_for(L.nb), block_for(L.nb), 0, s, L.nb, L.eptr, L.eidx, ev, L.bidx, V.res);
+    return 1;
 }
 
 template <int D, typename T>
@@ -824,8 +826,8 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
     const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
     Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
     const size_t m = 2 * (size_t)L.nact;
-    const size_t piv_bytes = sizeof(T) * (m + 1);
-    const size_t smem_full = 2 * m * m * sizeof(T) + piv_bytes;
+    const size_t piv_bytes = sizeof(T) * (m + 1) + sizeof(int) * (m + 1);  // column k and the interchanges
+    const size_t smem_full = m * m * sizeof(T) + piv_bytes;
     constexpr size_t kMaxSmem = 220 * 1024;
     if (smem_full <= kMaxSmem) {
         auto kern = k_coarsest_factor<D, T, true>;
@@ -873,8 +875,8 @@ int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, doubl
                     unsigned long long* norm, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_newton_F<D>, grid_for(tot), block_for(tot), 0, s, ls, L.gm, L.gw, W, G, F, make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2],
-                                            fc, norm);
+    launch_k(k_newton_F<D>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<double>(L), W, G, F,
+             make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2], fc, norm);
     return 1;
 }
 
@@ -928,7 +930,7 @@ int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double*
     template int launch_relax_ghosts<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, cudaStream_t); \
     template int launch_residual<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, unsigned long long*,  \
                                        cudaStream_t);                                                            \
-    template int launch_extend<D, T>(const LevelGeo&, const LevelVec<T>&, int, cudaStream_t);                    \
+    template int launch_extend<D, T>(const LevelGeo&, const LevelVec<T>&, cudaStream_t);                         \
     template int launch_restrict<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&, \
                                        cudaStream_t);                                                            \
     template int launch_prolong<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&,  \

@@ -161,109 +161,94 @@ __device__ __forceinline__ void relax_node(long long p, const CoefPtr<D, T>& cf,
     relax_apply<D, T, PW, CG>(p, k, rhs, x, st);
 }
 
-// The fixed part of ghost gi's boundary row s~(B) (Eq. JssD): the ghost node,
-// the upwind signs and the 1-D weights at offsets 0, 1, 2 per axis.
-template <int D, typename T>
-struct GhostRow {
-    long long g;
-    int m[3];
-    T wa[3][3];
+// Ghost boundary rows s~(B) (Eq. JssD) as member tables built once per level:
+// member kk of the upwind 3^D stencil of ghost gi has weight w (the tensor
+// product of the 1-D weights, 0 when absent), box node and ghost index (or -1),
+// stored member-major (kk * ng + gi) so a warp's loads of a member coalesce.
+template <typename T>
+struct GhostTab {
+    const T* w;
+    const int* node;
+    const int* src;
+    int ng;
 };
 
-template <int D, typename T>
-__device__ __forceinline__ GhostRow<D, T> fetch_ghost_row(int gi, long long g, const int8_t* gm, const T* gw) {
-    GhostRow<D, T> r;
-    r.g = g;
-    r.m[0] = r.m[1] = r.m[2] = 1;
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        r.m[a] = gm[(long long)gi * D + a];
-#pragma unroll
-        for (int k = 0; k < 3; k++) r.wa[a][k] = gw[(long long)gi * 3 * D + 3 * a + k];
-    }
-    return r;
+template <typename T>
+inline GhostTab<T> ghost_tab(const LevelGeo& L) {
+    GhostTab<T> t;
+    t.w = std::is_same<T, float>::value ? (const T*)L.gwk32 : (const T*)L.gwk;
+    t.node = L.gnode;
+    t.src = L.gsrc;
+    t.ng = L.ng;
+    return t;
 }
 
-// tensor weight and node of member kk of the upwind 3^D stencil
-template <int D, typename T>
-__device__ __forceinline__ T row_member(const GhostRow<D, T>& r, int kk, long long st1, long long st2,
-                                        long long& node) {
-    const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
-    T w = r.wa[0][k0] * r.wa[1][k1];
-    if (D == 3) w = w * r.wa[2][k2];
-    node = r.g - r.m[0] * k0 - r.m[1] * k1 * st1;
-    if (D == 3) node -= r.m[2] * k2 * st2;
-    return w;
-}
+// nine members of one row
+template <typename T>
+struct Members {
+    T w[9];
+    int node[9];
+    int src[9];
+};
 
-constexpr int kGhostSrc = 9;  // 2-D stencil members whose ghost index is fetched ahead
-
-// ghost index (or -1) of every stencil member with a nonzero weight (2-D)
-template <int D, typename T>
-__device__ __forceinline__ void fetch_ghost_src(const GhostRow<D, T>& r, const int* gpos, long long st1,
-                                                int* src) {
-    static_assert(D == 2, "member ghost indices are fetched ahead in 2-D only");
+template <typename T>
+__device__ __forceinline__ void fetch_members(const GhostTab<T>& tb, int gi, int k0, Members<T>& m) {
 #pragma unroll
-    for (int kk = 0; kk < kGhostSrc; kk++) {
-        long long node;
-        T w = row_member<D, T>(r, kk, st1, 0, node);
-        src[kk] = w == (T)0 ? -1 : gpos[node];
+    for (int j = 0; j < 9; j++) {
+        const long long o = (long long)(k0 + j) * tb.ng + gi;
+        m.w[j] = tb.w[o];
+        m.node[j] = tb.node[o];
+        m.src[j] = tb.src[o];
     }
 }
 
-// the row applied to the s component.  Ghost members come from the previous
-// relaxation pass (sin) unless from_x; their ghost indices from src when given
-// (2-D), else from gpos.  The member values are gathered nine at a time with
-// every load issued before any is used (one memory latency per nine members,
-// not one per member), then summed in member order.
+// acc plus nine members of the row applied to the s component.  Ghost members
+// come from the previous relaxation pass (sin) unless from_x.  Every load is
+// issued before any value is used, then the terms are summed in member order.
+template <typename T, bool CG>
+__device__ __forceinline__ T members_dot(const Members<T>& m, const typename V2<T>::t* x, const T* sin, bool from_x,
+                                         T acc) {
+    T v[9];
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+        const T* a = reinterpret_cast<const T*>(x + m.node[j]);
+        if (!from_x && m.src[j] >= 0) a = sin + m.src[j];
+        v[j] = m.w[j] != (T)0 ? ldx<CG>(a) : (T)0;
+    }
+#pragma unroll
+    for (int j = 0; j < 9; j++)
+        if (m.w[j] != (T)0) acc += m.w[j] * v[j];
+    return acc;
+}
+
+// the whole row: in 2-D from the members fetched ahead (pre), in 3-D fetched
+// here nine at a time
 template <int D, typename T, bool CG>
-__device__ __forceinline__ T row_dot(const GhostRow<D, T>& r, const int* src, const int* gpos,
-                                     const typename V2<T>::t* x, const T* sin, bool from_x, long long st1,
-                                     long long st2) {
-    constexpr int K = D == 2 ? 9 : 27;
+__device__ __forceinline__ T row_dot(const GhostTab<T>& tb, int gi, const Members<T>* pre,
+                                     const typename V2<T>::t* x, const T* sin, bool from_x) {
+    if (D == 2 && pre) return members_dot<T, CG>(*pre, x, sin, from_x, (T)0);
+    const int K = D == 2 ? 9 : 27;
     T acc = 0;
-#pragma unroll
+#pragma unroll 1
     for (int c0 = 0; c0 < K; c0 += 9) {
-        T w[9], v[9];
-#pragma unroll
-        for (int j = 0; j < 9; j++) {
-            long long node;
-            w[j] = row_member<D, T>(r, c0 + j, st1, st2, node);
-            const T* a = reinterpret_cast<const T*>(x + node);
-            if (!from_x) {
-                int gp = (D == 2 && src) ? src[j] : (w[j] != (T)0 ? gpos[node] : -1);
-                if (gp >= 0) a = sin + gp;
-            }
-            v[j] = w[j] != (T)0 ? ldx<CG>(a) : (T)0;
-        }
-#pragma unroll
-        for (int j = 0; j < 9; j++)
-            if (w[j] != (T)0) acc += w[j] * v[j];
+        Members<T> m;
+        fetch_members<T>(tb, gi, c0, m);
+        acc = members_dot<T, CG>(m, x, sin, from_x, acc);
     }
     return acc;
 }
 
+// one Jacobi pass of the ghost relaxation (Eq. RelGhost) for ghost gi at node
+// g: s_g += tau (r_g - row . x) from the previous pass's values, then the ghost
+// c row J^cs_gg s_g + J^cc_gg c_g = r^c_g solved for c_g with the fresh s_g
+// (q = (J^cs_gg, J^cc_gg), qinv = 1 / J^cc_gg)
 template <int D, typename T, bool CG>
-__device__ __forceinline__ T ghost_dot(int gi, long long g, const int8_t* gm, const T* gw, const int* gpos,
-                                       const typename V2<T>::t* x, const T* sin, bool from_x, long long st1,
-                                       long long st2) {
-    GhostRow<D, T> r = fetch_ghost_row<D, T>(gi, g, gm, gw);
-    return row_dot<D, T, CG>(r, nullptr, gpos, x, sin, from_x, st1, st2);
-}
-
-// one Jacobi pass of the ghost relaxation (Eq. RelGhost) for ghost gi from its
-// fetched row: s_g += tau (r_g - row . x) from the previous pass's values,
-// then the ghost c row J^cs_gg s_g + J^cc_gg c_g = r^c_g solved for c_g with
-// the fresh s_g (q = (J^cs_gg, J^cc_gg), qinv = 1 / J^cc_gg)
-template <int D, typename T, bool CG>
-__device__ __forceinline__ void ghost_pass_apply(int gi, const GhostRow<D, T>& row, const int* src,
-                                                 typename V2<T>::t q, T qinv, const int* gpos,
-                                                 const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* sin,
-                                                 T* sout, long long st1, long long st2, T tau, bool first,
+__device__ __forceinline__ void ghost_pass_apply(int gi, long long g, const GhostTab<T>& tb, const Members<T>* pre,
+                                                 typename V2<T>::t q, T qinv, const typename V2<T>::t* rhs,
+                                                 typename V2<T>::t* x, const T* sin, T* sout, T tau, bool first,
                                                  bool last) {
     typedef typename V2<T>::t T2;
-    const long long g = row.g;
-    T acc = row_dot<D, T, CG>(row, src, gpos, x, sin, first, st1, st2);
+    T acc = row_dot<D, T, CG>(tb, gi, pre, x, sin, first);
     T2 xg = ldx<CG>(x + g);
     T s_old = first ? xg.x : ldx<CG>(sin + gi);
     T2 b = ldx<CG>(rhs + g);
@@ -278,23 +263,26 @@ __device__ __forceinline__ void ghost_pass_apply(int gi, const GhostRow<D, T>& r
 }
 
 template <int D, typename T, bool CG>
-__device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const int* gpos, const int8_t* gm,
-                                                const T* gw, const typename V2<T>::t* gc,
-                                                const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* sin,
-                                                T* sout, long long st1, long long st2, T tau, bool first,
+__device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const GhostTab<T>& tb,
+                                                const typename V2<T>::t* gc, const typename V2<T>::t* rhs,
+                                                typename V2<T>::t* x, const T* sin, T* sout, T tau, bool first,
                                                 bool last) {
-    GhostRow<D, T> row = fetch_ghost_row<D, T>(gi, gidx[gi], gm, gw);
+    Members<T> m;
+    const Members<T>* pre = nullptr;
+    if (D == 2) {
+        fetch_members<T>(tb, gi, 0, m);
+        pre = &m;
+    }
     typename V2<T>::t q = gc[gi];
-    ghost_pass_apply<D, T, CG>(gi, row, nullptr, q, (T)1 / q.y, gpos, rhs, x, sin, sout, st1, st2, tau, first,
-                               last);
+    ghost_pass_apply<D, T, CG>(gi, gidx[gi], tb, pre, q, (T)1 / q.y, rhs, x, sin, sout, tau, first, last);
 }
 
 // defect r = rhs - J x at node p of kind 1 (inside, coefficients k) or 2
-// (ghost, boundary row and c-row q); returns max(|r_s|, |r_c|) as bits
+// (ghost gi, its row and c-row q); returns max(|r_s|, |r_c|) as bits
 template <int D, typename T, bool CG>
-__device__ __forceinline__ unsigned long long residual_apply(long long p, int kind, const InsideCoef<D, T>& k,
-                                                             const GhostRow<D, T>& row, typename V2<T>::t q,
-                                                             const typename V2<T>::t* rhs,
+__device__ __forceinline__ unsigned long long residual_apply(long long p, int kind, int gi, const InsideCoef<D, T>& k,
+                                                             const GhostTab<T>& tb, const Members<T>* pre,
+                                                             typename V2<T>::t q, const typename V2<T>::t* rhs,
                                                              const typename V2<T>::t* x, typename V2<T>::t* res,
                                                              long long st1, long long st2) {
     typedef typename V2<T>::t T2;
@@ -307,7 +295,7 @@ __device__ __forceinline__ unsigned long long residual_apply(long long p, int ki
         r.x = fmadd(-k.m0.y, xp.y, fmadd(-k.m0.x, xp.x, rs));
         r.y = fmadd(-k.m1.y, xp.y, fmadd(-k.m1.x, xp.x, b.y));
     } else {
-        T acc = row_dot<D, T, CG>(row, nullptr, nullptr, x, nullptr, true, st1, st2);
+        T acc = row_dot<D, T, CG>(tb, gi, pre, x, nullptr, true);
         r.x = b.x - acc;
         r.y = b.y - (q.x * xp.x + q.y * xp.y);
     }
@@ -316,99 +304,101 @@ __device__ __forceinline__ unsigned long long residual_apply(long long p, int ki
     return a0 > a1 ? a0 : a1;
 }
 
-// the fixed data of the defect at list position t
+// the fixed data of the defect at list position t (in 2-D a ghost's members)
 template <int D, typename T>
-__device__ __forceinline__ long long fetch_residual(int t, const Lists& ls, const int8_t* gm, const T* gw,
+__device__ __forceinline__ long long fetch_residual(int t, const Lists& ls, const GhostTab<T>& tb,
                                                    const CoefPtr<D, T>& cf, long long st1, long long st2, int& kind,
-                                                   InsideCoef<D, T>& k, GhostRow<D, T>& row,
+                                                   int& gi, InsideCoef<D, T>& k, Members<T>& m,
                                                    typename V2<T>::t& q) {
-    int gi = 0;
+    gi = 0;
     long long p = list_node(ls, t, kind, gi);
     if (kind == 1) {
         const long long st[3] = {1, st1, st2};
         k = fetch_inside<D, T, true>(p, cf, st);
     } else {
-        row = fetch_ghost_row<D, T>(gi, p, gm, gw);
+        if (D == 2) fetch_members<T>(tb, gi, 0, m);
         q = cf.gc[gi];
     }
     return p;
 }
 
 template <int D, typename T, bool CG>
-__device__ __forceinline__ unsigned long long residual_node(int t, const Lists& ls, const int8_t* gm, const T* gw,
+__device__ __forceinline__ unsigned long long residual_node(int t, const Lists& ls, const GhostTab<T>& tb,
                                                             const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
                                                             const typename V2<T>::t* x, typename V2<T>::t* res,
                                                             long long st1, long long st2) {
-    int kind;
+    int kind, gi;
     InsideCoef<D, T> k;
-    GhostRow<D, T> row;
+    Members<T> m;
     typename V2<T>::t q;
-    long long p = fetch_residual<D, T>(t, ls, gm, gw, cf, st1, st2, kind, k, row, q);
-    return residual_apply<D, T, CG>(p, kind, k, row, q, rhs, x, res, st1, st2);
+    long long p = fetch_residual<D, T>(t, ls, tb, cf, st1, st2, kind, gi, k, m, q);
+    return residual_apply<D, T, CG>(p, kind, gi, k, tb, D == 2 ? &m : nullptr, q, rhs, x, res, st1, st2);
 }
 
-// one explicit upwind Euler step of dr/dtau + n.grad r = 0 at band node b
-// (Sec. 3.5.2); band values start at 0.  The upwind references and |n_a| are
-// fixed geometry (BandRef, fetched ahead by the per-level kernel).
-template <int D, typename T>
-struct BandRef {
-    int ref[D];
-    T an[D];
+// The ghost defect extended into the band along the normal (Sec. 3.5.2): the
+// explicit upwind steps are linear in the ghost defects, so the extended value
+// at band node b is a precomputed weighted sum of ghost defects (CSR row b of
+// eptr/eidx/eval, built with the geometry).  Ghost nodes are never band nodes,
+// so all band nodes update at once.
+template <typename T>
+struct ExtRow {
+    static constexpr int kAhead = 8;  // entries fetched ahead of the wait
+    int j0, j1, node;
+    int idx[kAhead];
+    T w[kAhead];
 };
 
-template <int D, typename T>
-__device__ __forceinline__ BandRef<D, T> fetch_band(int b, const int* bref, const T* ban) {
-    BandRef<D, T> r;
+template <typename T>
+__device__ __forceinline__ ExtRow<T> fetch_ext(int b, const int* eptr, const int* eidx, const T* eval,
+                                               const int* bidx) {
+    ExtRow<T> r;
+    r.j0 = eptr[b];
+    r.j1 = eptr[b + 1];
+    r.node = bidx[b];
 #pragma unroll
-    for (int a = 0; a < D; a++) {
-        r.ref[a] = bref[(long long)b * D + a];
-        r.an[a] = ban[(long long)b * D + a];
+    for (int j = 0; j < ExtRow<T>::kAhead; j++) {
+        const bool on = r.j0 + j < r.j1;
+        r.idx[j] = on ? eidx[r.j0 + j] : 0;
+        r.w[j] = on ? eval[r.j0 + j] : (T)0;
     }
     return r;
 }
 
-template <int D, typename T, bool CG>
-__device__ __forceinline__ void extend_apply(int b, const BandRef<D, T>& br, const int* bidx,
-                                             typename V2<T>::t* res, const typename V2<T>::t* bin,
-                                             typename V2<T>::t* bout, T cfl, bool first, bool last) {
+template <typename T, bool CG>
+__device__ __forceinline__ void extend_apply(const ExtRow<T>& r, const int* eidx, const T* eval,
+                                             typename V2<T>::t* res) {
     typedef typename V2<T>::t T2;
-    T2 v, u[D];
-    v.x = 0;
-    v.y = 0;
-    if (!first) v = ldx<CG>(bin + b);
+    T2 v[ExtRow<T>::kAhead];
 #pragma unroll
-    for (int a = 0; a < D; a++) {
-        u[a].x = 0;
-        u[a].y = 0;
-        int ref = br.ref[a];
-        if (ref >= 0) {
-            if (!first) u[a] = ldx<CG>(bin + ref);
-        } else if (ref <= -2) {
-            u[a] = ldx<CG>(res + (-(long long)ref - 2));
-        }
+    for (int j = 0; j < ExtRow<T>::kAhead; j++) {
+        v[j].x = 0;
+        v[j].y = 0;
+        if (r.j0 + j < r.j1) v[j] = ldx<CG>(res + r.idx[j]);
     }
-    T ax = 0, ay = 0;
+    T sx = 0, sy = 0;
 #pragma unroll
-    for (int a = 0; a < D; a++) {
-        if (br.ref[a] == -1) continue;
-        ax += br.an[a] * (v.x - u[a].x);
-        ay += br.an[a] * (v.y - u[a].y);
+    for (int j = 0; j < ExtRow<T>::kAhead; j++) {
+        if (r.j0 + j >= r.j1) break;
+        sx += r.w[j] * v[j].x;
+        sy += r.w[j] * v[j].y;
     }
-    T2 nv;
-    nv.x = v.x - cfl * ax;
-    nv.y = v.y - cfl * ay;
-    if (last)
-        res[bidx[b]] = nv;
-    else
-        bout[b] = nv;
+    for (int j = r.j0 + ExtRow<T>::kAhead; j < r.j1; j++) {
+        T2 u = ldx<CG>(res + eidx[j]);
+        T w = eval[j];
+        sx += w * u.x;
+        sy += w * u.y;
+    }
+    T2 out;
+    out.x = sx;
+    out.y = sy;
+    res[r.node] = out;
 }
 
-template <int D, typename T, bool CG>
-__device__ __forceinline__ void extend_node(int b, const int* bidx, const int* bref, const T* ban,
-                                            typename V2<T>::t* res, const typename V2<T>::t* bin,
-                                            typename V2<T>::t* bout, T cfl, bool first, bool last) {
-    BandRef<D, T> br = fetch_band<D, T>(b, bref, ban);
-    extend_apply<D, T, CG>(b, br, bidx, res, bin, bout, cfl, first, last);
+template <typename T, bool CG>
+__device__ __forceinline__ void extend_node(int b, const int* eptr, const int* eidx, const T* eval, const int* bidx,
+                                            typename V2<T>::t* res) {
+    ExtRow<T> r = fetch_ext<T>(b, eptr, eidx, eval, bidx);
+    extend_apply<T, CG>(r, eidx, eval, res);
 }
 
 __device__ __forceinline__ bool valid_for(int8_t rule, int8_t t) {
@@ -426,6 +416,7 @@ struct RestrictGeo {
     T w1[3][3];
     unsigned valid;
     T wc;
+    T w[D == 2 ? 9 : 1];  // 2-D: the member weights, kept from the fetch
 };
 
 template <int D, typename T>
@@ -477,6 +468,7 @@ __device__ __forceinline__ RestrictGeo<D, T> fetch_restrict(int t, const Lists& 
             g.wc += w;
         else
             g.valid |= 1u << kk;
+        if (D == 2) g.w[kk % 9] = w;
     }
     return g;
 }
@@ -508,8 +500,13 @@ __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int f
             const int kk = c0 + j;
             if (!((g.valid >> kk) & 1u)) continue;
             const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
-            T w = g.w1[0][k0] * g.w1[1][k1];
-            if (D == 3) w = w * g.w1[2][k2];
+            T w;
+            if (D == 2) {
+                w = g.w[kk % 9];
+            } else {
+                w = g.w1[0][k0] * g.w1[1][k1];
+                w = w * g.w1[2][k2];
+            }
             as += w * v[j].x;
             ac += w * v[j].y;
         }
@@ -539,6 +536,7 @@ template <int D, typename T>
 struct ProlongGeo {
     long long i;
     long long node[1 << D];
+    T w[1 << D];  // corner weights
     unsigned use;
     T ws, iws;  // sum of the active corners' weights and its reciprocal
 };
@@ -582,6 +580,7 @@ __device__ __forceinline__ ProlongGeo<D, T> fetch_prolong(int t, const Lists& ls
     for (int cc = 0; cc < NC; cc++) {
         bool dup;
         T w = corner<D, T>(ii, cc, cst, g.node[cc], dup);
+        g.w[cc] = w;
         if (dup) continue;
         int8_t tc = ctype[g.node[cc]];
         if (tc != T_IN && tc != T_GHOST) continue;
@@ -598,10 +597,6 @@ __device__ __forceinline__ void prolong_apply(const ProlongGeo<D, T>& g, int fn,
     typedef typename V2<T>::t T2;
     if (!(g.ws > (T)0)) return;
     const int NC = 1 << D;
-    int ii[3] = {0, 0, 0};
-    ii[0] = (int)(g.i % fn);
-    ii[1] = (int)((g.i / fn) % fn);
-    if (D == 3) ii[2] = (int)(g.i / ((long long)fn * fn));
     T2 v[1 << D];
 #pragma unroll
     for (int cc = 0; cc < NC; cc++) {
@@ -611,15 +606,11 @@ __device__ __forceinline__ void prolong_apply(const ProlongGeo<D, T>& g, int fn,
     }
     T2 xf = ldx<CG>(fx + g.i);
     T as = 0, ac = 0;
-    const long long cst0[3] = {0, 0, 0};
 #pragma unroll
     for (int cc = 0; cc < NC; cc++) {
         if (!((g.use >> cc) & 1u)) continue;
-        long long unused;
-        bool dup;
-        T w = corner<D, T>(ii, cc, cst0, unused, dup);
-        as += w * v[cc].x;
-        ac += w * v[cc].y;
+        as += g.w[cc] * v[cc].x;
+        ac += g.w[cc] * v[cc].y;
     }
     xf.x = fmadd(as, g.iws, xf.x);
     xf.y = fmadd(ac, g.iws, xf.y);

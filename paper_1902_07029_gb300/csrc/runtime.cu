@@ -49,6 +49,14 @@ extern "C" unsigned long long sulf_estimate_device_bytes(int dim, int N, int coa
     double per_level = 128.0 + 16.0 * dim + 30.0;
     if (precision == 1) per_level += 64.0 + 8.0 * dim;
     double geo = 1.0 / (1.0 - 1.0 / (double)(1 << dim));
+    // ghost-row member tables: 3^dim members x (weight 8 + 4, node 4, ghost
+    // index 4) per ghost, ghosts bounded by 8 % (2-D) / 15 % (3-D) of the box
+    // nodes on every level (the coarse levels of thin 3-D shapes approach it)
+    const double members = dim == 2 ? 9.0 : 27.0;
+    per_level += (dim == 2 ? 0.08 : 0.15) * members * 20.0;
+    // band extension operator: 16 B per entry, at most 1.5 (2-D) / 3.2 (3-D)
+    // entries per box node on any level
+    per_level += (dim == 2 ? 1.5 : 3.2) * 16.0;
     double bytes = nn0 * (per_level * geo + 49.0);
     // ghost and band arrays, allocation granularity, coarsest dense matrices
     double nc = 1;

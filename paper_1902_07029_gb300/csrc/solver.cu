@@ -198,10 +198,7 @@ int alloc_vectors(sulf_domain* d, LevelVec<T>* V, bool share_state) {
         v.rhs = (T2*)d->mem.get(nb2);
         v.x = (T2*)d->mem.get(nb2);
         v.res = (T2*)d->mem.get(nb2);
-        for (int k = 0; k < 2; k++) {
-            v.gbuf[k] = (T*)d->mem.get(sizeof(T) * (G.ng + 1));
-            v.bbuf[k] = (T2*)d->mem.get(sizeof(T2) * (G.nb + 1));
-        }
+        for (int k = 0; k < 2; k++) v.gbuf[k] = (T*)d->mem.get(sizeof(T) * (G.ng + 1));
         for (int a = 0; a < G.dim; a++) v.edge[a] = (T2*)d->mem.get(nb2);
         v.Pa = (T2*)d->mem.get(nb2);
         v.Pb = (T2*)d->mem.get(nb2);
@@ -211,7 +208,7 @@ int alloc_vectors(sulf_domain* d, LevelVec<T>* V, bool share_state) {
         if (!v.Pa || !v.Pb || !v.Ia || !v.Ib || !v.gc || !v.edge[0] || !v.edge[1] || (G.dim == 3 && !v.edge[2]))
             return sulf_fail(SULF_ENOMEM, "out of device memory");
         if ((!share_state || l > 0) && !v.Wc) return sulf_fail(SULF_ENOMEM, "out of device memory");
-        if (!v.rhs || !v.x || !v.res || !v.gbuf[0] || !v.gbuf[1] || !v.bbuf[0] || !v.bbuf[1])
+        if (!v.rhs || !v.x || !v.res || !v.gbuf[0] || !v.gbuf[1])
             return sulf_fail(SULF_ENOMEM, "out of device memory");
         if (v.Wc) SULF_CUDA_TRY(cudaMemsetAsync(v.Wc, 0, nb2, d->stream));
         SULF_CUDA_TRY(cudaMemsetAsync(v.rhs, 0, nb2, d->stream));
@@ -329,7 +326,7 @@ struct MG {
         for (int k = 0; k < d->solver.nu1; k++)
             if ((rc = relax(l))) return rc;
         d->launches += launch_residual<D, T>(d->geo[l], V[l], make_coef<T>(d, l), nullptr, d->stream);
-        d->launches += launch_extend<D, T>(d->geo[l], V[l], 4, d->stream);
+        d->launches += launch_extend<D, T>(d->geo[l], V[l], d->stream);
         d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
         int gam = d->solver.cycle == 2 ? 2 : 1;
         for (int g = 0; g < gam; g++)
@@ -925,10 +922,10 @@ int sulf_dbg_restrict(sulf_handle h, int l, double* res, double* rhs_coarse) {
     int rc = copy_in(h, h->v64[l].res, res, sizeof(double2) * G.nn);
     if (rc) return rc;
     if (h->dim == 2) {
-        h->launches += launch_extend<2, double>(G, h->v64[l], 4, h->stream);
+        h->launches += launch_extend<2, double>(G, h->v64[l], h->stream);
         h->launches += launch_restrict<2, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
     } else {
-        h->launches += launch_extend<3, double>(G, h->v64[l], 4, h->stream);
+        h->launches += launch_extend<3, double>(G, h->v64[l], h->stream);
         h->launches += launch_restrict<3, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
     }
     rc = dbg_copy_out(h, l, h->v64[l].res, res, true);

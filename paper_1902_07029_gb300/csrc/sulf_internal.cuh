@@ -57,11 +57,26 @@ struct LevelGeo {
     double* gw = nullptr;     // ng*dim*3 1-D weights at offsets 0,1,2
     float* gw32 = nullptr;
     double* gB = nullptr;     // ng*dim boundary points
+    // each ghost's boundary row as a member table, member-major (kk * ng + gi)
+    // over the K = 3^dim members of its upwind stencil: tensor weight (0 when
+    // absent), box node, ghost index of the member or -1
+    double* gwk = nullptr;
+    float* gwk32 = nullptr;
+    int* gnode = nullptr;
+    int* gsrc = nullptr;
     int nb = 0;
     int* bidx = nullptr;     // band nodes, box order
     int* bref = nullptr;     // nb*dim: >=0 band index, -1 none, <=-2 ghost node -(idx+2)
     double* ban = nullptr;   // nb*dim |n_a|
     float* ban32 = nullptr;
+    // the band extension as one linear operator (CSR over band nodes): the
+    // extended defect at band node b is sum_j eval[j] * res(eidx[j]) over
+    // j in [eptr[b], eptr[b+1]), eidx a ghost node
+    int* eptr = nullptr;
+    int* eidx = nullptr;
+    double* eval = nullptr;
+    float* eval32 = nullptr;
+    long long ne = 0;
     int nact = 0;            // coarsest level: active list and map
     int* act = nullptr;
     int* apos = nullptr;
@@ -77,7 +92,6 @@ struct LevelVec {
     T2* x = nullptr;    // unknown: Newton update (finest) or coarse-grid error
     T2* res = nullptr;  // defect rhs - J x (band entries: extended defect)
     T* gbuf[2] = {nullptr, nullptr};   // ghost s values between relaxation passes
-    T2* bbuf[2] = {nullptr, nullptr};  // band values between extension steps
     T* Ainv = nullptr;  // coarsest level: inverse of the assembled Jacobian
     T* A = nullptr;     // coarsest level: work matrix
     // Jacobian stencil coefficients, refreshed once per Newton iteration from
@@ -136,7 +150,7 @@ template <int D, typename T>
 int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, unsigned long long* norm,
                     cudaStream_t s);
 template <int D, typename T>
-int launch_extend(const LevelGeo& L, const LevelVec<T>& V, int steps, cudaStream_t s);
+int launch_extend(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s);
 template <int D, typename T>
 int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
                     cudaStream_t s);

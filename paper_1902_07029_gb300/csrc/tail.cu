@@ -27,13 +27,12 @@ struct TailLevel {
     int n;
     long long st1, st2;
     const int8_t* type;
-    const int* gpos;
-    const int8_t* gm;
-    const T* gw;
+    stages::GhostTab<T> tab;
     int nb;
     const int* bidx;
-    const int* bref;
-    const T* ban;
+    const int* eptr;
+    const int* eidx;
+    const T* eval;
     int nact;
     const int* act;
     const T* Ainv;
@@ -41,7 +40,6 @@ struct TailLevel {
     T2* x;
     T2* res;
     T* gbuf[2];
-    T2* bbuf[2];
     const T2* edge[3];
     const T2* Pa;
     const T2* Pb;
@@ -51,8 +49,8 @@ struct TailLevel {
 };
 
 struct TailParams {
-    int l0, L, nu1, nu2, passes, ext, pointwise;
-    double tau, cfl;
+    int l0, L, nu1, nu2, passes, pointwise;
+    double tau;
 };
 
 template <int D, typename T>
@@ -88,8 +86,8 @@ __device__ void tail_relax(const TailLevel<T>& v, const TailParams& pr, int tid,
         const T* sin = first ? nullptr : v.gbuf[(p - 1) & 1];
         T* sout = v.gbuf[p & 1];
         for (int gi = tid; gi < v.ls.ng; gi += nthr)
-            stages::ghost_pass_node<D, T, false>(gi, v.ls.lg, v.gpos, v.gm, v.gw, v.gc, v.rhs, v.x, sin, sout, v.st1,
-                                                v.st2, (T)pr.tau, first, last);
+            stages::ghost_pass_node<D, T, false>(gi, v.ls.lg, v.tab, v.gc, v.rhs, v.x, sin, sout, (T)pr.tau, first,
+                                                last);
         __syncthreads();
     }
     if (pr.passes == 1) {
@@ -113,15 +111,11 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T>* __
         stages::CoefPtr<D, T> cf = coefs_of<D, T>(f);
         int tot = f.ls.n0 + f.ls.n1 + f.ls.ng;
         for (int t = tid; t < tot; t += nthr)
-            stages::residual_node<D, T, false>(t, f.ls, f.gm, f.gw, cf, f.rhs, f.x, f.res, f.st1, f.st2);
+            stages::residual_node<D, T, false>(t, f.ls, f.tab, cf, f.rhs, f.x, f.res, f.st1, f.st2);
         __syncthreads();
-        for (int k = 0; k < pr.ext; k++) {
-            bool first = k == 0, last = k == pr.ext - 1;
-            for (int b = tid; b < f.nb; b += nthr)
-                stages::extend_node<D, T, false>(b, f.bidx, f.bref, f.ban, f.res, f.bbuf[(k + 1) & 1], f.bbuf[k & 1],
-                                                (T)pr.cfl, first, last);
-            __syncthreads();
-        }
+        for (int b = tid; b < f.nb; b += nthr)
+            stages::extend_node<T, false>(b, f.eptr, f.eidx, f.eval, f.bidx, f.res);
+        __syncthreads();
         int ctot = c.ls.n0 + c.ls.n1 + c.ls.ng;
         for (int t = tid; t < ctot; t += nthr)
             stages::restrict_node<D, T, false>(t, c.ls, c.type, c.n, f.type, f.n, f.res, c.rhs, c.x);
@@ -164,23 +158,19 @@ TailLevel<T> describe(const LevelGeo& G, const LevelVec<T>& V) {
     t.st1 = G.st[1];
     t.st2 = G.st[2];
     t.type = G.type;
-    t.gpos = G.gpos;
-    t.gm = G.gm;
-    t.gw = std::is_same<T, float>::value ? (const T*)G.gw32 : (const T*)G.gw;
+    t.tab = stages::ghost_tab<T>(G);
     t.nb = G.nb;
     t.bidx = G.bidx;
-    t.bref = G.bref;
-    t.ban = std::is_same<T, float>::value ? (const T*)G.ban32 : (const T*)G.ban;
+    t.eptr = G.eptr;
+    t.eidx = G.eidx;
+    t.eval = std::is_same<T, float>::value ? (const T*)G.eval32 : (const T*)G.eval;
     t.nact = G.nact;
     t.act = G.act;
     t.Ainv = V.Ainv;
     t.rhs = V.rhs;
     t.x = V.x;
     t.res = V.res;
-    for (int k = 0; k < 2; k++) {
-        t.gbuf[k] = V.gbuf[k];
-        t.bbuf[k] = V.bbuf[k];
-    }
+    for (int k = 0; k < 2; k++) t.gbuf[k] = V.gbuf[k];
     for (int a = 0; a < 3; a++) t.edge[a] = V.edge[a];
     t.Pa = V.Pa;
     t.Pb = V.Pb;
@@ -214,10 +204,9 @@ TailParams make_params(int l0, int L, const sulf_solver& sv, int D) {
     pr.nu1 = sv.nu1;
     pr.nu2 = sv.nu2;
     pr.passes = sv.ghost_sweeps;
-    pr.ext = 4;
     pr.pointwise = sv.smoother == 1;
     pr.tau = sv.tau_s;
-    pr.cfl = D == 2 ? 0.5 : 1.0 / 3.0;
+    (void)D;
     return pr;
 }
 
