@@ -153,6 +153,13 @@ def measured_peaks():
         return {}
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count()
+
+
 def cpu_baseline(name, budget_s=20.0, precision="fp64"):
     """The oracle as it stands, single-threaded, on a bounded sample: the first
     CN steps of the same workload until about budget_s seconds of CPU work."""
@@ -173,7 +180,7 @@ def cpu_baseline(name, budget_s=20.0, precision="fp64"):
         if el >= budget_s or steps >= w["steps"]:
             break
     del info
-    return {"value": nact * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": nact * steps / el, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle",
             "sample": f"first {steps} CN step(s) of {name} ({nact} active nodes), {el:.1f} s, 1 thread"}
 
 
@@ -211,7 +218,7 @@ def run_reference(args):
            "ms_per_step": 1e3 * el / k_eff, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": args.workload, "N": N, "dim": dim, "dt": "h", "precision": "fp64"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle",
                             "sample": f"first {k_eff} of {args.steps} requested CN steps of {args.workload}"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -275,7 +282,8 @@ def run_gpu(args):
         relax_n += n
     torch.cuda.synchronize()
     dom.set_profiling(False)
-    elapsed_ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    elapsed_ms = sum(step_ms)
     st1 = dom.stats()
     launches = st1["kernel_launches"] - launches0
     value, elapsed_ms = whole_job_value(elapsed_ms, nact * args.steps, device=dev)
@@ -331,6 +339,8 @@ def run_gpu(args):
                           "cycle": "V(2,2) red-black collective GS, 4 ghost passes",
                           "newton_tol": 1e-10, "lin_rtol": 1e-10, "l2": "flushed between CN steps (512 MB write)",
                           "newton_iters": st1["newton_total"] - newton0, "cycles": st1["cycles_total"] - cyc0},
+               "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                                   "p99": float(np.percentile(step_ms, 99)), "max": float(max(step_ms))},
                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(out), flush=True)
     dom.close()
@@ -439,34 +449,85 @@ def run_serve(args):
         # solution at dt = h/2 (as the 65^2 disk at dt = h), so dt = h/4 there
         dt = 2.0 / N if dim == 2 else (0.5 if N >= 128 else 0.25) * 2.0 / N
         jobs.append((phi, dim, N, cN, m, dt, nsteps))
-    rate = args.rate
-    gaps = rng.exponential(1.0 / rate, size=len(jobs))
-    srv = pkg.Server(budget_bytes=150 << 30, nworkers=args.streams)
-    t0 = time.perf_counter()
-    ids = []
-    for (phi, dim, N, cN, m, dt, nsteps), gap in zip(jobs, gaps):
-        time.sleep(gap)
-        ids.append(srv.submit(phi, dim, N, m, dt, nsteps, coarsest_N=cN, precision=1))
-    failed = []
-    nodes = 0.0
-    for i, (phi, dim, N, cN, m, dt, nsteps) in zip(ids, jobs):
-        try:
-            s, c, res = srv.wait(i)
-            nodes += float(np.count_nonzero(phi < 0)) * nsteps
-        except pkg.SulfError as e:
-            failed.append({"dim": dim, "N": N, "nsteps": nsteps, "error": str(e)[:160]})
-    el = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
-    line = {"metric": "jobs/s and p50/p99 job latency", "value": st["completed"] / el, "unit": "jobs/s",
+    rates = [float(r) for r in str(args.rate).split(",")]
+    gap_rng = np.random.default_rng(6)
+    unit_gaps = gap_rng.exponential(1.0, size=len(jobs))  # the same arrival pattern, scaled per rate
+    runs = []
+    for rate in rates:
+        srv = pkg.Server(budget_bytes=150 << 30, nworkers=args.streams)
+        t0 = time.perf_counter()
+        ids = []
+        for (phi, dim, N, cN, m, dt, nsteps), g in zip(jobs, unit_gaps):
+            time.sleep(g / rate)
+            ids.append(srv.submit(phi, dim, N, m, dt, nsteps, coarsest_N=cN, precision=1))
+        failed = []
+        nodes = 0.0
+        for i, (phi, dim, N, cN, m, dt, nsteps) in zip(ids, jobs):
+            try:
+                s, c, res = srv.wait(i)
+                nodes += float(np.count_nonzero(phi < 0)) * nsteps
+            except pkg.SulfError as e:
+                failed.append({"dim": dim, "N": N, "nsteps": nsteps, "error": str(e)[:160]})
+        el = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        runs.append({"arrival_rate_per_s": rate, "jobs_per_s": st["completed"] / el, "p50_ms": st["p50_ms"],
+                     "p99_ms": st["p99_ms"], "completed": st["completed"], "failed": len(failed), "failures": failed,
+                     "max_running": st["max_running"], "peak_reserved_GB": st["peak_reserved_bytes"] / 2 ** 30,
+                     "inside_node_updates_per_s": nodes / el, "wall_s": el})
+    r0 = runs[0]
+    line = {"metric": "jobs/s and p50/p99 job latency", "value": r0["jobs_per_s"], "unit": "jobs/s",
             "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
             "config": {"workload": "Poisson-arrival serving of random star / rounded-box jobs", "jobs": len(jobs),
-                       "arrival_rate_per_s": rate, "workers": args.streams, "budget_GB": 150},
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"], "failed": len(failed),
-            "failures": failed,
-            "max_running": st["max_running"], "peak_reserved_GB": st["peak_reserved_bytes"] / 2 ** 30,
-            "inside_node_updates_per_s": nodes / el, "wall_s": el}
+                       "arrival_rate_per_s": r0["arrival_rate_per_s"], "workers": args.streams, "budget_GB": 150},
+            "p50_ms": r0["p50_ms"], "p99_ms": r0["p99_ms"], "completed": r0["completed"], "failed": r0["failed"],
+            "failures": r0["failures"], "max_running": r0["max_running"],
+            "peak_reserved_GB": r0["peak_reserved_GB"], "inside_node_updates_per_s": r0["inside_node_updates_per_s"],
+            "wall_s": r0["wall_s"], "sweep": runs if len(runs) > 1 else None}
+    print(json.dumps(line), flush=True)
+
+
+def run_rho(args):
+    """Multigrid convergence factors: the paper's W(2,1) and the default V(2,2),
+    collective and pointwise red-black smoothing, on the star at several N.
+    rho is the geometric mean of the defect ratios of cycles 4..12 of a linear
+    solve with the Jacobian at the state after one CN step and a seeded random
+    right-hand side."""
+    import torch
+
+    import paper_1902_07029_gb300 as pkg
+
+    pkg.build()
+    rows = []
+    for N in (128, 256, 512, 1024):
+        phi = workloads.star(N)
+        dt = 2.0 / N
+        for name, kw in (("V(2,2) collective", dict()), ("W(2,1) collective", dict(cycle=2, nu1=2, nu2=1)),
+                         ("V(2,2) pointwise", dict(smoother=1)),
+                         ("W(2,1) pointwise", dict(cycle=2, nu1=2, nu2=1, smoother=1))):
+            dom = pkg.Domain(phi, 2, (-1.0, 1.0), N)
+            dom.set_model(workloads.PAPER_MODEL)
+            dom.step(dt, 1)
+            dom.set_solver(**kw)
+            s, c, t = dom.get_state()
+            W = np.zeros(2 * s.size)
+            W[0::2] = s.ravel()
+            W[1::2] = c.ravel()
+            act = ((t == 1) | (t == 2)).ravel()
+            rng = np.random.default_rng(7)
+            rhs = np.zeros_like(W)
+            rhs[0::2][act] = rng.standard_normal(act.sum())
+            rhs[1::2][act] = rng.standard_normal(act.sum())
+            torch.cuda.synchronize()
+            _, rn = dom.cycles(dt, W, rhs, 12)
+            ratios = rn[3:] / rn[2:-1]
+            rows.append({"N": N, "cycle": name, "rho": float(np.exp(np.mean(np.log(ratios))))})
+            dom.close()
+    line = {"metric": "multigrid convergence factor", "value": None, "unit": "defect ratio per cycle",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "star r - 0.6 - 0.2 sin 5 theta, Jacobian after one CN step, dt = h"},
+            "rows": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -476,11 +537,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sulfmg", choices=["sulfmg", "reference"])
-    ap.add_argument("--workload", default="star1025", choices=sorted(workloads.WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="star1025", choices=sorted(workloads.WORKLOADS) + ["batch", "serve", "rho"])
     ap.add_argument("--instances", type=int, default=256, help="batch: number of instances")
     ap.add_argument("--streams", type=int, default=8, help="batch/serve: worker streams")
     ap.add_argument("--jobs", type=int, default=40, help="serve: number of jobs")
-    ap.add_argument("--rate", type=float, default=4.0, help="serve: Poisson arrival rate (jobs/s)")
+    ap.add_argument("--rate", default="4.0",
+                    help="serve: Poisson arrival rate(s) in jobs/s, comma-separated for a sweep")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle CPU work for cpu_baseline")
     args = ap.parse_args()
@@ -490,6 +552,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "rho":
+        run_rho(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -142,6 +142,22 @@ int sulf_set_state(sulf_handle h, const double* s, const double* c, double t);
 /* Same, from device arrays. */
 int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_dev, double t);
 
+/* Source terms of the manufactured-solution accuracy tests (Sec. 4.1): f1 and
+   f2 are added to the right-hand sides of Eq. maineq and averaged over the CN
+   step, i.e. F^s_p -= (f1_old[p] + f1_new[p]) / 2 on inside nodes and
+   F^c_p -= (f2_old[p] + f2_new[p]) / 2 on inside and ghost nodes.  Host
+   arrays of (N+1)^dim values at t_n (old) and t_{n+1} (new), copied; they
+   apply to every following step until changed.  All four NULL clears them;
+   a partial set is SULF_EINVAL. */
+int sulf_set_sources(sulf_handle h, const double* f1_old, const double* f1_new, const double* f2_old,
+                     const double* f2_new);
+
+/* Dirichlet values s_b at the ghosts' boundary points B (Eq. BCs), one per
+   finest-level ghost in the order of sulf_dbg_level_ghosts (box order of the
+   ghost nodes).  Copied; they apply to every following step until changed.
+   NULL restores the model's constant s_ext. */
+int sulf_set_ghost_values(sulf_handle h, const double* sb);
+
 int sulf_get_stats(sulf_handle h, sulf_stats* out);
 
 /* Kernel timing for measurement: the library brackets launches of the

@@ -75,6 +75,8 @@ _SIGS = {
     "sulf_set_state": (ctypes.c_int, [P, _dp, _dp, ctypes.c_double]),
     "sulf_set_state_device": (ctypes.c_int, [P, P, P, ctypes.c_double]),
     "sulf_get_stats": (ctypes.c_int, [P, ctypes.POINTER(SulfStats)]),
+    "sulf_set_sources": (ctypes.c_int, [P, _dp, _dp, _dp, _dp]),
+    "sulf_set_ghost_values": (ctypes.c_int, [P, _dp]),
     "sulf_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
     "sulf_kernel_time": (ctypes.c_int, [P, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "sulf_newton_residual_noalloc": (ctypes.c_int, [P, ctypes.c_double, P, P, P, P]),
@@ -218,6 +220,24 @@ class Domain:
         pointers as ints); queued on the handle's stream, no allocation."""
         _chk(self.lib, self.lib.sulf_newton_residual_noalloc(self.h, dt, P(W_ptr), P(Wn_ptr), P(F_ptr),
                                                              P(fnorm_ptr)))
+
+    def set_sources(self, f1_old=None, f1_new=None, f2_old=None, f2_new=None):
+        """Manufactured source terms at t_n and t_{n+1} (box arrays), or none."""
+        if f1_old is None:
+            _chk(self.lib, self.lib.sulf_set_sources(self.h, None, None, None, None))
+            return
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (f1_old, f1_new, f2_old, f2_new)]
+        if any(a.size != self.nn for a in arrs):
+            raise ValueError("source arrays must hold (N+1)^dim values")
+        _chk(self.lib, self.lib.sulf_set_sources(self.h, *[_d(a) for a in arrs]))
+
+    def set_ghost_values(self, sb=None):
+        """Dirichlet values per finest-level ghost (ghost order), or None for s_ext."""
+        if sb is None:
+            _chk(self.lib, self.lib.sulf_set_ghost_values(self.h, None))
+            return
+        sb = np.ascontiguousarray(sb, dtype=np.float64).ravel()
+        _chk(self.lib, self.lib.sulf_set_ghost_values(self.h, _d(sb)))
 
     def set_profiling(self, on):
         """0/False off; 1/True the first finest-level sweep of every cycle; 2

@@ -594,7 +594,19 @@ __global__ void __launch_bounds__(kT) k_old_time(Lists ls, const double2* __rest
         double Ls = Ls_h<D>(p, Wn, of, f, phd);
         g.x = -ph * w.x * f.idt - 0.5 * Ls;
     }
+    if (f.src) {  // manufactured sources: F^s -= (f1o + f1n)/2 inside, F^c -= (f2o + f2n)/2
+        double2 q = f.src[p];
+        if (kind == 1) g.x -= q.x;
+        g.y -= q.y;
+    }
     G[p] = g;
+}
+
+__global__ void k_average_sources(long long nn, const double* __restrict__ f4, double2* __restrict__ src) {
+    pdl_enter();
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    src[i] = make_double2(0.5 * (f4[i] + f4[nn + i]), 0.5 * (f4[2 * nn + i] + f4[3 * nn + i]));
 }
 
 template <int D>
@@ -618,7 +630,7 @@ __global__ void __launch_bounds__(kT) k_newton_F(Lists ls, GhostTab<double> tb, 
             double Ls = Ls_h<D>(p, W, of, f, phd);
             out.x = ph * w.x * f.idt - 0.5 * Ls + g.x;
         } else {
-            out.x = stages::row_dot<D, double, false>(tb, gi, nullptr, W, nullptr, true) - f.sb;
+            out.x = stages::row_dot<D, double, false>(tb, gi, nullptr, W, nullptr, true) - (f.sbg ? f.sbg[gi] : f.sb);
         }
         F[p] = out;
         unsigned long long a0 = abs_bits(out.x), a1 = abs_bits(out.y);
@@ -891,6 +903,11 @@ int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* 
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
     launch_k(k_norm_active, grid_for(tot), block_for(tot), 0, s, ls, v, norm);
+    return 1;
+}
+
+int launch_average_sources(long long nn, const double* f4, double2* src, cudaStream_t s) {
+    launch_k(k_average_sources, grid_for(nn), block_for(nn), 0, s, nn, f4, src);
     return 1;
 }
 

@@ -84,6 +84,12 @@ struct sulf_domain {
     unsigned long long* hnorm = nullptr;  // pinned
     int* dsing = nullptr;
     double* stage = nullptr;  // 2*nn doubles + nn bytes, device staging for state I/O
+    // manufactured-solution inputs (optional): CN-averaged sources per box
+    // node, their upload staging, and Dirichlet values per ghost
+    double2* src = nullptr;
+    double* src_stage = nullptr;
+    double* sbg = nullptr;
+    bool src_on = false, sbg_on = false;
     sulf_model model{};
     sulf_solver solver{};
     cudaStream_t stream = nullptr;
@@ -184,6 +190,8 @@ FConst make_fconst(const sulf_domain* d) {
     f.idt = 1.0 / d->dt;
     f.dh2 = m.d / (2.0 * h * h);
     f.sb = m.s_ext;
+    f.src = d->src_on ? d->src : nullptr;
+    f.sbg = d->sbg_on ? d->sbg : nullptr;
     return f;
 }
 
@@ -756,6 +764,44 @@ int sulf_set_state(sulf_handle h, const double* s, const double* c, double t) {
     SULF_CUDA_TRY(cudaMemcpyAsync(h->stage, s, sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
     SULF_CUDA_TRY(cudaMemcpyAsync(h->stage + nn, c, sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
     return sulf_set_state_device(h, h->stage, h->stage + nn, t);
+}
+
+int sulf_set_sources(sulf_handle h, const double* f1_old, const double* f1_new, const double* f2_old,
+                     const double* f2_new) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    const int given = (f1_old != nullptr) + (f1_new != nullptr) + (f2_old != nullptr) + (f2_new != nullptr);
+    if (given == 0) {
+        h->src_on = false;
+        return SULF_OK;
+    }
+    if (given != 4) return sulf_fail(SULF_EINVAL, "give all four source arrays or none");
+    const long long nn = h->geo[0].nn;
+    if (!h->src) h->src = (double2*)h->mem.get(sizeof(double2) * nn);
+    if (!h->src_stage) h->src_stage = (double*)h->mem.get(sizeof(double) * 4 * nn);
+    if (!h->src || !h->src_stage) return sulf_fail(SULF_ENOMEM, "out of device memory");
+    const double* in[4] = {f1_old, f1_new, f2_old, f2_new};
+    for (int k = 0; k < 4; k++)
+        SULF_CUDA_TRY(cudaMemcpyAsync(h->src_stage + k * nn, in[k], sizeof(double) * nn, cudaMemcpyHostToDevice,
+                                      h->stream));
+    h->launches += launch_average_sources(nn, h->src_stage, h->src, h->stream);
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->src_on = true;
+    return SULF_OK;
+}
+
+int sulf_set_ghost_values(sulf_handle h, const double* sb) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    if (!sb) {
+        h->sbg_on = false;
+        return SULF_OK;
+    }
+    const int ng = h->geo[0].ng;
+    if (!h->sbg) h->sbg = (double*)h->mem.get(sizeof(double) * (ng + 1));
+    if (!h->sbg) return sulf_fail(SULF_ENOMEM, "out of device memory");
+    SULF_CUDA_TRY(cudaMemcpyAsync(h->sbg, sb, sizeof(double) * ng, cudaMemcpyHostToDevice, h->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->sbg_on = true;
+    return SULF_OK;
 }
 
 int sulf_get_stats(sulf_handle h, sulf_stats* o) {

@@ -121,6 +121,8 @@ struct FConst {
     double alpha, beta, amc, ams;  // a/m_c, a/m_s
     double idt, dh2;               // 1/dt, d/(2h^2)
     double sb;                     // Dirichlet value
+    const double2* src;            // optional CN-averaged sources (f1, f2) per box node
+    const double* sbg;             // optional Dirichlet value per ghost
 };
 
 // Device memory owned by one handle, from the device's stream-ordered pool
@@ -174,6 +176,9 @@ int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, doubl
 int launch_newton_update(const LevelGeo& L, double2* W, const double2* x, unsigned long long* norms,
                          cudaStream_t s);
 int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* norm, cudaStream_t s);
+
+// CN average of manufactured source terms: src = ((f1o+f1n)/2, (f2o+f2n)/2)
+int launch_average_sources(long long nn, const double* f4, double2* src, cudaStream_t s);
 
 // mixed precision transfers on the finest level (active nodes)
 int launch_to_float(const LevelGeo& L, const double2* src, float2* dst, cudaStream_t s);

@@ -397,3 +397,22 @@ def test_invalid_domains_rejected(oracle_mod):
         oracle_mod.Oracle(workloads.disk(32, 1.2), 2, -1.0, 1.0, 32)  # touches the box edge
     with pytest.raises(oracle_mod.OracleError):
         oracle_mod.Oracle(workloads.disk(32) + 5.0, 2, -1.0, 1.0, 32)  # no inside node
+
+
+def test_manufactured_sources_match_symbolic_derivation():
+    """The hand-written sources of the Sec. 4.1 manufactured solution equal a
+    symbolic derivation from Eq. maineq (sympy)."""
+    pytest.importorskip("sympy")
+    import manufactured as M
+
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-2, 2, 200)
+    Y = rng.uniform(-2, 2, 200)
+    fs, fc, f1s, f2s = M.symbolic(tuple(PARAMS[:6]))
+    for t in (0.0, 0.37, 1.0):
+        s, c = M.exact(PARAMS[:6], X, Y, t)
+        f1, f2 = M.sources(PARAMS[:6], X, Y, t)
+        assert np.allclose(s, fs(X, Y, t), rtol=1e-14, atol=0)
+        assert np.allclose(c, fc(X, Y, t), rtol=1e-14, atol=0)
+        assert np.allclose(f1, f1s(X, Y, t), rtol=1e-12, atol=1e-9)
+        assert np.allclose(f2, f2s(X, Y, t), rtol=1e-12, atol=1e-9)
