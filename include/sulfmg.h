@@ -180,6 +180,8 @@ int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
                     not read)
      F_dev          output, same layout; written on active nodes only
      fnorm_dev      output, one double: |F|_inf over the active nodes
+   It evaluates the model's equations with the constant s_ext: the optional
+   inputs of sulf_set_sources and sulf_set_ghost_values are not applied.
    Work is queued on the handle's stream and the call returns without waiting.
    Scratch: a static array inside the library holding 65536 partial maxima
    (512 KiB), kept by every GPU that loads the library until the process exits;
