@@ -66,6 +66,8 @@ def _load():
         "oracle_level_band": (ctypes.c_int, [P, ctypes.c_int, lp, lp, dp]),
         "oracle_set_ghost_sb": (ctypes.c_int, [P, dp]),
         "oracle_set_sources": (ctypes.c_int, [P, dp, dp, dp, dp]),
+        "oracle_set_bc": (ctypes.c_int, [P, ctypes.c_int]),
+        "oracle_level_rows": (ctypes.c_int, [P, ctypes.c_int, dp, dp]),
         "oracle_eval_F": (ctypes.c_int, [P, ctypes.c_double, dp, dp, dp]),
         "oracle_apply_J": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, dp, dp, dp]),
         "oracle_dense_J": (ctypes.c_int, [P, ctypes.c_double, dp, dp, lp]),
@@ -208,6 +210,21 @@ class Oracle:
         self._chk(self.lib.oracle_level_ghosts(self.h, l, _l(idx), _b(kind), _b(m), _d(w), _d(B)))
         return dict(idx=idx[:ng], kind=kind[:ng], m=m[:ng * d].reshape(ng, d), w=w[:ng * d * 3].reshape(ng, d, 3),
                     B=B[:ng * d].reshape(ng, d))
+
+    def level_rows(self, l):
+        """Member weights of every ghost row (ng x 3^dim) and the unit normal of
+        phi~ at each boundary point (ng x dim)."""
+        ng = self.level_info(l)["ng"]
+        d = self.dim
+        K = 9 if d == 2 else 27
+        wk = np.zeros(max(ng, 1) * K)
+        nt = np.zeros(max(ng, 1) * d)
+        self._chk(self.lib.oracle_level_rows(self.h, l, _d(wk), _d(nt)))
+        return wk[:ng * K].reshape(ng, K), nt[:ng * d].reshape(ng, d)
+
+    def set_bc(self, bc):
+        """0: Dirichlet s = s_b (Eq. BCs); 1: Neumann ds/dn = s_b (Eq. BCsN)."""
+        self._chk(self.lib.oracle_set_bc(self.h, int(bc)))
 
     def level_band(self, l):
         nb = self.level_info(l)["nb"]

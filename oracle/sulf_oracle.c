@@ -90,6 +90,10 @@ typedef struct {
     signed char *gm;    /* ng*dim */
     double *gw;         /* ng*dim*3, offsets 0,1,2 */
     double *gB;         /* ng*dim */
+    signed char *gord;  /* ng*dim per-axis interpolation orders of the row */
+    double *gth;        /* ng*dim theta per axis at B */
+    double *gnt;        /* ng*dim unit normal of phi~ at B (Neumann rows) */
+    double *gwk;        /* ng*3^dim weights of the row's stencil members */
     int nb;
     long *bidx;
     long *bup;          /* nb*dim, -1 when there is no upwind value */
@@ -108,6 +112,7 @@ typedef struct {
     /* model, Eq. maineq and Eq. dataeq */
     double a, d, m_s, m_c, alpha, beta, s_ext, s0, c0;
     /* solver */
+    int bc; /* 0 Dirichlet (Eq. BCs), 1 Neumann for s (Eq. BCsN) */
     int nu1, nu2, cycle, max_newton, max_cycles, smoother, ext_steps, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;
     double t, dt;
@@ -192,6 +197,70 @@ static double lag(int order, int k, double xi)
     return 0.0;
 }
 
+/* derivative of lag with respect to xi: the 1-D first-derivative weights of
+   Eq. intcoeffsN (times h) for the quadratic, (1, -1) for the linear, 0 for
+   the constant */
+static double dlag(int order, int k, double xi)
+{
+    if (order == 0) return 0.0;
+    if (order == 2) {
+        if (k == 0) return xi + 0.5;
+        if (k == 1) return -2.0 * xi;
+        return xi - 0.5;
+    }
+    if (k == 0) return 1.0;
+    if (k == 1) return -1.0;
+    return 0.0;
+}
+
+/* gradient of the tensor interpolant phi~ of the given order on the upwind
+   stencil of ghost g, at the local coordinates xi (Eq. Neumanntilde: n~* =
+   grad phi~); d/dX_a = (m_a / h) d/dxi_a */
+static void grad_phi_tilde(const OLevel *L, int order, long g, const int *m, const double *xi, double *gr)
+{
+    int nk = ipow3(L->dim);
+    for (int a = 0; a < L->dim; a++) gr[a] = 0.0;
+    for (int kk = 0; kk < nk; kk++) {
+        int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
+        long node = g;
+        int skip = 0;
+        for (int a = 0; a < L->dim; a++) {
+            if (order == 1 && k[a] == 2) skip = 1;
+            node -= (long)m[a] * k[a] * L->st[a];
+        }
+        if (skip) continue;
+        for (int a = 0; a < L->dim; a++) {
+            double t = (m[a] / L->h) * dlag(order, k[a], xi[a]);
+            for (int b = 0; b < L->dim; b++)
+                if (b != a) t *= lag(order, k[b], xi[b]);
+            gr[a] += t * L->phi[node];
+        }
+    }
+}
+
+/* weight of stencil member kk in a ghost's row.  Dirichlet (Eq. JssD): the
+   tensor product of the 1-D value weights.  Neumann (Eq. JccN, built
+   dimension by dimension): n~ . grad s~ at B, i.e. sum over axes a of
+   n~_a (m_a / h) dlag_a prod_{b != a} lag_b. */
+static double member_weight(int bc, int D, double h, const int *m, const int *ord, const double *th,
+                            const double *nt, int kk)
+{
+    int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
+    if (bc == 0) {
+        double w = 1.0;
+        for (int a = 0; a < D; a++) w *= lag(ord[a], k[a], th[a]);
+        return w;
+    }
+    double w = 0.0;
+    for (int a = 0; a < D; a++) {
+        double t = nt[a] * (m[a] / h) * dlag(ord[a], k[a], th[a]);
+        for (int b = 0; b < D; b++)
+            if (b != a) t *= lag(ord[b], k[b], th[b]);
+        w += t;
+    }
+    return w;
+}
+
 /* tensor-product interpolant (Eq. JssD built dimension by dimension) of phi on
    the upwind stencil of the ghost at box index g (coordinates ii, signs m),
    evaluated at X.  The local coordinate xi_a = 1 - m_a (G_a - X_a) / h equals
@@ -229,19 +298,15 @@ static int stencil_in_box(const OLevel *L, const int *ii, const int *m, int orde
     return 1;
 }
 
-/* does every stencil node with a nonzero tensor weight belong to the active set? */
-static int weighted_nodes_active(const OLevel *L, long g, const int *m, const double *w)
+/* does every stencil node with a nonzero member weight belong to the active set? */
+static int weighted_nodes_active(const OLevel *L, long g, const int *m, const double *wk)
 {
     int nk = ipow3(L->dim);
     for (int kk = 0; kk < nk; kk++) {
         int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
-        double wt = 1.0;
         long node = g;
-        for (int a = 0; a < L->dim; a++) {
-            wt *= w[3 * a + k[a]];
-            node -= (long)m[a] * k[a] * L->st[a];
-        }
-        if (wt != 0.0 && !active(L->type[node])) return 0;
+        for (int a = 0; a < L->dim; a++) node -= (long)m[a] * k[a] * L->st[a];
+        if (wk[kk] != 0.0 && !active(L->type[node])) return 0;
     }
     return 1;
 }
@@ -255,12 +320,22 @@ static int weighted_nodes_active(const OLevel *L, long g, const int *m, const do
    node it weights to be active; the per-axis interpolation orders tried are
    all 2 (the paper's row), all 1, then order 0 on the axis with the smallest
    |n_a| (others 2, then 1), then on the two smallest (3-D); else the identity
-   row (R6).  Returns 0 (all axes quadratic), 1 (reduced order) or 2 (identity). */
-static int ghost_geometry(const OLevel *L, long g, signed char *m_out, double *w_out, double *B_out)
+   row (R6).  Returns 0 (all axes quadratic), 1 (reduced order) or 2 (identity).
+   Also returns the per-axis orders and theta of the row, the unit normal of
+   phi~ at B (the quadratic interpolant where its stencil fits in the box, else
+   the linear one, else the node normal), and the member weights for the
+   boundary condition bc.  The activity test uses the member weights, so a
+   Neumann row (whose derivative weights reach members that a value weight
+   misses when theta = 0) is checked on the nodes it actually uses.  The
+   identity row is s_g for Dirichlet and s_g / h for Neumann (the scale of a
+   derivative row). */
+static int ghost_geometry(const OLevel *L, long g, int bc, signed char *m_out, double *w_out, double *B_out,
+                          signed char *ord_out, double *th_out, double *nt_out, double *wk_out)
 {
     int ii[3];
     coords(L, g, ii);
     int D = L->dim;
+    int nk = ipow3(D);
     double gr[3] = {0, 0, 0}, n[3] = {0, 0, 0};
     grad_phi(L, g, ii, gr);
     double nrm = 0.0;
@@ -298,6 +373,7 @@ static int ghost_geometry(const OLevel *L, long g, signed char *m_out, double *w
             border = order;
         }
     }
+    double nt[3] = {n[0], n[1], n[2]};
     if (border) {
         /* axes by increasing |n_a| (ties: lower axis first) */
         int ax[3] = {0, 1, 2};
@@ -310,14 +386,28 @@ static int ghost_geometry(const OLevel *L, long g, signed char *m_out, double *w
                 }
         double th[3] = {0, 0, 0};
         for (int a = 0; a < D; a++) th[a] = 1.0 - m[a] * ((L->lo + ii[a] * L->h) - B[a]) / L->h;
+        int q = stencil_in_box(L, ii, m, 2) ? 2 : (stencil_in_box(L, ii, m, 1) ? 1 : 0);
+        if (q) {
+            double gt[3] = {0, 0, 0}, gn = 0.0;
+            grad_phi_tilde(L, q, g, m, th, gt);
+            for (int a = 0; a < D; a++) gn += gt[a] * gt[a];
+            gn = sqrt(gn);
+            if (gn > 0.0)
+                for (int a = 0; a < D; a++) nt[a] = gt[a] / gn;
+        }
         for (int nzero = 0; nzero < D; nzero++) {
             for (int top = border; top >= 1; top--) {
                 int ord[3] = {top, top, top};
                 for (int z = 0; z < nzero; z++) ord[ax[z]] = 0;
-                for (int a = 0; a < D; a++)
-                    for (int k = 0; k < 3; k++) w_out[3 * a + k] = lag(ord[a], k, th[a]);
-                if (weighted_nodes_active(L, g, m, w_out)) {
-                    for (int a = 0; a < D; a++) B_out[a] = B[a];
+                for (int kk = 0; kk < nk; kk++) wk_out[kk] = member_weight(bc, D, L->h, m, ord, th, nt, kk);
+                if (weighted_nodes_active(L, g, m, wk_out)) {
+                    for (int a = 0; a < D; a++) {
+                        for (int k = 0; k < 3; k++) w_out[3 * a + k] = lag(ord[a], k, th[a]);
+                        B_out[a] = B[a];
+                        ord_out[a] = (signed char)ord[a];
+                        th_out[a] = th[a];
+                        nt_out[a] = nt[a];
+                    }
                     return (nzero == 0 && top == 2) ? 0 : 1;
                 }
             }
@@ -328,8 +418,32 @@ static int ghost_geometry(const OLevel *L, long g, signed char *m_out, double *w
         w_out[3 * a + 1] = 0.0;
         w_out[3 * a + 2] = 0.0;
         B_out[a] = L->lo + ii[a] * L->h;
+        ord_out[a] = 0;
+        th_out[a] = 1.0;
+        nt_out[a] = nt[a];
     }
+    for (int kk = 0; kk < nk; kk++) wk_out[kk] = 0.0;
+    wk_out[0] = bc == 0 ? 1.0 : 1.0 / L->h;
     return 2;
+}
+
+/* (re)build the boundary rows of every ghost of a level for the boundary
+   condition bc; the finest level refuses identity rows */
+static int build_ghost_rows(Oracle *O, OLevel *L, int finest, int bc)
+{
+    int D = L->dim, nk = ipow3(D);
+    for (int gi = 0; gi < L->ng; gi++) {
+        long g = L->gidx[gi];
+        int kind = ghost_geometry(L, g, bc, L->gm + (size_t)D * gi, L->gw + (size_t)3 * D * gi,
+                                  L->gB + (size_t)D * gi, L->gord + (size_t)D * gi, L->gth + (size_t)D * gi,
+                                  L->gnt + (size_t)D * gi, L->gwk + (size_t)nk * gi);
+        L->gkind[gi] = (signed char)kind;
+        if (kind == 2 && finest) {
+            snprintf(O->err, sizeof O->err, "ghost %ld has no valid boundary stencil", g);
+            return OR_EGEOM;
+        }
+    }
+    return OR_OK;
 }
 
 static int build_level_geometry(Oracle *O, OLevel *L, int finest)
@@ -370,7 +484,12 @@ static int build_level_geometry(Oracle *O, OLevel *L, int finest)
     L->gm = (signed char *)malloc((size_t)L->dim * (ng + 1));
     L->gw = (double *)malloc(sizeof(double) * 3 * L->dim * (ng + 1));
     L->gB = (double *)malloc(sizeof(double) * L->dim * (ng + 1));
-    if (!L->gidx || !L->gkind || !L->gm || !L->gw || !L->gB) return OR_ENOMEM;
+    L->gord = (signed char *)malloc((size_t)L->dim * (ng + 1));
+    L->gth = (double *)malloc(sizeof(double) * L->dim * (ng + 1));
+    L->gnt = (double *)malloc(sizeof(double) * L->dim * (ng + 1));
+    L->gwk = (double *)malloc(sizeof(double) * ipow3(L->dim) * (ng + 1));
+    if (!L->gidx || !L->gkind || !L->gm || !L->gw || !L->gB || !L->gord || !L->gth || !L->gnt || !L->gwk)
+        return OR_ENOMEM;
     int k = 0;
     for (long i = 0; i < nn; i++)
         if (L->type[i] == T_GHOST) L->gidx[k++] = i;
@@ -378,16 +497,8 @@ static int build_level_geometry(Oracle *O, OLevel *L, int finest)
     if (!L->gpos) return OR_ENOMEM;
     for (long i = 0; i < nn; i++) L->gpos[i] = -1;
     for (int gi = 0; gi < ng; gi++) L->gpos[L->gidx[gi]] = gi;
-    for (int gi = 0; gi < ng; gi++) {
-        long g = L->gidx[gi];
-        int kind = ghost_geometry(L, g, L->gm + (size_t)L->dim * gi, L->gw + (size_t)3 * L->dim * gi,
-                                  L->gB + (size_t)L->dim * gi);
-        L->gkind[gi] = (signed char)kind;
-        if (kind == 2 && finest) {
-            snprintf(O->err, sizeof O->err, "ghost %ld has no valid boundary stencil", g);
-            return OR_EGEOM;
-        }
-    }
+    int rc = build_ghost_rows(O, L, finest, O->bc);
+    if (rc) return rc;
     /* band for the ghost-defect extension (R10) */
     signed char *layer = (signed char *)calloc(nn, 1);
     if (!layer) return OR_ENOMEM;
@@ -505,15 +616,10 @@ static void jrow_c(const Oracle *O, const OLevel *L, long p, double *cs, double 
 static double ghost_w(const OLevel *L, int gi, int kk, long *node)
 {
     int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
-    long g = L->gidx[gi];
-    double w = 1.0;
-    long nd = g;
-    for (int a = 0; a < L->dim; a++) {
-        w *= L->gw[(size_t)3 * L->dim * gi + 3 * a + k[a]];
-        nd -= (long)L->gm[(size_t)L->dim * gi + a] * k[a] * L->st[a];
-    }
+    long nd = L->gidx[gi];
+    for (int a = 0; a < L->dim; a++) nd -= (long)L->gm[(size_t)L->dim * gi + a] * k[a] * L->st[a];
     *node = nd;
-    return w;
+    return L->gwk[(size_t)ipow3(L->dim) * gi + kk];
 }
 
 static double ghost_row_dot(const OLevel *L, int gi, const double *v)
@@ -632,10 +738,13 @@ static void relax_ghosts(const Oracle *O, OLevel *L)
     double *x = L->x;
     const double *rhs = L->rhs;
     double *ns = (double *)malloc(sizeof(double) * (L->ng + 1));
+    /* Neumann rows have a diagonal of order 1/h: tau_s scales the bound of
+       Eq. CFLcondN, 2 sqrt(2) h / 3 in 2-D, i.e. 4 h / (3 sqrt(d)) */
+    const double tau = O->bc ? O->tau_s * 4.0 * L->h / (3.0 * sqrt((double)L->dim)) : O->tau_s;
     for (int rep = 0; rep < O->ghost_sweeps; rep++) {
         for (int gi = 0; gi < L->ng; gi++) {
             long g = L->gidx[gi];
-            ns[gi] = x[2 * g] + O->tau_s * (rhs[2 * g] - ghost_row_dot(L, gi, x));
+            ns[gi] = x[2 * g] + tau * (rhs[2 * g] - ghost_row_dot(L, gi, x));
         }
         for (int gi = 0; gi < L->ng; gi++) {
             long g = L->gidx[gi];
@@ -1080,6 +1189,7 @@ static int cn_step(Oracle *O)
 static void free_level(OLevel *L)
 {
     free(L->phi); free(L->type); free(L->gidx); free(L->gpos); free(L->gkind); free(L->gm); free(L->gw); free(L->gB);
+    free(L->gord); free(L->gth); free(L->gnt); free(L->gwk);
     free(L->bidx); free(L->bup); free(L->ban); free(L->Wc); free(L->rhs); free(L->x); free(L->res);
     free(L->act); free(L->pos); free(L->A); free(L->piv);
     memset(L, 0, sizeof *L);
@@ -1349,6 +1459,18 @@ int oracle_level_ghosts(void *h, int l, long *idx, signed char *kind, signed cha
     return OR_OK;
 }
 
+/* per-ghost member weights (ng x 3^dim, member kk = k0 + 3 k1 + 9 k2 at node
+   g - sum_a m_a k_a e_a) and the unit normal of phi~ at B (ng x dim) */
+int oracle_level_rows(void *h, int l, double *wk, double *nt)
+{
+    Oracle *O = (Oracle *)h;
+    if (l < 0 || l >= O->L) return OR_EINVAL;
+    OLevel *L = &O->lev[l];
+    memcpy(wk, L->gwk, sizeof(double) * ipow3(L->dim) * L->ng);
+    memcpy(nt, L->gnt, sizeof(double) * L->dim * L->ng);
+    return OR_OK;
+}
+
 int oracle_level_band(void *h, int l, long *idx, long *up, double *an)
 {
     Oracle *O = (Oracle *)h;
@@ -1377,6 +1499,21 @@ int oracle_set_ghost_sb(void *h, const double *sb)
 
 /* source terms of the manufactured-solution tests (Sec. 4.1) at t_n and t_{n+1},
    node values of the finest level; NULL clears them */
+/* boundary condition for s: 0 Dirichlet (Eq. BCs), 1 Neumann (Eq. BCsN, Sec.
+   3.6) with s_b the prescribed normal derivative; rebuilds the ghost rows of
+   every level */
+int oracle_set_bc(void *h, int bc)
+{
+    Oracle *O = (Oracle *)h;
+    if (bc != 0 && bc != 1) return OR_EINVAL;
+    O->bc = bc;
+    for (int l = 0; l < O->L; l++) {
+        int rc = build_ghost_rows(O, &O->lev[l], l == 0, bc);
+        if (rc) return rc;
+    }
+    return OR_OK;
+}
+
 int oracle_set_sources(void *h, const double *f1o, const double *f1n, const double *f2o, const double *f2n)
 {
     Oracle *O = (Oracle *)h;

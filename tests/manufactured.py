@@ -40,6 +40,47 @@ def sources(params, X, Y, t):
     return f1, f2
 
 
+def exact_grad_s(params, X, Y, t):
+    """Gradient of the exact s."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    st = np.sin(t + R2)
+    return np.cos(X) * np.cos(Y) * st, -np.sin(X) * np.sin(Y) * st
+
+
+def test_levelset(test, X, Y):
+    """The level sets of Tests 1 and 2 (Sec. 4.1) as functions of the point."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    if test.startswith("test1"):
+        return np.sqrt((X - np.sqrt(2.0) / 30.0) ** 2 + (Y - np.sqrt(3.0) / 40.0) ** 2) - 1.486
+    Lh, D = 0.9567, 0.3
+    p1 = np.maximum(np.abs(X), np.abs(Y)) - Lh
+    p2 = np.sqrt((np.abs(X) - Lh) ** 2 + (np.abs(Y) - Lh) ** 2) - D
+    return np.minimum(p1, p2)
+
+
+def boundary_normal(test, B):
+    """Outward unit normal of the exact boundary at the points B (n x 2), from
+    central differences of the level set function (step 1e-7)."""
+    e = 1e-7
+    gx = (test_levelset(test, B[:, 0] + e, B[:, 1]) - test_levelset(test, B[:, 0] - e, B[:, 1])) / (2 * e)
+    gy = (test_levelset(test, B[:, 0], B[:, 1] + e) - test_levelset(test, B[:, 0], B[:, 1] - e)) / (2 * e)
+    nrm = np.sqrt(gx * gx + gy * gy)
+    return np.stack([gx / nrm, gy / nrm], 1)
+
+
+def boundary_values(params, B, t, bc, normals=None):
+    """s_b at the boundary points: s itself (Dirichlet), or (Neumann) the
+    exact gradient of s along the given unit normals -- the discrete normals
+    n~ of phi~ at B, as the scheme imposes them (Eq. BCsN): Test 2's boundary
+    has corners where the exact normal jumps and no smooth normal exists."""
+    if bc == 0:
+        return exact(params, B[:, 0], B[:, 1], t)[0]
+    sx, sy = exact_grad_s(params, B[:, 0], B[:, 1], t)
+    return sx * normals[:, 0] + sy * normals[:, 1]
+
+
 def symbolic(params):
     """The same exact solution and sources derived symbolically (sympy):
     (s, c, f1, f2) as numpy callables of (x, y, t)."""
@@ -57,9 +98,11 @@ def symbolic(params):
     return mk(s), mk(c), mk(f1), mk(f2)
 
 
-def run_oracle(oracle_mod, phi, N, lo, hi, params, T=1.0, dt_factor=1.0):
+def run_oracle(oracle_mod, phi, N, lo, hi, params, T=1.0, dt_factor=1.0, bc=0):
     """Advance the oracle from the exact data at t = 0 to t = T with dt = h (the
-    paper's choice, Sec. 4) and return (s, c, type, X, Y)."""
+    paper's choice, Sec. 4) and return (s, c, type, X, Y, T).  bc = 1 imposes
+    the Neumann condition ds/dn = s_b of Sec. 3.6 with the exact normal
+    derivative along the discrete normal as s_b."""
     import workloads
 
     X, Y = workloads.node_coords(2, lo, hi, N)
@@ -70,16 +113,18 @@ def run_oracle(oracle_mod, phi, N, lo, hi, params, T=1.0, dt_factor=1.0):
     full = tuple(params) + (1.0, 0.0, 0.0)
     o.set_model(full)
     o.set_solver(newton_tol=1e-11)
+    if bc:
+        o.set_bc(bc)
     s0, c0 = exact(params, X, Y, 0.0)
     o.set_state(s0, c0, 0.0)
     g = o.level_ghosts(0)
+    _, nt = o.level_rows(0)
     for k in range(nsteps):
         t0, t1 = k * dt, (k + 1) * dt
         f1o, f2o = sources(params, X, Y, t0)
         f1n, f2n = sources(params, X, Y, t1)
         o.set_sources(f1o, f1n, f2o, f2n)
-        sb, _ = exact(params, g["B"][:, 0], g["B"][:, 1], t1)
-        o.set_ghost_sb(sb)
+        o.set_ghost_sb(boundary_values(params, g["B"], t1, bc, nt))
         o.step(dt, 1)
     s, c, ty = o.get_state()
     return s, c, ty, X, Y, nsteps * dt
