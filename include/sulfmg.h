@@ -142,6 +142,17 @@ int sulf_set_state(sulf_handle h, const double* s, const double* c, double t);
 /* Same, from device arrays. */
 int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_dev, double t);
 
+/* Boundary condition for s (Sec. 3.6): 0 Dirichlet s = s_b at the boundary
+   points (Eq. BCs, the default); 1 Neumann ds/dn = s_b there (Eq. BCsN), the
+   normal being that of the interpolated level set at B (Eq. Neumanntilde).
+   s_b is the model's s_ext, or the per-ghost values of
+   sulf_set_ghost_values.  With Neumann rows the ghost relaxation parameter is
+   tau_s * 2 sqrt(2) h / 3 in 2-D (Eq. CFLcondN; 4 h / (3 sqrt 3) in 3-D) on a
+   level of spacing h.  Rebuilds the boundary rows of every level;
+   SULF_EGEOM (and the previous rows kept) if a finest-level ghost has no
+   usable row for the new condition. */
+int sulf_set_bc(sulf_handle h, int type);
+
 /* Source terms of the manufactured-solution accuracy tests (Sec. 4.1): f1 and
    f2 are added to the right-hand sides of Eq. maineq and averaged over the CN
    step, i.e. F^s_p -= (f1_old[p] + f1_new[p]) / 2 on inside nodes and
@@ -180,8 +191,10 @@ int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
                     not read)
      F_dev          output, same layout; written on active nodes only
      fnorm_dev      output, one double: |F|_inf over the active nodes
-   It evaluates the model's equations with the constant s_ext: the optional
-   inputs of sulf_set_sources and sulf_set_ghost_values are not applied.
+   It evaluates the model's equations with the constant s_ext and Dirichlet
+   boundary rows: the optional inputs of sulf_set_sources and
+   sulf_set_ghost_values are not applied, and after sulf_set_bc(h, 1) the call
+   returns SULF_EINVAL.
    Work is queued on the handle's stream and the call returns without waiting.
    Scratch: a static array inside the library holding 65536 partial maxima
    (512 KiB), kept by every GPU that loads the library until the process exits;

@@ -33,6 +33,13 @@ int sulf_dbg_level_type(sulf_handle h, int level, int8_t* type);
 int sulf_dbg_level_ghosts(sulf_handle h, int level, int64_t* idx, int8_t* kind, int8_t* m, double* w,
                           double* B);
 
+/* the boundary rows of a level as member weights, ghost-major: wk holds
+   3^dim weights per ghost (member kk = k0 + 3 k1 + 9 k2 at node
+   g - sum_a m_a k_a e_a; Eq. JssD for Dirichlet, Eq. JccN for Neumann), nt the
+   unit normal of the interpolated level set at B (dim per ghost, Eq.
+   Neumanntilde) */
+int sulf_dbg_level_rows(sulf_handle h, int level, double* wk, double* nt);
+
 /* Newton residual F(W; W^n) of Eqs. FDs, FDc, BCs on the finest level */
 int sulf_dbg_eval_F(sulf_handle h, double dt, const double* W, const double* Wn, double* F);
 

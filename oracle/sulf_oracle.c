@@ -58,6 +58,13 @@
  *   R13 Newton stops on min{||F||, ||dW||/||W||} < tol; if ||F(W^n)|| < tol
  *       already, the step takes no Newton iteration.  Linear solve: cycles until
  *       ||r|| <= rtol ||F|| or the cycle cap.
+ *   R16 Neumann rows (Sec. 3.6): n~ . grad s~ at B with n~ the unit gradient of
+ *       the quadratic phi~ at B (linear where the 3^d stencil leaves the box);
+ *       per axis the first-derivative weights of Eq. intcoeffsN times m_a / h,
+ *       the other axes' value weights (Eq. JccN dimension by dimension), with
+ *       the orders of R6 (checked on the members these weights reach); the
+ *       identity fallback is s_g / h; tau = tau_s * 4 h / (3 sqrt(d)), the
+ *       bound 2 sqrt(2) h / 3 of Eq. CFLcondN in 2-D.
  */
 #include <math.h>
 #include <stdio.h>

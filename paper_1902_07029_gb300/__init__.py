@@ -75,6 +75,8 @@ _SIGS = {
     "sulf_set_state": (ctypes.c_int, [P, _dp, _dp, ctypes.c_double]),
     "sulf_set_state_device": (ctypes.c_int, [P, P, P, ctypes.c_double]),
     "sulf_get_stats": (ctypes.c_int, [P, ctypes.POINTER(SulfStats)]),
+    "sulf_set_bc": (ctypes.c_int, [P, ctypes.c_int]),
+    "sulf_dbg_level_rows": (ctypes.c_int, [P, ctypes.c_int, _dp, _dp]),
     "sulf_set_sources": (ctypes.c_int, [P, _dp, _dp, _dp, _dp]),
     "sulf_set_ghost_values": (ctypes.c_int, [P, _dp]),
     "sulf_set_profiling": (ctypes.c_int, [P, ctypes.c_int]),
@@ -220,6 +222,21 @@ class Domain:
         pointers as ints); queued on the handle's stream, no allocation."""
         _chk(self.lib, self.lib.sulf_newton_residual_noalloc(self.h, dt, P(W_ptr), P(Wn_ptr), P(F_ptr),
                                                              P(fnorm_ptr)))
+
+    def set_bc(self, bc):
+        """0: Dirichlet s = s_b (Eq. BCs); 1: Neumann ds/dn = s_b (Eq. BCsN)."""
+        _chk(self.lib, self.lib.sulf_set_bc(self.h, int(bc)))
+
+    def level_rows(self, l):
+        """Member weights of every ghost row (ng x 3^dim) and the unit normal of
+        the interpolated level set at each boundary point (ng x dim)."""
+        ng = self.level_info(l)["ng"]
+        d = self.dim
+        K = 9 if d == 2 else 27
+        wk = np.zeros(max(ng, 1) * K)
+        nt = np.zeros(max(ng, 1) * d)
+        _chk(self.lib, self.lib.sulf_dbg_level_rows(self.h, l, _d(wk), _d(nt)))
+        return wk[:ng * K].reshape(ng, K), nt[:ng * d].reshape(ng, d)
 
     def set_sources(self, f1_old=None, f1_new=None, f2_old=None, f2_new=None):
         """Manufactured source terms at t_n and t_{n+1} (box arrays), or none."""

@@ -174,6 +174,69 @@ __device__ __forceinline__ double basis(int order, int k, double xi) {
     return 0.0;
 }
 
+// derivative of basis with respect to xi: the 1-D first-derivative weights of
+// Eq. intcoeffsN (times h) for the quadratic, (1, -1) linear, 0 constant
+__device__ __forceinline__ double dbasis(int order, int k, double xi) {
+    if (order == 0) return 0.0;
+    if (order == 2) {
+        if (k == 0) return xi + 0.5;
+        if (k == 1) return -2.0 * xi;
+        return xi - 0.5;
+    }
+    if (k == 0) return 1.0;
+    if (k == 1) return -1.0;
+    return 0.0;
+}
+
+// gradient of the tensor interpolant of phi of the given order on the upwind
+// stencil of ghost g at the local coordinates xi (Eq. Neumanntilde:
+// n~* = grad phi~); d/dX_a = (m_a / h) d/dxi_a
+template <int D>
+__device__ void grad_interp_phi(const double* phi, int order, long long g, const int* m, const double* xi, int n,
+                                double h, double* gr) {
+    long long st[3] = {1, n, (long long)n * n};
+    for (int a = 0; a < D; a++) gr[a] = 0.0;
+    const int K = D == 2 ? 9 : 27;
+    for (int kk = 0; kk < K; kk++) {
+        int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
+        bool skip = false;
+        long long node = g;
+        for (int a = 0; a < D; a++) {
+            if (order == 1 && k[a] == 2) skip = true;
+            node -= (long long)m[a] * k[a] * st[a];
+        }
+        if (skip) continue;
+        for (int a = 0; a < D; a++) {
+            double t = (m[a] / h) * dbasis(order, k[a], xi[a]);
+            for (int b = 0; b < D; b++)
+                if (b != a) t *= basis(order, k[b], xi[b]);
+            gr[a] += t * phi[node];
+        }
+    }
+}
+
+// weight of stencil member kk of a ghost row: Dirichlet (Eq. JssD) the tensor
+// product of the 1-D value weights; Neumann (Eq. JccN built dimension by
+// dimension) n~ . grad s~ at B = sum_a n~_a (m_a / h) dbasis_a prod_{b != a} basis_b
+template <int D>
+__device__ double member_weight(int bc, double h, const int* m, const int* ord, const double* th, const double* nt,
+                                int kk) {
+    int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
+    if (bc == 0) {
+        double w = 1.0;
+        for (int a = 0; a < D; a++) w *= basis(ord[a], k[a], th[a]);
+        return w;
+    }
+    double w = 0.0;
+    for (int a = 0; a < D; a++) {
+        double t = nt[a] * (m[a] / h) * dbasis(ord[a], k[a], th[a]);
+        for (int b = 0; b < D; b++)
+            if (b != a) t *= basis(ord[b], k[b], th[b]);
+        w += t;
+    }
+    return w;
+}
+
 // tensor-product interpolant of phi on the upwind stencil of ghost g, at X;
 // local coordinate xi_a = 1 - m_a (G_a - X_a) / h
 template <int D>
@@ -199,20 +262,17 @@ __device__ double interp_phi(const double* phi, int order, long long g, const in
     return acc;
 }
 
-// every stencil node with a nonzero tensor weight must be active
+// every stencil node with a nonzero member weight must be active
 template <int D>
-__device__ bool weighted_active(const int8_t* type, long long g, const int* m, const double* w, int n) {
+__device__ bool weighted_active(const int8_t* type, long long g, const int* m, int bc, double h, const int* ord,
+                                const double* th, const double* nt, int n) {
     long long st[3] = {1, n, (long long)n * n};
     const int K = D == 2 ? 9 : 27;
     for (int kk = 0; kk < K; kk++) {
         int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
-        double wt = 1.0;
         long long node = g;
-        for (int a = 0; a < D; a++) {
-            wt *= w[3 * a + k[a]];
-            node -= (long long)m[a] * k[a] * st[a];
-        }
-        if (wt != 0.0 && !is_active(type[node])) return false;
+        for (int a = 0; a < D; a++) node -= (long long)m[a] * k[a] * st[a];
+        if (member_weight<D>(bc, h, m, ord, th, nt, kk) != 0.0 && !is_active(type[node])) return false;
     }
     return true;
 }
@@ -225,8 +285,8 @@ __device__ bool weighted_active(const int8_t* type, long long g, const int* m, c
 // node it weights to be active, else the identity row
 template <int D>
 __global__ void k_ghost_geom(const double* __restrict__ phi, const int8_t* __restrict__ type, int n, double lo,
-                             double h, const int* __restrict__ gidx, int ng, int8_t* gkind, int8_t* gm, double* gw,
-                             double* gB) {
+                             double h, const int* __restrict__ gidx, int ng, int bc, int8_t* gkind, int8_t* gm,
+                             double* gw, double* gB, int8_t* gord, double* gth, double* gnt) {
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= ng) return;
     long long g = gidx[gi];
@@ -274,6 +334,8 @@ __global__ void k_ghost_geom(const double* __restrict__ phi, const int8_t* __res
         }
     }
     int kind = 2;
+    double nt[3] = {nv[0], nv[1], nv[2]}, thout[3] = {1.0, 1.0, 1.0};
+    int ordout[3] = {0, 0, 0};
     if (border) {
         int ax[3] = {0, 1, 2};
         for (int i = 0; i < D; i++)
@@ -285,15 +347,37 @@ __global__ void k_ghost_geom(const double* __restrict__ phi, const int8_t* __res
                 }
         double th[3] = {0, 0, 0};
         for (int a = 0; a < D; a++) th[a] = 1.0 - m[a] * ((lo + ii[a] * h) - B[a]) / h;
+        // unit normal of phi~ at B: quadratic interpolant where its stencil fits
+        // in the box, else the linear one, else the node normal
+        int q = 0;
+        for (int o = 2; o >= 1 && !q; o--) {
+            bool inbox = true;
+            for (int a = 0; a < D; a++) {
+                int ia = ii[a] - m[a] * o;
+                if (ia < 0 || ia > n - 1) inbox = false;
+            }
+            if (inbox) q = o;
+        }
+        if (q) {
+            double gt[3] = {0, 0, 0}, gn = 0.0;
+            grad_interp_phi<D>(phi, q, g, m, th, n, h, gt);
+            for (int a = 0; a < D; a++) gn += gt[a] * gt[a];
+            gn = sqrt(gn);
+            if (gn > 0.0)
+                for (int a = 0; a < D; a++) nt[a] = gt[a] / gn;
+        }
         for (int nzero = 0; nzero < D && kind == 2; nzero++)
             for (int top = border; top >= 1 && kind == 2; top--) {
                 int ord[3] = {top, top, top};
                 for (int z = 0; z < nzero; z++) ord[ax[z]] = 0;
-                for (int a = 0; a < D; a++)
-                    for (int k = 0; k < 3; k++) wout[3 * a + k] = basis(ord[a], k, th[a]);
-                if (weighted_active<D>(type, g, m, wout, n)) {
+                if (weighted_active<D>(type, g, m, bc, h, ord, th, nt, n)) {
                     kind = (nzero == 0 && top == 2) ? 0 : 1;
-                    for (int a = 0; a < D; a++) bout[a] = B[a];
+                    for (int a = 0; a < D; a++) {
+                        for (int k = 0; k < 3; k++) wout[3 * a + k] = basis(ord[a], k, th[a]);
+                        bout[a] = B[a];
+                        ordout[a] = ord[a];
+                        thout[a] = th[a];
+                    }
                 }
             }
     }
@@ -308,6 +392,9 @@ __global__ void k_ghost_geom(const double* __restrict__ phi, const int8_t* __res
     for (int a = 0; a < D; a++) {
         gm[(long long)gi * D + a] = (int8_t)m[a];
         gB[(long long)gi * D + a] = bout[a];
+        gord[(long long)gi * D + a] = (int8_t)ordout[a];
+        gth[(long long)gi * D + a] = thout[a];
+        gnt[(long long)gi * D + a] = nt[a];
         for (int k = 0; k < 3; k++) gw[(long long)gi * 3 * D + 3 * a + k] = wout[3 * a + k];
     }
 }
@@ -323,14 +410,22 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 template <int D>
 __global__ void k_ghost_members(int ng, const int* __restrict__ gidx, const int8_t* __restrict__ gm,
                                 const double* __restrict__ gw, const float* __restrict__ gw32,
-                                const int* __restrict__ gpos, long long st1, long long st2, double* wk, float* wk32,
-                                int* node, int* src) {
+                                const int* __restrict__ gpos, long long st1, long long st2, int bc, double h,
+                                const int8_t* __restrict__ gkind, const int8_t* __restrict__ gord,
+                                const double* __restrict__ gth, const double* __restrict__ gnt, double* wk,
+                                float* wk32, int* node, int* src) {
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= ng) return;
     const int K = D == 2 ? 9 : 27;
     const long long g = gidx[gi];
-    int m[3] = {1, 1, 1};
-    for (int a = 0; a < D; a++) m[a] = gm[(long long)gi * D + a];
+    int m[3] = {1, 1, 1}, ord[3] = {0, 0, 0};
+    double th[3] = {1, 1, 1}, nt[3] = {0, 0, 0};
+    for (int a = 0; a < D; a++) {
+        m[a] = gm[(long long)gi * D + a];
+        ord[a] = gord[(long long)gi * D + a];
+        th[a] = gth[(long long)gi * D + a];
+        nt[a] = gnt[(long long)gi * D + a];
+    }
     for (int kk = 0; kk < K; kk++) {
         const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
         const double* w = gw + (long long)gi * 3 * D;
@@ -340,6 +435,11 @@ __global__ void k_ghost_members(int ng, const int* __restrict__ gidx, const int8
         if (D == 3) {
             wd = wd * w[6 + k2];
             wf = wf * w32[6 + k2];
+        }
+        if (bc == 1) {
+            // Neumann row (Eq. JccN); the identity fallback is s_g / h
+            wd = gkind[gi] == 2 ? (kk == 0 ? 1.0 / h : 0.0) : member_weight<D>(1, h, m, ord, th, nt, kk);
+            wf = (float)wd;
         }
         long long nd = g - m[0] * k0 - m[1] * k1 * st1;
         if (D == 3) nd -= m[2] * k2 * st2;
@@ -536,6 +636,43 @@ int compact(int which, const LevelGeo& L, int*& out, DevMem& mem, cudaStream_t s
 
 }  // namespace
 
+int build_ghost_rows(LevelGeo& L, int bc, bool finest, cudaStream_t s, std::string& err, long long& launches) {
+    if (L.ng == 0) return SULF_OK;
+    const int D = L.dim;
+    if (D == 2)
+        k_ghost_geom<2><<<nblk(L.ng, 128), 128, 0, s>>>(L.phi, L.type, L.n, L.lo, L.h, L.gidx, L.ng, bc, L.gkind,
+                                                        L.gm, L.gw, L.gB, L.gord, L.gth, L.gnt);
+    else
+        k_ghost_geom<3><<<nblk(L.ng, 128), 128, 0, s>>>(L.phi, L.type, L.n, L.lo, L.h, L.gidx, L.ng, bc, L.gkind,
+                                                        L.gm, L.gw, L.gB, L.gord, L.gth, L.gnt);
+    k_to_float<<<nblk(L.ng * 3LL * D), kThreads, 0, s>>>(L.gw, L.gw32, L.ng * 3LL * D);
+    if (D == 2)
+        k_ghost_members<2><<<nblk(L.ng, 128), 128, 0, s>>>(L.ng, L.gidx, L.gm, L.gw, L.gw32, L.gpos, L.st[1], L.st[2],
+                                                           bc, L.h, L.gkind, L.gord, L.gth, L.gnt, L.gwk, L.gwk32,
+                                                           L.gnode, L.gsrc);
+    else
+        k_ghost_members<3><<<nblk(L.ng, 128), 128, 0, s>>>(L.ng, L.gidx, L.gm, L.gw, L.gw32, L.gpos, L.st[1], L.st[2],
+                                                           bc, L.h, L.gkind, L.gord, L.gth, L.gnt, L.gwk, L.gwk32,
+                                                           L.gnode, L.gsrc);
+    launches += 3;
+    std::vector<int8_t> kinds(L.ng);
+    cudaMemcpyAsync(kinds.data(), L.gkind, L.ng, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        err = "ghost geometry failed";
+        return SULF_EDEVICE;
+    }
+    for (int k = 0; k < 3; k++) L.kinds[k] = 0;
+    for (int8_t k : kinds) L.kinds[(int)k]++;
+    if (finest && L.kinds[2] > 0) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "%d finest-level ghost(s) have no usable boundary stencil: refine the grid",
+                 L.kinds[2]);
+        err = buf;
+        return SULF_EGEOM;
+    }
+    return SULF_OK;
+}
+
 int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool coarsest, DevMem& mem,
                          cudaStream_t s, std::string& err, long long& launches) {
     const long long nn = L.nn;
@@ -599,42 +736,22 @@ int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool c
     L.gwk32 = (float*)mem.get(sizeof(float) * ng1 * K);
     L.gnode = (int*)mem.get(sizeof(int) * ng1 * K);
     L.gsrc = (int*)mem.get(sizeof(int) * ng1 * K);
-    if (!L.gpos || !L.gkind || !L.gm || !L.gw || !L.gw32 || !L.gB || !L.gwk || !L.gwk32 || !L.gnode || !L.gsrc) {
+    L.gord = (int8_t*)mem.get(ng1 * D);
+    L.gth = (double*)mem.get(sizeof(double) * ng1 * D);
+    L.gnt = (double*)mem.get(sizeof(double) * ng1 * D);
+    if (!L.gpos || !L.gkind || !L.gm || !L.gw || !L.gw32 || !L.gB || !L.gwk || !L.gwk32 || !L.gnode || !L.gsrc ||
+        !L.gord || !L.gth || !L.gnt) {
         err = "out of device memory";
         return SULF_ENOMEM;
     }
     cudaMemsetAsync(L.gpos, 0xff, sizeof(int) * nn, s);
     if (L.ng > 0) {
         k_scatter_pos<<<nblk(L.ng), kThreads, 0, s>>>(L.gidx, L.ng, L.gpos);
-        if (D == 2)
-            k_ghost_geom<2><<<nblk(L.ng, 128), 128, 0, s>>>(L.phi, L.type, L.n, L.lo, L.h, L.gidx, L.ng, L.gkind,
-                                                            L.gm, L.gw, L.gB);
-        else
-            k_ghost_geom<3><<<nblk(L.ng, 128), 128, 0, s>>>(L.phi, L.type, L.n, L.lo, L.h, L.gidx, L.ng, L.gkind,
-                                                            L.gm, L.gw, L.gB);
-        k_to_float<<<nblk(L.ng * 3LL * D), kThreads, 0, s>>>(L.gw, L.gw32, L.ng * 3LL * D);
-        if (D == 2)
-            k_ghost_members<2><<<nblk(L.ng, 128), 128, 0, s>>>(L.ng, L.gidx, L.gm, L.gw, L.gw32, L.gpos, L.st[1],
-                                                               L.st[2], L.gwk, L.gwk32, L.gnode, L.gsrc);
-        else
-            k_ghost_members<3><<<nblk(L.ng, 128), 128, 0, s>>>(L.ng, L.gidx, L.gm, L.gw, L.gw32, L.gpos, L.st[1],
-                                                               L.st[2], L.gwk, L.gwk32, L.gnode, L.gsrc);
-        launches += 4;
-        std::vector<int8_t> kinds(L.ng);
-        cudaMemcpyAsync(kinds.data(), L.gkind, L.ng, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) {
-            err = "ghost geometry failed";
-            return SULF_EDEVICE;
-        }
-        for (int k = 0; k < 3; k++) L.kinds[k] = 0;
-        for (int8_t k : kinds) L.kinds[(int)k]++;
-        if (finest && L.kinds[2] > 0) {
-            char buf[128];
-            snprintf(buf, sizeof buf, "%d finest-level ghost(s) have no usable boundary stencil: refine the grid",
-                     L.kinds[2]);
-            err = buf;
-            return SULF_EGEOM;
-        }
+        launches++;
+    }
+    {
+        int rc = build_ghost_rows(L, 0, finest, s, err, launches);
+        if (rc) return rc;
     }
     // band: inactive nodes within Chebyshev distance 2 of a ghost
     int8_t* mark = (int8_t*)mem.get(nn);

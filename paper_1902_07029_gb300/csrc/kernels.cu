@@ -378,8 +378,7 @@ __global__ void __launch_bounds__(kT) k_inject(Lists ls, int cn, const int8_t* _
 template <int D, typename T, bool SMEM>
 __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* __restrict__ act,
                                                           const int* __restrict__ apos, const int8_t* __restrict__ type,
-                                                          const int* __restrict__ gpos, const int8_t* __restrict__ gm,
-                                                          const T* __restrict__ gw,
+                                                          const int* __restrict__ gpos, GhostTab<T> tb,
                                                           const typename V2<T>::t* __restrict__ Wc, Offs<D> of,
                                                           long long st1, long long st2, Coef<T> c, T* Ag, T* Ainv_g,
                                                           int* singular) {
@@ -419,21 +418,14 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
             rs[2 * r] += ss;
             rs[2 * r + 1] += sc;
         } else {
+            // the ghost's boundary row from its member table (Dirichlet or Neumann)
             int gi = gpos[p];
-            int mv[3] = {1, 1, 1};
-            for (int a = 0; a < D; a++) mv[a] = gm[(long long)gi * D + a];
-            long long st[3] = {1, st1, st2};
             const int K = D == 2 ? 9 : 27;
             for (int kk = 0; kk < K; kk++) {
-                int k[3] = {kk % 3, (kk / 3) % 3, kk / 9};
-                T wt = 1;
-                long long node = p;
-                for (int a = 0; a < D; a++) {
-                    wt *= gw[(long long)gi * 3 * D + 3 * a + k[a]];
-                    node -= mv[a] * k[a] * st[a];
-                }
+                const long long o = (long long)kk * tb.ng + gi;
+                T wt = tb.w[o];
                 if (wt == (T)0) continue;
-                rs[2 * apos[node]] += wt;
+                rs[2 * apos[tb.node[o]]] += wt;
             }
         }
         rc[2 * r] += c.a2ms * ph * cp;
@@ -835,7 +827,7 @@ int launch_inject(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, c
 template <int D, typename T>
 int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int* singular,
                            cudaStream_t s) {
-    const T* gw = std::is_same<T, float>::value ? (const T*)L.gw32 : (const T*)L.gw;
+    GhostTab<T> tb = stages::ghost_tab<T>(L);
     Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
     const size_t m = 2 * (size_t)L.nact;
     const size_t piv_bytes = sizeof(T) * (m + 1) + sizeof(int) * (m + 1);  // column k and the interchanges
@@ -857,10 +849,10 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
                 if (dev >= 0 && dev < 64) raised[dev] = true;
             }
         }
-        launch_k(kern, 1, 1024, smem_full, s, L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw, V.Wc, of, L.st[1], L.st[2],
+        launch_k(kern, 1, 1024, smem_full, s, L.nact, L.act, L.apos, L.type, L.gpos, tb, V.Wc, of, L.st[1], L.st[2],
                                         c, V.A, V.Ainv, singular);
     } else {
-        launch_k(k_coarsest_factor<D, T, false>, 1, 1024, piv_bytes, s, L.nact, L.act, L.apos, L.type, L.gpos, L.gm, gw,
+        launch_k(k_coarsest_factor<D, T, false>, 1, 1024, piv_bytes, s, L.nact, L.act, L.apos, L.type, L.gpos, tb,
                                                                   V.Wc, of, L.st[1], L.st[2], c, V.A, V.Ainv,
                                                                   singular);
     }

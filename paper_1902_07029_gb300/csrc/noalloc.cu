@@ -161,6 +161,8 @@ extern "C" int sulf_newton_residual_noalloc(sulf_handle h, double dt, const doub
     const sulf_model* m = handle_model(h);
     if (!G || !m || !W_dev || !Wn_dev || !F_dev || !fnorm_dev || !(dt > 0))
         return sulf_fail(SULF_EINVAL, "invalid arguments");
+    if (handle_bc(h) != 0)
+        return sulf_fail(SULF_EINVAL, "sulf_newton_residual_noalloc evaluates Dirichlet boundary rows only");
     long long nact = (long long)G->nin[0] + G->nin[1] + G->ng;
     long long nblocks = (nact + kThreads - 1) / kThreads;
     if (nblocks > kMaxBlocks)

@@ -53,7 +53,7 @@ extern "C" unsigned long long sulf_estimate_device_bytes(int dim, int N, int coa
     // index 4) per ghost, ghosts bounded by 8 % (2-D) / 15 % (3-D) of the box
     // nodes on every level (the coarse levels of thin 3-D shapes approach it)
     const double members = dim == 2 ? 9.0 : 27.0;
-    per_level += (dim == 2 ? 0.08 : 0.15) * members * 20.0;
+    per_level += (dim == 2 ? 0.08 : 0.15) * (members * 20.0 + 17.0 * dim);  // + orders, theta, normal
     // band extension operator: 16 B per entry, at most 1.5 (2-D) / 3.2 (3-D)
     // entries per box node on any level
     per_level += (dim == 2 ? 1.5 : 3.2) * 16.0;

@@ -77,6 +77,7 @@ struct sulf_domain {
     LevelVec<double> v64[SULF_MAXLEV];
     LevelVec<float> v32[SULF_MAXLEV];
     bool have32 = false;
+    int bc = 0;  // boundary condition for s: 0 Dirichlet (Eq. BCs), 1 Neumann (Eq. BCsN)
     double2* W = nullptr;   // state, = v64[0].Wc
     double2* Wn = nullptr;  // state at t_n
     double2* G = nullptr;   // old-time part of the CN step
@@ -175,7 +176,9 @@ Coef<T> make_coef(const sulf_domain* d, int l) {
     c.a2ms = (T)(m.a / (2.0 * m.m_s));
     c.idt = (T)(1.0 / d->dt);
     c.kap = (T)(m.d / (4.0 * h * h));
-    c.tau = (T)d->solver.tau_s;
+    // Neumann rows have a diagonal of order 1/h: tau_s scales the bound of
+    // Eq. CFLcondN, 2 sqrt(2) h / 3 in 2-D, i.e. 4 h / (3 sqrt(d))
+    c.tau = (T)(d->bc ? d->solver.tau_s * tail_tau_scale(d->dim, h) : d->solver.tau_s);
     return c;
 }
 
@@ -326,7 +329,7 @@ struct MG {
         int rc;
         if (l == tail_level(d) && d->tail_ready[p] && d->solver.cycle == 1) {
             // this level and all coarser ones in one single-CTA launch
-            rc = launch_tail<D, T>(d->tail_desc[p], l, d->L, d->solver, d->stream);
+            rc = launch_tail<D, T>(d->tail_desc[p], l, d->L, d->solver, d->bc, d->stream);
             if (rc) return rc;
             d->launches += 1;
             return SULF_OK;
@@ -568,6 +571,7 @@ int copy_in(sulf_domain* d, void* dst, const void* src, size_t n) {
 namespace sulf {
 const LevelGeo* handle_fine_geo(sulf_handle h) { return h ? &h->geo[0] : nullptr; }
 const sulf_model* handle_model(sulf_handle h) { return h ? &h->model : nullptr; }
+int handle_bc(sulf_handle h) { return h ? h->bc : 0; }
 cudaStream_t handle_stream(sulf_handle h) { return h ? h->stream : nullptr; }
 void handle_count_launches(sulf_handle h, int n) {
     if (h) h->launches += n;
@@ -766,6 +770,31 @@ int sulf_set_state(sulf_handle h, const double* s, const double* c, double t) {
     return sulf_set_state_device(h, h->stage, h->stage + nn, t);
 }
 
+int sulf_set_bc(sulf_handle h, int type) {
+    if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
+    if (type != 0 && type != 1) return sulf_fail(SULF_EINVAL, "boundary condition must be 0 (Dirichlet) or 1 (Neumann)");
+    if (type == h->bc) return SULF_OK;
+    std::string err;
+    for (int l = 0; l < h->L; l++) {
+        int rc = build_ghost_rows(h->geo[l], type, l == 0, h->stream, err, h->launches);
+        if (rc) {
+            // put the previous rows back
+            std::string ignore;
+            for (int k = 0; k <= l; k++) build_ghost_rows(h->geo[k], h->bc, k == 0, h->stream, ignore, h->launches);
+            return sulf_fail(rc, err);
+        }
+    }
+    h->bc = type;
+    // the captured cycles bake the relaxation parameter and the fused kernel's
+    // boundary condition: capture them again
+    for (auto& g : h->graph)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+    return SULF_OK;
+}
+
 int sulf_set_sources(sulf_handle h, const double* f1_old, const double* f1_new, const double* f2_old,
                      const double* f2_new) {
     if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
@@ -881,6 +910,22 @@ int sulf_dbg_level_ghosts(sulf_handle h, int l, int64_t* idx, int8_t* kind, int8
     SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
     if (idx)
         for (int k = 0; k < G.ng; k++) idx[k] = tmp[k];
+    return SULF_OK;
+}
+
+int sulf_dbg_level_rows(sulf_handle h, int l, double* wk, double* nt) {
+    if (!dbg_level_ok(h, l)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G = h->geo[l];
+    const int D = G.dim, K = D == 2 ? 9 : 27;
+    if (wk) {
+        std::vector<double> t((size_t)K * G.ng + 1);
+        SULF_CUDA_TRY(cudaMemcpyAsync(t.data(), G.gwk, sizeof(double) * K * G.ng, cudaMemcpyDeviceToHost, h->stream));
+        SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        for (int gi = 0; gi < G.ng; gi++)
+            for (int kk = 0; kk < K; kk++) wk[(size_t)gi * K + kk] = t[(size_t)kk * G.ng + gi];
+    }
+    if (nt) SULF_CUDA_TRY(cudaMemcpyAsync(nt, G.gnt, sizeof(double) * G.ng * D, cudaMemcpyDeviceToHost, h->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return SULF_OK;
 }
 

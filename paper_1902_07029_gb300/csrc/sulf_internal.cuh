@@ -57,6 +57,9 @@ struct LevelGeo {
     double* gw = nullptr;     // ng*dim*3 1-D weights at offsets 0,1,2
     float* gw32 = nullptr;
     double* gB = nullptr;     // ng*dim boundary points
+    int8_t* gord = nullptr;   // ng*dim per-axis interpolation orders of the row
+    double* gth = nullptr;    // ng*dim theta per axis at B
+    double* gnt = nullptr;    // ng*dim unit normal of the interpolated level set at B
     // each ghost's boundary row as a member table, member-major (kk * ng + gi)
     // over the K = 3^dim members of its upwind stencil: tensor weight (0 when
     // absent), box node, ghost index of the member or -1
@@ -139,6 +142,10 @@ struct DevMem {
 // ---- geometry (geometry.cu) ----
 int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool coarsest, DevMem& mem,
                          cudaStream_t s, std::string& err, long long& launches);
+// (re)build the boundary rows of a level's ghosts for boundary condition bc
+// (0 Dirichlet, Eq. BCs; 1 Neumann, Eq. BCsN): normals, orders, weights,
+// member tables; the finest level refuses identity rows (SULF_EGEOM)
+int build_ghost_rows(LevelGeo& L, int bc, bool finest, cudaStream_t s, std::string& err, long long& launches);
 
 // ---- multigrid and Newton kernels (kernels.cu); each returns kernels launched ----
 template <int D, typename T>
@@ -194,7 +201,13 @@ size_t tail_desc_bytes(int L);
 template <typename T>
 int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, cudaStream_t s);
 template <int D, typename T>
-int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, cudaStream_t s);
+int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int bc, cudaStream_t s);
+
+// factor of tau_s for Neumann ghost rows on a level of spacing h (Eq.
+// CFLcondN): 4 h / (3 sqrt(dim)), i.e. 2 sqrt(2) h / 3 in 2-D
+__host__ __device__ inline double tail_tau_scale(int dim, double h) {
+    return 4.0 * h / (3.0 * (dim == 3 ? 1.7320508075688772 : 1.4142135623730951));
+}
 
 // Programmatic dependent launch.  Every kernel of the Newton and multigrid
 // path starts with pdl_enter(): griddepcontrol.wait blocks until the previous
@@ -239,6 +252,7 @@ inline void launch_k(void (*k)(P...), unsigned grid, unsigned block, size_t smem
 // read-only views of a handle (solver.cu)
 const LevelGeo* handle_fine_geo(sulf_handle h);
 const sulf_model* handle_model(sulf_handle h);
+int handle_bc(sulf_handle h);
 cudaStream_t handle_stream(sulf_handle h);
 void handle_count_launches(sulf_handle h, int n);
 

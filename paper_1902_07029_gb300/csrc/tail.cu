@@ -25,6 +25,7 @@ struct TailLevel {
     typedef typename V2<T>::t T2;
     Lists ls;
     int n;
+    double h;
     long long st1, st2;
     const int8_t* type;
     stages::GhostTab<T> tab;
@@ -49,7 +50,7 @@ struct TailLevel {
 };
 
 struct TailParams {
-    int l0, L, nu1, nu2, passes, pointwise;
+    int l0, L, nu1, nu2, passes, pointwise, bc;
     double tau;
 };
 
@@ -81,13 +82,13 @@ __device__ void tail_relax(const TailLevel<T>& v, const TailParams& pr, int tid,
         }
         __syncthreads();
     }
+    const T tau = (T)(pr.bc ? pr.tau * tail_tau_scale(D, v.h) : pr.tau);
     for (int p = 0; p < pr.passes; p++) {
         bool first = p == 0, last = p == pr.passes - 1 && pr.passes > 1;
         const T* sin = first ? nullptr : v.gbuf[(p - 1) & 1];
         T* sout = v.gbuf[p & 1];
         for (int gi = tid; gi < v.ls.ng; gi += nthr)
-            stages::ghost_pass_node<D, T, false>(gi, v.ls.lg, v.tab, v.gc, v.rhs, v.x, sin, sout, (T)pr.tau, first,
-                                                last);
+            stages::ghost_pass_node<D, T, false>(gi, v.ls.lg, v.tab, v.gc, v.rhs, v.x, sin, sout, tau, first, last);
         __syncthreads();
     }
     if (pr.passes == 1) {
@@ -155,6 +156,7 @@ TailLevel<T> describe(const LevelGeo& G, const LevelVec<T>& V) {
     TailLevel<T> t;
     t.ls = stages::make_lists(G);
     t.n = G.n;
+    t.h = G.h;
     t.st1 = G.st[1];
     t.st2 = G.st[2];
     t.type = G.type;
@@ -197,7 +199,7 @@ int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, 
 
 namespace {
 
-TailParams make_params(int l0, int L, const sulf_solver& sv, int D) {
+TailParams make_params(int l0, int L, const sulf_solver& sv, int bc, int D) {
     TailParams pr;
     pr.l0 = l0;
     pr.L = L;
@@ -206,6 +208,7 @@ TailParams make_params(int l0, int L, const sulf_solver& sv, int D) {
     pr.passes = sv.ghost_sweeps;
     pr.pointwise = sv.smoother == 1;
     pr.tau = sv.tau_s;
+    pr.bc = bc;
     (void)D;
     return pr;
 }
@@ -213,8 +216,8 @@ TailParams make_params(int l0, int L, const sulf_solver& sv, int D) {
 }  // namespace
 
 template <int D, typename T>
-int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, cudaStream_t s) {
-    launch_k(k_tail<D, T>, 1, kTailThreads, 0, s, (const TailLevel<T>*)dev_desc, make_params(l0, L, sv, D));
+int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int bc, cudaStream_t s) {
+    launch_k(k_tail<D, T>, 1, kTailThreads, 0, s, (const TailLevel<T>*)dev_desc, make_params(l0, L, sv, bc, D));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sulf_fail_cuda(e, "fused coarse-level cycle launch");
     return SULF_OK;
@@ -222,9 +225,9 @@ int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, cuda
 
 template int upload_tail_desc<double>(const LevelGeo*, const LevelVec<double>*, int, void*, cudaStream_t);
 template int upload_tail_desc<float>(const LevelGeo*, const LevelVec<float>*, int, void*, cudaStream_t);
-template int launch_tail<2, double>(const void*, int, int, const sulf_solver&, cudaStream_t);
-template int launch_tail<2, float>(const void*, int, int, const sulf_solver&, cudaStream_t);
-template int launch_tail<3, double>(const void*, int, int, const sulf_solver&, cudaStream_t);
-template int launch_tail<3, float>(const void*, int, int, const sulf_solver&, cudaStream_t);
+template int launch_tail<2, double>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
+template int launch_tail<2, float>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
+template int launch_tail<3, double>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
+template int launch_tail<3, float>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
 
 }  // namespace sulf
