@@ -67,6 +67,8 @@ def _load():
         "oracle_set_ghost_sb": (ctypes.c_int, [P, dp]),
         "oracle_set_sources": (ctypes.c_int, [P, dp, dp, dp, dp]),
         "oracle_set_bc": (ctypes.c_int, [P, ctypes.c_int]),
+        "oracle_reinit": (ctypes.c_int, [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]),
+        "oracle_mask_levelset": (ctypes.c_int, [bp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]),
         "oracle_level_rows": (ctypes.c_int, [P, ctypes.c_int, dp, dp]),
         "oracle_eval_F": (ctypes.c_int, [P, ctypes.c_double, dp, dp, dp]),
         "oracle_apply_J": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, dp, dp, dp]),
@@ -329,3 +331,25 @@ def interleave(s, c):
     W[0::2] = np.ravel(s)
     W[1::2] = np.ravel(c)
     return W
+
+
+def reinit(phi, dim, N, h, steps):
+    """Reinitialization toward the signed distance (Sec. 2), oracle version."""
+    lib = _load()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    out = np.zeros_like(phi)
+    rc = lib.oracle_reinit(_d(phi), dim, N, h, steps, _d(out))
+    if rc:
+        raise RuntimeError(f"oracle_reinit error {rc}")
+    return out
+
+
+def mask_levelset(mask, dim, N, steps):
+    """Provisional level set of a binary mask (Sec. 2), oracle version."""
+    lib = _load()
+    m = np.ascontiguousarray(mask, dtype=np.int8)
+    out = np.zeros(m.shape, dtype=np.float64)
+    rc = lib.oracle_mask_levelset(m.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)), dim, N, steps, _d(out))
+    if rc:
+        raise RuntimeError(f"oracle_mask_levelset error {rc}")
+    return out

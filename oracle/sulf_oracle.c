@@ -1695,3 +1695,104 @@ int oracle_coarsest_solve(void *h, double dt, const double *Wc0, const double *r
     memcpy(x_c, C->x, sizeof(double) * 2 * C->nn);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* level-set preprocessing (Sec. 2)                                     */
+/* ------------------------------------------------------------------ */
+
+/* one-sided differences of v at box node i along axis a; a missing neighbour
+   (box edge) gives a zero difference on that side */
+static void one_sided(const double *v, long i, const int *ii, int a, int N, const long *st, double h, double *dm,
+                      double *dp)
+{
+    *dm = ii[a] > 0 ? (v[i] - v[i - st[a]]) / h : 0.0;
+    *dp = ii[a] < N ? (v[i + st[a]] - v[i]) / h : 0.0;
+}
+
+/* Reinitialization (Sec. 2): the PDE d phi_d / d mu = sgn(phi)(1 - |grad phi_d|)
+   with phi_d = phi at mu = 0, marched `steps` explicit Euler steps of
+   d mu = h / dim.  sgn is the smoothed sign phi / sqrt(phi^2 + h^2) of the
+   initial phi; |grad phi_d| is Godunov's upwind approximation from the
+   one-sided differences (first order), chosen by the sign of phi: where
+   phi > 0, sqrt(sum_a max(max(D-_a,0)^2, min(D+_a,0)^2)); where phi < 0,
+   sqrt(sum_a max(min(D-_a,0)^2, max(D+_a,0)^2)).  phi_out may alias nothing. */
+int oracle_reinit(const double *phi0, int dim, int N, double h, int steps, double *phi_out)
+{
+    if ((dim != 2 && dim != 3) || N < 2 || !(h > 0) || steps < 0) return OR_EINVAL;
+    long n = N + 1, nn = dim == 2 ? n * n : n * n * n;
+    long st[3] = {1, n, n * n};
+    double *a = (double *)malloc(sizeof(double) * nn), *b = (double *)malloc(sizeof(double) * nn);
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return OR_ENOMEM;
+    }
+    memcpy(a, phi0, sizeof(double) * nn);
+    const double dmu = h / dim;
+    for (int k = 0; k < steps; k++) {
+        for (long i = 0; i < nn; i++) {
+            int ii[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / (n * n))};
+            double p0 = phi0[i];
+            double sg = p0 / sqrt(p0 * p0 + h * h);
+            double g2 = 0.0;
+            for (int ax = 0; ax < dim; ax++) {
+                double dm, dp;
+                one_sided(a, i, ii, ax, N, st, h, &dm, &dp);
+                double l, r;
+                if (p0 > 0.0) {
+                    l = dm > 0.0 ? dm : 0.0;
+                    r = dp < 0.0 ? dp : 0.0;
+                } else {
+                    l = dm < 0.0 ? dm : 0.0;
+                    r = dp > 0.0 ? dp : 0.0;
+                }
+                g2 += l * l > r * r ? l * l : r * r;
+            }
+            b[i] = p0 == 0.0 ? a[i] : a[i] - dmu * sg * (sqrt(g2) - 1.0);
+        }
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    memcpy(phi_out, a, sizeof(double) * nn);
+    free(a);
+    free(b);
+    return OR_OK;
+}
+
+/* A provisional level set from a binary mask (Sec. 2): phi = -1 inside
+   (mask != 0), +1 outside, then `steps` explicit steps of the heat equation
+   phi += lambda sum_q (phi_q - phi) over the axis neighbours present in the
+   box, lambda = 1 / (4 dim) (half the stability limit). */
+int oracle_mask_levelset(const unsigned char *mask, int dim, int N, int steps, double *phi_out)
+{
+    if ((dim != 2 && dim != 3) || N < 2 || steps < 0) return OR_EINVAL;
+    long n = N + 1, nn = dim == 2 ? n * n : n * n * n;
+    long st[3] = {1, n, n * n};
+    double *a = (double *)malloc(sizeof(double) * nn), *b = (double *)malloc(sizeof(double) * nn);
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return OR_ENOMEM;
+    }
+    for (long i = 0; i < nn; i++) a[i] = mask[i] ? -1.0 : 1.0;
+    const double lam = 1.0 / (4.0 * dim);
+    for (int k = 0; k < steps; k++) {
+        for (long i = 0; i < nn; i++) {
+            int ii[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / (n * n))};
+            double acc = 0.0;
+            for (int ax = 0; ax < dim; ax++) {
+                if (ii[ax] > 0) acc += a[i - st[ax]] - a[i];
+                if (ii[ax] < N) acc += a[i + st[ax]] - a[i];
+            }
+            b[i] = a[i] + lam * acc;
+        }
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    memcpy(phi_out, a, sizeof(double) * nn);
+    free(a);
+    free(b);
+    return OR_OK;
+}
