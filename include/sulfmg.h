@@ -142,6 +142,24 @@ int sulf_set_state(sulf_handle h, const double* s, const double* c, double t);
 /* Same, from device arrays. */
 int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_dev, double t);
 
+/* Level-set preprocessing (Sec. 2), run before sulf_create_domain; both take
+   and return host arrays of (N+1)^dim values (x fastest) and use device
+   memory only for the duration of the call.
+
+   Reinitialization toward the signed distance: `steps` explicit Euler steps
+   of d phi_d / d mu = sgn(phi)(1 - |grad phi_d|), phi_d = phi at mu = 0, with
+   d mu = h / dim, the smoothed sign phi / sqrt(phi^2 + h^2) and Godunov's
+   first-order upwind |grad phi_d| (a missing box-edge side counts as a zero
+   difference).  Information travels about h / dim per step, so 2 N steps
+   reach the whole box. */
+int sulf_reinit_levelset(const double* phi_in, int dim, int N, double h, int steps, double* phi_out);
+
+/* Provisional level set of a binary mask (a scanned shape, Sec. 2): -1 where
+   mask != 0 (inside), +1 elsewhere, then `steps` explicit heat steps
+   phi += (1 / (4 dim)) sum_q (phi_q - phi) over the axis neighbours in the
+   box.  Follow with sulf_reinit_levelset for a distance-like level set. */
+int sulf_levelset_from_mask(const uint8_t* mask, int dim, int N, int steps, double* phi_out);
+
 /* Boundary condition for s (Sec. 3.6): 0 Dirichlet s = s_b at the boundary
    points (Eq. BCs, the default); 1 Neumann ds/dn = s_b there (Eq. BCsN), the
    normal being that of the interpolated level set at B (Eq. Neumanntilde).

@@ -75,6 +75,9 @@ _SIGS = {
     "sulf_set_state": (ctypes.c_int, [P, _dp, _dp, ctypes.c_double]),
     "sulf_set_state_device": (ctypes.c_int, [P, P, P, ctypes.c_double]),
     "sulf_get_stats": (ctypes.c_int, [P, ctypes.POINTER(SulfStats)]),
+    "sulf_reinit_levelset": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]),
+    "sulf_levelset_from_mask": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, _dp]),
     "sulf_set_bc": (ctypes.c_int, [P, ctypes.c_int]),
     "sulf_dbg_level_rows": (ctypes.c_int, [P, ctypes.c_int, _dp, _dp]),
     "sulf_set_sources": (ctypes.c_int, [P, _dp, _dp, _dp, _dp]),
@@ -147,6 +150,29 @@ def default_solver(**kw) -> SulfSolver:
     for k, v in kw.items():
         setattr(s, k, v)
     return s
+
+
+def reinit_levelset(phi, dim, N, h, steps):
+    """Reinitialization toward the signed distance (Sec. 2), on the GPU."""
+    lib = load()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    if phi.size != (N + 1) ** dim:
+        raise ValueError("phi must hold (N+1)^dim values")
+    out = np.zeros_like(phi)
+    _chk(lib, lib.sulf_reinit_levelset(_d(phi), dim, N, float(h), int(steps), _d(out)))
+    return out
+
+
+def levelset_from_mask(mask, dim, N, steps):
+    """Provisional level set of a binary mask (Sec. 2), on the GPU."""
+    lib = load()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    if m.size != (N + 1) ** dim:
+        raise ValueError("mask must hold (N+1)^dim values")
+    out = np.zeros(m.shape, dtype=np.float64)
+    _chk(lib, lib.sulf_levelset_from_mask(m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), dim, N, int(steps),
+                                          _d(out)))
+    return out
 
 
 class Domain:

@@ -46,6 +46,11 @@ def test_argument_errors_without_gpu(sulfmg):
     rc = lib.sulf_create_domain(None, 2, box.ctypes.data_as(dp), 16, 8, ctypes.byref(h))
     assert rc == sulfmg.EINVAL
     assert lib.sulf_step(None, 0.1, 1) == sulfmg.EINVAL
+    out = np.zeros(17 * 17)
+    assert lib.sulf_reinit_levelset(None, 2, 16, 0.1, 4, out.ctypes.data_as(dp)) == sulfmg.EINVAL
+    assert lib.sulf_reinit_levelset(phi.ctypes.data_as(dp), 4, 16, 0.1, 4, out.ctypes.data_as(dp)) == sulfmg.EINVAL
+    assert lib.sulf_levelset_from_mask(None, 2, 16, 4, out.ctypes.data_as(dp)) == sulfmg.EINVAL
+    assert lib.sulf_set_bc(None, 1) == sulfmg.EINVAL
     assert lib.sulf_set_solver(None, None) == sulfmg.EINVAL
     lib.sulf_destroy(None)
 
