@@ -69,6 +69,7 @@ def _load():
         "oracle_set_bc": (ctypes.c_int, [P, ctypes.c_int]),
         "oracle_reinit": (ctypes.c_int, [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]),
         "oracle_mask_levelset": (ctypes.c_int, [bp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]),
+        "oracle_extrapolate": (ctypes.c_int, [dp, bp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]),
         "oracle_level_rows": (ctypes.c_int, [P, ctypes.c_int, dp, dp]),
         "oracle_eval_F": (ctypes.c_int, [P, ctypes.c_double, dp, dp, dp]),
         "oracle_apply_J": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, dp, dp, dp]),
@@ -352,4 +353,17 @@ def mask_levelset(mask, dim, N, steps):
     rc = lib.oracle_mask_levelset(m.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)), dim, N, steps, _d(out))
     if rc:
         raise RuntimeError(f"oracle_mask_levelset error {rc}")
+    return out
+
+
+def extrapolate(phi, types, u, dim, N, h, iters):
+    """Linear extrapolation of u from the inside nodes to the rest of the box
+    (the PDE approach used for the initial data, Sec. 3.3), oracle version."""
+    lib = _load()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    t = np.ascontiguousarray(types, dtype=np.int8)
+    out = np.ascontiguousarray(u, dtype=np.float64).copy()
+    rc = lib.oracle_extrapolate(_d(phi), t.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)), dim, N, h, iters, _d(out))
+    if rc:
+        raise RuntimeError(f"oracle_extrapolate error {rc}")
     return out

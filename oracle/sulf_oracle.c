@@ -1796,3 +1796,101 @@ int oracle_mask_levelset(const unsigned char *mask, int dim, int N, int steps, d
     free(b);
     return OR_OK;
 }
+
+/* Extrapolation of initial data to the ghosts (Sec. 3.3: the ICs of s and c
+   are extrapolated outside the domain with second order, by the PDE approach
+   of the cited extrapolation technique).  For a field u known at the inside
+   nodes (phi < 0) of the finest level:
+     1. u_n = n . grad u by central differences where all axis neighbours are
+        inside, n = grad phi / |grad phi| (Eq. ncurv, central differences);
+     2. u_n extended to the other nodes by `iters` Jacobi steps of
+        d q / d tau + n . grad q = 0, i.e. q <- q - (dtau / h) sum_a |n_a|
+        (q - q_up(a)), with q_up(a) the neighbour toward the inside along axis
+        a (index i - sign(n_a)), dtau = h / 2;
+     3. u extended linearly to the non-inside nodes by `iters` Jacobi steps of
+        d u / d tau + n . grad u = u_n, i.e. u <- u - dtau ((1/h) sum_a |n_a|
+        (u - u_up(a)) - u_n).
+   Known values never change; unknown ones start at 0.  u is overwritten at
+   the non-inside nodes (all of the box: callers read the ghosts). */
+int oracle_extrapolate(const double *phi, const signed char *type, int dim, int N, double h, int iters, double *u)
+{
+    if ((dim != 2 && dim != 3) || N < 2 || !(h > 0) || iters < 0) return OR_EINVAL;
+    long n = N + 1, nn = dim == 2 ? n * n : n * n * n;
+    long st[3] = {1, n, n * n};
+    double *nv = (double *)calloc((size_t)dim * nn, sizeof(double));
+    double *q = (double *)calloc(nn, sizeof(double)), *q2 = (double *)calloc(nn, sizeof(double));
+    double *v2 = (double *)malloc(sizeof(double) * nn);
+    signed char *kn = (signed char *)calloc(nn, 1);
+    if (!nv || !q || !q2 || !v2 || !kn) {
+        free(nv); free(q); free(q2); free(v2); free(kn);
+        return OR_ENOMEM;
+    }
+    /* normals and u_n where the central stencil is inside */
+    for (long i = 0; i < nn; i++) {
+        int ii[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / (n * n))};
+        double g[3] = {0, 0, 0}, gn = 0.0;
+        for (int a = 0; a < dim; a++) {
+            int lo = ii[a] > 0, hi = ii[a] < N;
+            if (lo && hi) g[a] = (phi[i + st[a]] - phi[i - st[a]]) / (2.0 * h);
+            else if (hi) g[a] = (phi[i + st[a]] - phi[i]) / h;
+            else g[a] = (phi[i] - phi[i - st[a]]) / h;
+            gn += g[a] * g[a];
+        }
+        gn = sqrt(gn);
+        for (int a = 0; a < dim; a++) nv[(size_t)dim * i + a] = gn > 0.0 ? g[a] / gn : 0.0;
+        if (type[i] != T_IN) continue;
+        int ok = 1;
+        for (int a = 0; a < dim; a++) {
+            if (ii[a] == 0 || ii[a] == N || type[i - st[a]] != T_IN || type[i + st[a]] != T_IN) ok = 0;
+        }
+        if (!ok) continue;
+        double un = 0.0;
+        for (int a = 0; a < dim; a++) un += nv[(size_t)dim * i + a] * (u[i + st[a]] - u[i - st[a]]) / (2.0 * h);
+        q[i] = un;
+        kn[i] = 1;
+    }
+    const double dtau = 0.5 * h;
+    /* the upwind neighbour of node i along axis a, or -1 */
+#define UPW(i, a)                                                                                          \
+    (nv[(size_t)dim * (i) + (a)] == 0.0                                                                    \
+         ? -1L                                                                                             \
+         : ((nv[(size_t)dim * (i) + (a)] > 0.0) ? ((((i) / st[a]) % n) > 0 ? (i) - st[a] : -1L)             \
+                                                 : ((((i) / st[a]) % n) < N ? (i) + st[a] : -1L)))
+    for (int it = 0; it < iters; it++) {
+        for (long i = 0; i < nn; i++) {
+            if (kn[i]) {
+                q2[i] = q[i];
+                continue;
+            }
+            double acc = 0.0;
+            for (int a = 0; a < dim; a++) {
+                long up = UPW(i, a);
+                if (up < 0) continue;
+                acc += fabs(nv[(size_t)dim * i + a]) * (q[i] - q[up]);
+            }
+            q2[i] = q[i] - (dtau / h) * acc;
+        }
+        double *t = q; q = q2; q2 = t;
+    }
+    for (long i = 0; i < nn; i++)
+        if (type[i] != T_IN) u[i] = 0.0;
+    for (int it = 0; it < iters; it++) {
+        for (long i = 0; i < nn; i++) {
+            if (type[i] == T_IN) {
+                v2[i] = u[i];
+                continue;
+            }
+            double acc = 0.0;
+            for (int a = 0; a < dim; a++) {
+                long up = UPW(i, a);
+                if (up < 0) continue;
+                acc += fabs(nv[(size_t)dim * i + a]) * (u[i] - u[up]);
+            }
+            v2[i] = u[i] - dtau * (acc / h - q[i]);
+        }
+        memcpy(u, v2, sizeof(double) * nn);
+    }
+#undef UPW
+    free(nv); free(q); free(q2); free(v2); free(kn);
+    return OR_OK;
+}

@@ -83,3 +83,52 @@ def test_mask_heat_step_keeps_linear_profiles(oracle_mod):
     assert np.all(one[:, 2: N // 2 - 2] == -1.0) and np.all(one[:, N // 2 + 2: N - 1] == 1.0)
     # the jump is smoothed symmetrically: lambda = 1/8 moves 1/4 toward each side
     assert np.allclose(one[:, N // 2 - 1], -0.75) and np.allclose(one[:, N // 2], 0.75)
+
+
+def _types(phi):
+    """inside phi < 0; ghost: not inside with an inside axis neighbour"""
+    ins = phi < 0
+    g = np.zeros_like(ins)
+    for ax in range(phi.ndim):
+        sl_lo = [slice(None)] * phi.ndim
+        sl_hi = [slice(None)] * phi.ndim
+        sl_lo[ax], sl_hi[ax] = slice(1, None), slice(None, -1)
+        g[tuple(sl_lo)] |= ins[tuple(sl_hi)]
+        g[tuple(sl_hi)] |= ins[tuple(sl_lo)]
+    t = np.zeros(phi.shape, dtype=np.int8)
+    t[ins] = 1
+    t[g & ~ins] = 2
+    return t
+
+
+def test_extrapolation_is_exact_for_linear_data_at_a_plane(oracle_mod):
+    """Linear data across a planar interface: the normal derivative is
+    constant and the upwind differences are exact, so the extended values are
+    the linear function itself (at ghosts away from the box edges)."""
+    N = 64
+    h = 2.0 / N
+    X, Y = workloads.node_coords(2, -1.0, 1.0, N)
+    phi = 0.6 * X - 0.8 * Y - 0.1
+    t = _types(phi)
+    u = 1.0 + 2.0 * X - 3.0 * Y
+    e = oracle_mod.extrapolate(phi, t, u, 2, N, h, 64)
+    inner = np.zeros(t.shape, dtype=bool)
+    inner[4:-4, 4:-4] = True
+    g = (t == 2) & inner
+    assert g.sum() > 50
+    assert np.abs(e - u)[g].max() <= 1e-12
+    assert np.array_equal(e[t == 1], u[t == 1])
+
+
+def test_extrapolation_is_second_order_at_the_ghosts(oracle_mod):
+    errs = []
+    for N in (32, 64, 128):
+        h = 2.0 / N
+        X, Y = workloads.node_coords(2, -1.0, 1.0, N)
+        phi = np.sqrt(X * X + Y * Y) - 0.7
+        t = _types(phi)
+        u = np.sin(2 * X) * np.cos(Y) + X * Y
+        e = oracle_mod.extrapolate(phi, t, u, 2, N, h, 64)
+        errs.append(np.abs(e - u)[t == 2].max())
+    o = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(o >= 1.8), (errs, o)
