@@ -139,6 +139,15 @@ int sulf_get_state_device(sulf_handle h, double* s_dev, double* c_dev);
    nodes are ignored) and set the time to t: checkpoint/resume. */
 int sulf_set_state(sulf_handle h, const double* s, const double* c, double t);
 
+/* Same, but only the values at inside nodes are read: the ghost values (on
+   which the c equation is discretised, Eq. FDc) are extrapolated from them
+   with second order, as the paper prescribes for non-uniform initial data
+   (Sec. 3.3, by a PDE extrapolation): the normal derivative u_n = n . grad u
+   is extended outward by 64 Jacobi steps of dq/dtau + n . grad q = 0, then u
+   by 64 steps of du/dtau + n . grad u = u_n (upwind toward the inside,
+   dtau = h/2, n the central-difference normal of the level set). */
+int sulf_set_state_extrapolated(sulf_handle h, const double* s, const double* c, double t);
+
 /* Same, from device arrays. */
 int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_dev, double t);
 

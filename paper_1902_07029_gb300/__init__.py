@@ -78,6 +78,7 @@ _SIGS = {
     "sulf_reinit_levelset": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]),
     "sulf_levelset_from_mask": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, _dp]),
+    "sulf_set_state_extrapolated": (ctypes.c_int, [P, _dp, _dp, ctypes.c_double]),
     "sulf_set_bc": (ctypes.c_int, [P, ctypes.c_int]),
     "sulf_dbg_level_rows": (ctypes.c_int, [P, ctypes.c_int, _dp, _dp]),
     "sulf_set_sources": (ctypes.c_int, [P, _dp, _dp, _dp, _dp]),
@@ -234,6 +235,13 @@ class Domain:
         s = np.ascontiguousarray(s, dtype=np.float64).ravel()
         c = np.ascontiguousarray(c, dtype=np.float64).ravel()
         _chk(self.lib, self.lib.sulf_set_state(self.h, _d(s), _d(c), t))
+
+    def set_state_extrapolated(self, s, c, t=0.0):
+        """Set the state from its inside values; the ghost values are
+        extrapolated (second order) from them."""
+        s = np.ascontiguousarray(s, dtype=np.float64).ravel()
+        c = np.ascontiguousarray(c, dtype=np.float64).ravel()
+        _chk(self.lib, self.lib.sulf_set_state_extrapolated(self.h, _d(s), _d(c), t))
 
     def set_state_device(self, s_ptr: int, c_ptr: int, t=0.0):
         _chk(self.lib, self.lib.sulf_set_state_device(self.h, P(s_ptr), P(c_ptr), t))

@@ -159,3 +159,150 @@ extern "C" int sulf_levelset_from_mask(const uint8_t* mask, int dim, int N, int 
     SULF_CUDA_TRY(cudaStreamSynchronize(sc.s));
     return SULF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Linear extrapolation of initial data from the inside nodes (the PDE approach
+// the paper cites for the ICs on the ghosts, Sec. 3.3): u_n = n . grad u where
+// the central stencil is inside, u_n extended by Jacobi steps of
+// d q / d tau + n . grad q = 0, then u by Jacobi steps of
+// d u / d tau + n . grad u = u_n; upwind differences toward the inside,
+// d tau = h / 2, n the central-difference unit normal of phi.
+
+namespace sulf {
+namespace {
+
+template <int D>
+__device__ __forceinline__ void unit_normal(const double* phi, long long i, const int* ii, int n, double h,
+                                            double* nv) {
+    const long long st[3] = {1, n, (long long)n * n};
+    double g[3] = {0, 0, 0}, gn = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        const bool lo = ii[a] > 0, hi = ii[a] < n - 1;
+        if (lo && hi)
+            g[a] = (phi[i + st[a]] - phi[i - st[a]]) / (2.0 * h);
+        else if (hi)
+            g[a] = (phi[i + st[a]] - phi[i]) / h;
+        else
+            g[a] = (phi[i] - phi[i - st[a]]) / h;
+        gn += g[a] * g[a];
+    }
+    gn = sqrt(gn);
+#pragma unroll
+    for (int a = 0; a < D; a++) nv[a] = gn > 0.0 ? g[a] / gn : 0.0;
+}
+
+// u_n at inside nodes whose axis neighbours are all inside, else 0 (unknown)
+template <int D>
+__global__ void k_xn_init(long long nn, int n, double h, const double* __restrict__ phi,
+                          const int8_t* __restrict__ type, const double* __restrict__ u, double* __restrict__ q) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    int ii[3];
+    box_coords<D>(i, n, ii);
+    const long long st[3] = {1, n, (long long)n * n};
+    bool ok = type[i] == T_IN;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+        if (ii[a] == 0 || ii[a] == n - 1 || type[i - st[a]] != T_IN || type[i + st[a]] != T_IN) ok = false;
+    double un = 0.0;
+    if (ok) {
+        double nv[3];
+        unit_normal<D>(phi, i, ii, n, h, nv);
+#pragma unroll
+        for (int a = 0; a < D; a++) un += nv[a] * (u[i + st[a]] - u[i - st[a]]) / (2.0 * h);
+    }
+    q[i] = un;
+}
+
+template <int D>
+__device__ __forceinline__ bool un_known(const int8_t* type, long long i, const int* ii, int n) {
+    const long long st[3] = {1, n, (long long)n * n};
+    if (type[i] != T_IN) return false;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+        if (ii[a] == 0 || ii[a] == n - 1 || type[i - st[a]] != T_IN || type[i + st[a]] != T_IN) return false;
+    return true;
+}
+
+// one Jacobi step: q (source = 0, known nodes fixed) or u (source q, inside
+// nodes fixed)
+template <int D, bool FOR_U>
+__global__ void k_x_step(long long nn, int n, double h, const double* __restrict__ phi,
+                         const int8_t* __restrict__ type, const double* __restrict__ src,
+                         const double* __restrict__ v, double* __restrict__ w) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    int ii[3];
+    box_coords<D>(i, n, ii);
+    const bool fixed = FOR_U ? type[i] == T_IN : un_known<D>(type, i, ii, n);
+    if (fixed) {
+        w[i] = v[i];
+        return;
+    }
+    const long long st[3] = {1, n, (long long)n * n};
+    double nv[3];
+    unit_normal<D>(phi, i, ii, n, h, nv);
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        long long up = -1;
+        if (nv[a] > 0.0 && ii[a] > 0) up = i - st[a];
+        if (nv[a] < 0.0 && ii[a] < n - 1) up = i + st[a];
+        if (up < 0) continue;
+        acc += fabs(nv[a]) * (v[i] - v[up]);
+    }
+    const double dtau = 0.5 * h;
+    w[i] = FOR_U ? v[i] - dtau * (acc / h - src[i]) : v[i] - (dtau / h) * acc;
+}
+
+__global__ void k_x_zero_outside(long long nn, const int8_t* __restrict__ type, double* __restrict__ u) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < nn && type[i] != T_IN) u[i] = 0.0;
+}
+
+}  // namespace
+
+// u (device, box of the finest level) extended from the inside nodes; work
+// arrays q, q2, u2 of nn doubles each
+int launch_extrapolate(const LevelGeo& L, double* u, double* q, double* q2, double* u2, int iters, cudaStream_t s) {
+    const long long nn = L.nn;
+    const int n = L.n;
+    const unsigned g = blocks_for(nn);
+    int launches = 0;
+    if (L.dim == 2)
+        k_xn_init<2><<<g, kLsThreads, 0, s>>>(nn, n, L.h, L.phi, L.type, u, q);
+    else
+        k_xn_init<3><<<g, kLsThreads, 0, s>>>(nn, n, L.h, L.phi, L.type, u, q);
+    launches++;
+    double *a = q, *b = q2;
+    for (int k = 0; k < iters; k++) {
+        if (L.dim == 2)
+            k_x_step<2, false><<<g, kLsThreads, 0, s>>>(nn, n, L.h, L.phi, L.type, nullptr, a, b);
+        else
+            k_x_step<3, false><<<g, kLsThreads, 0, s>>>(nn, n, L.h, L.phi, L.type, nullptr, a, b);
+        double* t = a;
+        a = b;
+        b = t;
+        launches++;
+    }
+    k_x_zero_outside<<<g, kLsThreads, 0, s>>>(nn, L.type, u);
+    launches++;
+    double *v = u, *w = u2;
+    for (int k = 0; k < iters; k++) {
+        if (L.dim == 2)
+            k_x_step<2, true><<<g, kLsThreads, 0, s>>>(nn, n, L.h, L.phi, L.type, a, v, w);
+        else
+            k_x_step<3, true><<<g, kLsThreads, 0, s>>>(nn, n, L.h, L.phi, L.type, a, v, w);
+        double* t = v;
+        v = w;
+        w = t;
+        launches++;
+    }
+    if (v != u) {
+        cudaMemcpyAsync(u, v, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+    }
+    return launches;
+}
+
+}  // namespace sulf

@@ -91,6 +91,7 @@ struct sulf_domain {
     double* src_stage = nullptr;
     double* sbg = nullptr;
     bool src_on = false, sbg_on = false;
+    double* xbuf = nullptr;  // 5 * nn doubles: extrapolation of initial data
     sulf_model model{};
     sulf_solver solver{};
     cudaStream_t stream = nullptr;
@@ -125,6 +126,11 @@ struct sulf_domain {
 };
 
 namespace {
+
+// Jacobi steps of each stage of the initial-data extrapolation (d tau = h/2:
+// the ghosts lie within about 2 h of the inside nodes whose normal derivative
+// is known, and the steps contract toward the steady state)
+constexpr int kExtrapolationIters = 64;
 
 sulf_solver default_solver() {
     sulf_solver s;
@@ -757,6 +763,24 @@ int sulf_get_state(sulf_handle h, double* s, double* c, int8_t* type) {
 int sulf_set_state_device(sulf_handle h, const double* s_dev, const double* c_dev, double t) {
     if (!valid(h) || !s_dev || !c_dev) return sulf_fail(SULF_EINVAL, "invalid arguments");
     h->launches += launch_import_state(h->geo[0], h->W, s_dev, c_dev, h->stream);
+    SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->t = t;
+    return SULF_OK;
+}
+
+int sulf_set_state_extrapolated(sulf_handle h, const double* s, const double* c, double t) {
+    if (!valid(h) || !s || !c) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const LevelGeo& G0 = h->geo[0];
+    const long long nn = G0.nn;
+    if (!h->xbuf) h->xbuf = (double*)h->mem.get(sizeof(double) * 5 * nn);
+    if (!h->xbuf) return sulf_fail(SULF_ENOMEM, "out of device memory");
+    double *us = h->xbuf, *uc = h->xbuf + nn, *q = h->xbuf + 2 * nn, *q2 = h->xbuf + 3 * nn, *u2 = h->xbuf + 4 * nn;
+    SULF_CUDA_TRY(cudaMemcpyAsync(us, s, sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
+    SULF_CUDA_TRY(cudaMemcpyAsync(uc, c, sizeof(double) * nn, cudaMemcpyHostToDevice, h->stream));
+    h->launches += launch_extrapolate(G0, us, q, q2, u2, kExtrapolationIters, h->stream);
+    h->launches += launch_extrapolate(G0, uc, q, q2, u2, kExtrapolationIters, h->stream);
+    h->launches += launch_import_state(G0, h->W, us, uc, h->stream);
+    SULF_CUDA_TRY(cudaGetLastError());
     SULF_CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->t = t;
     return SULF_OK;

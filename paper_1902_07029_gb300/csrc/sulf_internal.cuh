@@ -184,6 +184,10 @@ int launch_newton_update(const LevelGeo& L, double2* W, const double2* x, unsign
                          cudaStream_t s);
 int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* norm, cudaStream_t s);
 
+// linear extrapolation of u (device box of level L) from its inside nodes to
+// the rest of the box (levelset.cu); q, q2, u2 are work arrays of nn doubles
+int launch_extrapolate(const LevelGeo& L, double* u, double* q, double* q2, double* u2, int iters, cudaStream_t s);
+
 // CN average of manufactured source terms: src = ((f1o+f1n)/2, (f2o+f2n)/2)
 int launch_average_sources(long long nn, const double* f4, double2* src, cudaStream_t s);
 
