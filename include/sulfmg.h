@@ -76,11 +76,18 @@ typedef struct {
    pdl           1 = kernels of a step are launched as programmatic dependent
                  launches (each may be scheduled while its predecessor runs and
                  waits on the device for its completion); 0 = plain stream
-                 order.  Results are the same either way.                default 1 */
+                 order.  Results are the same either way.                default 1
+   ghost_compose 1 = the ghost_sweeps passes of one sweep's ghost relaxation
+                 are applied as one precomputed affine map per ghost (the
+                 passes are affine in the ghosts' values before them, their
+                 right-hand sides and the inside values; built per level for
+                 tau_s, ghost_sweeps and the boundary condition, and only
+                 where it stays within 24 (2-D) / 27 (3-D) entries per ghost
+                 on average); 0 = pass by pass.  Equal up to rounding.  default 1 */
 typedef struct {
     int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;
-    int precision, smoother, graphs, fuse_below, pdl;
+    int precision, smoother, graphs, fuse_below, pdl, ghost_compose;
 } sulf_solver;
 
 /* Counters and timings of the handle. */

@@ -18,9 +18,12 @@
 extern "C" {
 #endif
 
-/* info: N, n, ghosts, band nodes, active nodes of the coarsest level (0 on
-   other levels), inside nodes, then the ghost-row kinds: quadratic, linear,
-   identity (Sec. 3.3 and its fallbacks). */
+/* info (11 entries): N, n, ghosts, band nodes, active nodes of the coarsest
+   level (0 on other levels), inside nodes, then the ghost-row kinds:
+   quadratic, linear, identity (Sec. 3.3 and its fallbacks), then the entries
+   of the level's composed ghost relaxation (Eq. RelGhost, all passes of a
+   sweep as one affine map; -1 when the level relaxes pass by pass) and the
+   passes it composes (0 when none). */
 int sulf_dbg_level_info(sulf_handle h, int level, int64_t* info);
 
 /* node types of a level: 0 inactive, 1 inside, 2 ghost, 3 band (inactive nodes

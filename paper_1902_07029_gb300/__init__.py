@@ -27,7 +27,7 @@ class SulfSolver(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("ghost_sweeps", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("lin_rtol", ctypes.c_double), ("tau_s", ctypes.c_double), ("precision", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("graphs", ctypes.c_int), ("fuse_below", ctypes.c_int),
-                ("pdl", ctypes.c_int)]
+                ("pdl", ctypes.c_int), ("ghost_compose", ctypes.c_int)]
 
 
 class SulfStats(ctypes.Structure):
@@ -147,7 +147,8 @@ def _chk(lib, rc):
 
 def default_solver(**kw) -> SulfSolver:
     s = SulfSolver(nu1=2, nu2=2, cycle=1, max_newton=20, max_cycles=30, ghost_sweeps=4, newton_tol=1e-10,
-                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1, fuse_below=-1, pdl=1)
+                   lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1, fuse_below=-1, pdl=1,
+                   ghost_compose=1)
     for k, v in kw.items():
         setattr(s, k, v)
     return s
@@ -303,10 +304,11 @@ class Domain:
 
     # ---- stage-level entry points (interleaved (s,c) arrays) ----
     def level_info(self, l):
-        info = np.zeros(9, dtype=np.int64)
+        info = np.zeros(11, dtype=np.int64)
         _chk(self.lib, self.lib.sulf_dbg_level_info(self.h, l, info.ctypes.data_as(_i64p)))
         return dict(N=int(info[0]), n=int(info[1]), ng=int(info[2]), nb=int(info[3]), nact=int(info[4]),
-                    nin=int(info[5]), kinds=(int(info[6]), int(info[7]), int(info[8])))
+                    nin=int(info[5]), kinds=(int(info[6]), int(info[7]), int(info[8])),
+                    ghost_map_entries=int(info[9]), ghost_map_passes=int(info[10]))
 
     def level_type(self, l):
         n = self.level_info(l)["n"]

@@ -594,6 +594,125 @@ __global__ void k_band_info(const double* __restrict__ phi, const int8_t* __rest
 
 inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
+// ---- composed ghost relaxation (Eq. RelGhost) ----
+// One pass updates every ghost from the previous pass's values,
+//   s_g^{k+1} = s_g^k + tau (b_g - sum_j w_gj u_j^k),
+// u_j^k the s of member j: a fixed inside value, or ghost h's s_h^k.  The
+// passes are affine in the ghosts' s before the first pass, their right-hand
+// sides and the inside members' values, with coefficients fixed by the rows
+// and tau, so after P passes s_g is one short weighted sum.  It is expanded
+// pass by pass backwards from s_g^P, merging the terms that reach the same
+// ghost at the same pass (the frontier) and accumulating the fixed inputs.
+constexpr int kGopRowCap = 256;   // entries of one composed row
+constexpr int kGopFront = 64;     // ghosts of one frontier
+constexpr int kGopMaxPasses = 8;
+
+// per-thread workspace of the row expansion, in shared memory (4.5 KB a
+// thread; as local arrays it would make the driver reserve that much stack for
+// every resident thread of the device)
+struct GopWork {
+    double coef[kGopRowCap];
+    double ca[kGopFront], cb[kGopFront];
+    int code[kGopRowCap];
+    int fa[kGopFront], fb[kGopFront];
+};
+constexpr int kGopBuildThreads = 8;  // 36 KB of workspace per CTA
+
+template <int D>
+__device__ int gop_row(int gi, int passes, double tau, int ng, const int* __restrict__ gidx,
+                       const double* __restrict__ wk, const int* __restrict__ node, const int* __restrict__ src,
+                       GopWork& ws) {
+    const int K = D == 2 ? 9 : 27;
+    int* code = ws.code;
+    double* coef = ws.coef;
+    int *fa = ws.fa, *fb = ws.fb;
+    double *ca = ws.ca, *cb = ws.cb;
+    int nf = 1, n = 0;
+    fa[0] = gi;
+    ca[0] = 1.0;
+    auto out = [&](int c, double v) -> bool {
+        int j = 0;
+        while (j < n && code[j] != c) j++;
+        if (j == n) {
+            if (n == kGopRowCap) return false;
+            code[n] = c;
+            coef[n] = 0.0;
+            n++;
+        }
+        coef[j] += v;
+        return true;
+    };
+    for (int k = passes; k > 0; k--) {
+        int nn = 0;
+        auto front = [&](int h, double v) -> bool {
+            int j = 0;
+            while (j < nn && fb[j] != h) j++;
+            if (j == nn) {
+                if (nn == kGopFront) return false;
+                fb[nn] = h;
+                cb[nn] = 0.0;
+                nn++;
+            }
+            cb[j] += v;
+            return true;
+        };
+        for (int i = 0; i < nf; i++) {
+            const int h = fa[i];
+            const double a = ca[i];
+            if (!front(h, a)) return -1;
+            if (!out(~(2 * gidx[h] + 1), tau * a)) return -1;
+            for (int kk = 0; kk < K; kk++) {
+                const long long o = (long long)kk * ng + h;
+                const double w = wk[o];
+                if (w == 0.0) continue;
+                const double v = -tau * w * a;
+                const int sr = src[o];
+                if (sr >= 0) {
+                    if (!front(sr, v)) return -1;
+                } else if (!out(node[o], v)) {
+                    return -1;
+                }
+            }
+        }
+        for (int i = 0; i < nn; i++) {
+            fa[i] = fb[i];
+            ca[i] = cb[i];
+        }
+        nf = nn;
+    }
+    for (int i = 0; i < nf; i++)
+        if (!out(~(2 * fa[i]), ca[i])) return -1;
+    return n;
+}
+
+template <int D>
+__global__ void k_gop_count(int ng, int passes, double tau, const int* __restrict__ gidx,
+                            const double* __restrict__ wk, const int* __restrict__ node,
+                            const int* __restrict__ src, int* cnt) {
+    extern __shared__ GopWork gop_ws[];
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ng) return;
+    cnt[gi] = gop_row<D>(gi, passes, tau, ng, gidx, wk, node, src, gop_ws[threadIdx.x]);
+}
+
+template <int D>
+__global__ void k_gop_fill(int ng, int passes, double tau, const int* __restrict__ gidx,
+                           const double* __restrict__ wk, const int* __restrict__ node, const int* __restrict__ src,
+                           const int* __restrict__ ptr, int* gcode, double* gval, float* gval32) {
+    extern __shared__ GopWork gop_ws[];
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ng) return;
+    GopWork& ws = gop_ws[threadIdx.x];
+    const int n = gop_row<D>(gi, passes, tau, ng, gidx, wk, node, src, ws);
+    const int o = ptr[gi];
+    for (int j = 0; j < n; j++) {
+        gcode[o + j] = ws.code[j];
+        gval[o + j] = ws.coef[j];
+        gval32[o + j] = (float)ws.coef[j];
+    }
+}
+
+
 // ordered compaction: returns the count, fills out (allocated by the caller
 // after a first counting pass when out == nullptr)
 int compact(int which, const LevelGeo& L, int*& out, DevMem& mem, cudaStream_t s, std::string& err,
@@ -635,6 +754,74 @@ int compact(int which, const LevelGeo& L, int*& out, DevMem& mem, cudaStream_t s
 }
 
 }  // namespace
+
+int build_ghost_op(LevelGeo& L, double tau, int passes, int bc, DevMem& mem, cudaStream_t s, std::string& err,
+                   long long& launches) {
+    L.gop_on = false;
+    L.gop_tau = tau;
+    L.gop_passes = passes;
+    L.gop_bc = bc;
+    // the codes hold 2 * node + 1 in 31 bits
+    if (L.ng == 0 || passes < 1 || passes > kGopMaxPasses || L.nn >= (1LL << 30)) return SULF_OK;
+    if (!L.gop_ptr) {
+        L.gop_ptr = (int*)mem.get(sizeof(int) * (L.ng + 1));
+        if (!L.gop_ptr) {
+            err = "out of device memory";
+            return SULF_ENOMEM;
+        }
+    }
+    const int bt = kGopBuildThreads;
+    const size_t shm = sizeof(GopWork) * bt;
+    if (L.dim == 2)
+        k_gop_count<2><<<nblk(L.ng, bt), bt, shm, s>>>(L.ng, passes, tau, L.gidx, L.gwk, L.gnode, L.gsrc, L.gop_ptr);
+    else
+        k_gop_count<3><<<nblk(L.ng, bt), bt, shm, s>>>(L.ng, passes, tau, L.gidx, L.gwk, L.gnode, L.gsrc, L.gop_ptr);
+    launches++;
+    std::vector<int> cnt(L.ng + 1, 0);
+    if (cudaMemcpyAsync(cnt.data(), L.gop_ptr, sizeof(int) * L.ng, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        err = "ghost relaxation map failed";
+        return SULF_EDEVICE;
+    }
+    long long tot = 0;
+    for (int g = 0; g < L.ng; g++) {
+        if (cnt[g] < 0) return SULF_OK;  // a row too long: passes one by one
+        const int c = cnt[g];
+        cnt[g] = (int)tot;
+        tot += c;
+    }
+    cnt[L.ng] = (int)tot;
+    if (tot > (long long)(L.dim == 2 ? kGopAvg2 : kGopAvg3) * L.ng) return SULF_OK;
+    if (tot + 1 > L.gop_cap) {
+        L.gop_code = (int*)mem.get(sizeof(int) * (tot + 1));
+        L.gop_val = (double*)mem.get(sizeof(double) * (tot + 1));
+        L.gop_val32 = (float*)mem.get(sizeof(float) * (tot + 1));
+        if (!L.gop_code || !L.gop_val || !L.gop_val32) {
+            L.gop_cap = 0;
+            err = "out of device memory";
+            return SULF_ENOMEM;
+        }
+        L.gop_cap = tot + 1;
+    }
+    if (cudaMemcpyAsync(L.gop_ptr, cnt.data(), sizeof(int) * (L.ng + 1), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        err = "ghost relaxation map failed";
+        return SULF_EDEVICE;
+    }
+    if (L.dim == 2)
+        k_gop_fill<2><<<nblk(L.ng, bt), bt, shm, s>>>(L.ng, passes, tau, L.gidx, L.gwk, L.gnode, L.gsrc, L.gop_ptr,
+                                                      L.gop_code, L.gop_val, L.gop_val32);
+    else
+        k_gop_fill<3><<<nblk(L.ng, bt), bt, shm, s>>>(L.ng, passes, tau, L.gidx, L.gwk, L.gnode, L.gsrc, L.gop_ptr,
+                                                      L.gop_code, L.gop_val, L.gop_val32);
+    launches++;
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        err = "ghost relaxation map failed";
+        return SULF_EDEVICE;
+    }
+    L.gop_nnz = tot;
+    L.gop_on = true;
+    return SULF_OK;
+}
 
 int build_ghost_rows(LevelGeo& L, int bc, bool finest, cudaStream_t s, std::string& err, long long& launches) {
     if (L.ng == 0) return SULF_OK;

@@ -185,10 +185,13 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
 // ---------------------------------------------------------------------------
 // relaxation (Sec. 3.5.1)
 
+// one colour of inside nodes; with snap_n > 0 also the copy of the ghosts' s
+// (nodes sidx) into snap that the composed ghost relaxation starts from
 template <int D, typename T, bool PW>
 __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
                                                       const typename V2<T>::t* __restrict__ rhs,
-                                                      typename V2<T>::t* __restrict__ x, long long st1, long long st2) {
+                                                      typename V2<T>::t* __restrict__ x, long long st1, long long st2,
+                                                      const int* __restrict__ sidx, int snap_n, T* snap) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const long long st[3] = {1, st1, st2};
     // the list and the stencil coefficients are fixed during the linear solve:
@@ -199,7 +202,9 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
         p = list[t];
         k = stages::fetch_inside<D, T, PW>(p, cf, st);
     }
+    const int sg = t < snap_n ? sidx[t] : 0;
     pdl_enter();
+    if (t < snap_n) snap[t] = reinterpret_cast<const T*>(x + sg)[0];
     if (t >= cnt) return;
     stages::relax_apply<D, T, PW, false>(p, k, rhs, x, st);
 }
@@ -230,6 +235,66 @@ __global__ void __launch_bounds__(kT) k_ghost_pass(const int* __restrict__ gidx,
     if (!on) return;
     stages::ghost_pass_apply<D, T, false>(gi, g, tb, D == 2 ? &m : nullptr, q, qinv, rhs, x, sin, sout, c.tau,
                                           first != 0, last != 0);
+}
+
+// The ghost relaxation of one sweep as the composed map (geometry.cu): s_g =
+// sum_j val_j u(code_j), u the s of an inside node (x), a ghost's s before the
+// passes (snap) or a ghost's right-hand side; then the ghost's c row with the
+// new s_g.  kGopLanes lanes share a row: the entries are fetched before the
+// wait (they are fixed during the linear solve), so after it only one round of
+// gathered loads and a lane reduction remain.
+using stages::kGopLanes;
+constexpr int kGopPre = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kT) k_ghost_op(int ng, const int* __restrict__ gidx, const int* __restrict__ ptr,
+                                                  const int* __restrict__ code, const T* __restrict__ val,
+                                                  const typename V2<T>::t* __restrict__ gc,
+                                                  const typename V2<T>::t* rhs, typename V2<T>::t* x,
+                                                  const T* snap) {
+    typedef typename V2<T>::t T2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gi = t / kGopLanes, ln = t % kGopLanes;
+    const bool on = gi < ng;
+    int beg = 0, end = 0, g = 0;
+    int cd[kGopPre];
+    T w[kGopPre];
+    T2 q;
+    q.x = 0;
+    q.y = 1;
+    if (on) {
+        beg = ptr[gi];
+        end = ptr[gi + 1];
+#pragma unroll
+        for (int i = 0; i < kGopPre; i++) {
+            const int j = beg + ln + i * kGopLanes;
+            cd[i] = j < end ? code[j] : 0;
+            w[i] = j < end ? val[j] : (T)0;
+        }
+        if (ln == 0) {
+            g = gidx[gi];
+            q = gc[gi];
+        }
+    }
+    pdl_enter();
+    auto u = [&](int c) -> T { return stages::gop_input<T>(c, x, rhs, snap); };
+    const T by = on && ln == 0 ? reinterpret_cast<const T*>(rhs + g)[1] : (T)0;
+    T acc = 0;
+    if (on) {
+        T v[kGopPre];
+#pragma unroll
+        for (int i = 0; i < kGopPre; i++) v[i] = beg + ln + i * kGopLanes < end ? u(cd[i]) : (T)0;
+#pragma unroll
+        for (int i = 0; i < kGopPre; i++) acc = stages::fmadd(w[i], v[i], acc);
+        for (int j = beg + ln + kGopPre * kGopLanes; j < end; j += kGopLanes) acc = stages::fmadd(val[j], u(code[j]), acc);
+    }
+#pragma unroll
+    for (int o = kGopLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!on || ln != 0) return;
+    T2 r;
+    r.x = acc;
+    r.y = stages::fmadd(-q.x, acc, by) * ((T)1 / q.y);
+    x[g] = r;
 }
 
 template <typename T>
@@ -744,23 +809,33 @@ int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cuda
 
 template <int D, typename T>
 int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int colour, bool pointwise,
-                        cudaStream_t s) {
+                        T* snap, cudaStream_t s) {
     int cnt = L.nin[colour];
-    if (cnt == 0) return 0;
+    const int sn = snap ? L.ng : 0;
+    const int tot = cnt > sn ? cnt : sn;
+    if (tot == 0) return 0;
     (void)c;
     CoefPtr<D, T> cf = coef_ptr<D, T>(V);
     if (pointwise)
-        launch_k(k_relax_inside<D, T, true>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf,
-                 V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, true>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
+                 V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     else
-        launch_k(k_relax_inside<D, T, false>, grid_for(cnt), block_for(cnt), 0, s, L.inl[colour], cnt, cf,
-                 V.rhs, V.x, L.st[1], L.st[2]);
+        launch_k(k_relax_inside<D, T, false>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
+                 V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     return 1;
 }
 
 template <int D, typename T>
-int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, cudaStream_t s) {
+int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, bool composed,
+                        cudaStream_t s) {
     if (L.ng == 0 || passes < 1) return 0;
+    if (composed) {
+        const long long nt = (long long)L.ng * kGopLanes;
+        const T* val = std::is_same<T, float>::value ? (const T*)L.gop_val32 : (const T*)L.gop_val;
+        launch_k(k_ghost_op<T>, grid_for(nt), block_for(nt), 0, s, L.ng, L.gidx, L.gop_ptr, L.gop_code, val, V.gc,
+                 V.rhs, V.x, V.gbuf[0]);
+        return 1;
+    }
     int n = 0;
     for (int p = 0; p < passes; p++) {
         bool first = p == 0, last = p == passes - 1 && passes > 1;
@@ -934,9 +1009,10 @@ int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double*
 
 #define SULF_INST(D, T)                                                                                          \
     template int launch_coefs<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, cudaStream_t);          \
-    template int launch_relax_inside<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, bool,       \
+    template int launch_relax_inside<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, bool, T*,   \
                                            cudaStream_t);                                                        \
-    template int launch_relax_ghosts<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, cudaStream_t); \
+    template int launch_relax_ghosts<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, bool,          \
+                                           cudaStream_t);                                                        \
     template int launch_residual<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, unsigned long long*,  \
                                        cudaStream_t);                                                            \
     template int launch_extend<D, T>(const LevelGeo&, const LevelVec<T>&, cudaStream_t);                         \

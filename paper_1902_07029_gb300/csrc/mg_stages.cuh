@@ -277,6 +277,52 @@ __device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const G
     ghost_pass_apply<D, T, CG>(gi, gidx[gi], tb, pre, q, (T)1 / q.y, rhs, x, sin, sout, tau, first, last);
 }
 
+// The composed ghost relaxation (all passes of a sweep as one affine map per
+// ghost, built in geometry.cu).  An entry's code names its input: the s of box
+// node code (code >= 0, an inside member), else with u = ~code the s of ghost
+// u >> 1 before the passes (u even, from the copy snap) or the right-hand side
+// of box node u >> 1 (u odd).
+constexpr int kGopLanes = 8;
+
+template <typename T>
+__device__ __forceinline__ T gop_input(int code, const typename V2<T>::t* x, const typename V2<T>::t* rhs,
+                                       const T* snap) {
+    if (code >= 0) return reinterpret_cast<const T*>(x + code)[0];
+    const unsigned u = ~(unsigned)code;
+    return (u & 1u) ? reinterpret_cast<const T*>(rhs + (u >> 1))[0] : snap[u >> 1];
+}
+
+// lane k of kGopLanes sums the entries beg + k, beg + k + kGopLanes, ... (one
+// FMA chain each); the lane sums are combined pairwise, lane 0 with lane 4,
+// then 2, then 1: the order of the per-level kernel's shuffle reduction, so
+// both give the same bits
+template <typename T>
+__device__ __forceinline__ T gop_lane_tree(const T (&p)[kGopLanes]) {
+    return ((p[0] + p[4]) + (p[2] + p[6])) + ((p[1] + p[5]) + (p[3] + p[7]));
+}
+
+// the whole row in one thread, then the ghost's c row with the new s_g (as in
+// ghost_pass_apply)
+template <typename T>
+__device__ __forceinline__ void gop_node(int gi, long long g, const int* ptr, const int* code, const T* val,
+                                         typename V2<T>::t q, const typename V2<T>::t* rhs, typename V2<T>::t* x,
+                                         const T* snap) {
+    const int beg = ptr[gi], end = ptr[gi + 1];
+    T p[kGopLanes];
+#pragma unroll
+    for (int k = 0; k < kGopLanes; k++) {
+        T a = 0;
+        for (int j = beg + k; j < end; j += kGopLanes) a = fmadd(val[j], gop_input<T>(code[j], x, rhs, snap), a);
+        p[k] = a;
+    }
+    const T sg = gop_lane_tree<T>(p);
+    const T by = reinterpret_cast<const T*>(rhs + g)[1];
+    typename V2<T>::t r;
+    r.x = sg;
+    r.y = fmadd(-q.x, sg, by) * ((T)1 / q.y);
+    x[g] = r;
+}
+
 // defect r = rhs - J x at node p of kind 1 (inside, coefficients k) or 2
 // (ghost gi, its row and c-row q); returns max(|r_s|, |r_c|) as bits
 template <int D, typename T, bool CG>

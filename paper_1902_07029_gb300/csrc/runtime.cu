@@ -54,6 +54,9 @@ extern "C" unsigned long long sulf_estimate_device_bytes(int dim, int N, int coa
     // nodes on every level (the coarse levels of thin 3-D shapes approach it)
     const double members = dim == 2 ? 9.0 : 27.0;
     per_level += (dim == 2 ? 0.08 : 0.15) * (members * 20.0 + 17.0 * dim);  // + orders, theta, normal
+    // composed ghost relaxation: at most 24 (2-D) / 27 (3-D) entries per ghost
+    // of 16 B (code 4, FP64 and FP32 weight) and the row pointer
+    per_level += (dim == 2 ? 0.08 * (24.0 * 16.0 + 4.0) : 0.15 * (27.0 * 16.0 + 4.0));
     // band extension operator: 16 B per entry, at most 1.5 (2-D) / 3.2 (3-D)
     // entries per box node on any level
     per_level += (dim == 2 ? 1.5 : 3.2) * 16.0;

@@ -148,6 +148,7 @@ sulf_solver default_solver() {
     s.graphs = 1;
     s.fuse_below = -1;
     s.pdl = 1;
+    s.ghost_compose = 1;
     return s;
 }
 
@@ -171,6 +172,13 @@ double bits_to_double(unsigned long long b) {
     return d;
 }
 
+// the ghost relaxation parameter of level l; Neumann rows have a diagonal of
+// order 1/h: tau_s scales the bound of Eq. CFLcondN, 2 sqrt(2) h / 3 in 2-D,
+// i.e. 4 h / (3 sqrt(d))
+double level_tau(const sulf_domain* d, int l) {
+    return d->bc ? d->solver.tau_s * tail_tau_scale(d->dim, d->geo[l].h) : d->solver.tau_s;
+}
+
 template <typename T>
 Coef<T> make_coef(const sulf_domain* d, int l) {
     Coef<T> c;
@@ -182,9 +190,7 @@ Coef<T> make_coef(const sulf_domain* d, int l) {
     c.a2ms = (T)(m.a / (2.0 * m.m_s));
     c.idt = (T)(1.0 / d->dt);
     c.kap = (T)(m.d / (4.0 * h * h));
-    // Neumann rows have a diagonal of order 1/h: tau_s scales the bound of
-    // Eq. CFLcondN, 2 sqrt(2) h / 3 in 2-D, i.e. 4 h / (3 sqrt(d))
-    c.tau = (T)(d->bc ? d->solver.tau_s * tail_tau_scale(d->dim, h) : d->solver.tau_s);
+    c.tau = (T)level_tau(d, l);
     return c;
 }
 
@@ -293,6 +299,37 @@ int ensure_tail(sulf_domain* d, const LevelVec<T>* V) {
     return SULF_OK;
 }
 
+// forget the captured cycles (they hold pointers and parameters that changed)
+void drop_graphs(sulf_domain* d) {
+    for (auto& g : d->graph)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+}
+
+// (re)build the composed ghost relaxation of every level whose map was built
+// for another relaxation parameter, pass count or boundary condition
+int refresh_ghost_ops(sulf_domain* d) {
+    if (!d->solver.ghost_compose) return SULF_OK;
+    bool changed = false;
+    for (int l = 0; l < d->L; l++) {
+        LevelGeo& G = d->geo[l];
+        const double tau = level_tau(d, l);
+        if (G.gop_bc == d->bc && G.gop_passes == d->solver.ghost_sweeps && G.gop_tau == tau) continue;
+        std::string err;
+        int rc = build_ghost_op(G, tau, d->solver.ghost_sweeps, d->bc, d->mem, d->stream, err, d->launches);
+        if (rc) return sulf_fail(rc, err);
+        changed = true;
+    }
+    if (changed) {
+        // the fused kernel's descriptors hold the maps' pointers
+        drop_graphs(d);
+        d->tail_ready[0] = d->tail_ready[1] = false;
+    }
+    return SULF_OK;
+}
+
 // ---- multigrid on precision T ----
 template <int D, typename T>
 struct MG {
@@ -306,6 +343,10 @@ struct MG {
         bool pw = d->solver.smoother == 1;
         const bool timed_sweep = l == 0 && (d->prof == 2 || (d->prof == 1 && fine_sweeps == 0));
         if (l == 0) fine_sweeps++;
+        // the composed ghost relaxation starts from a copy of the ghosts' s
+        // taken by the second colour's launch
+        const bool gop =
+            d->solver.ghost_compose && G.gop_bc == d->bc && ghost_op_ready<T>(G, c.tau, d->solver.ghost_sweeps);
         for (int colour = 0; colour < 2; colour++) {
             bool timed = timed_sweep;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -316,13 +357,14 @@ struct MG {
                 e0 = next_event(d);
                 cudaEventRecordWithFlags(e0, d->stream, fl);
             }
-            d->launches += launch_relax_inside<D, T>(G, V[l], c, colour, pw, d->stream);
+            d->launches += launch_relax_inside<D, T>(G, V[l], c, colour, pw,
+                                                     gop && colour == 1 ? V[l].gbuf[0] : nullptr, d->stream);
             if (timed) {
                 e1 = next_event(d);
                 cudaEventRecordWithFlags(e1, d->stream, fl);
             }
         }
-        d->launches += launch_relax_ghosts<D, T>(G, V[l], c, d->solver.ghost_sweeps, d->stream);
+        d->launches += launch_relax_ghosts<D, T>(G, V[l], c, d->solver.ghost_sweeps, gop, d->stream);
         return SULF_OK;
     }
 
@@ -335,7 +377,13 @@ struct MG {
         int rc;
         if (l == tail_level(d) && d->tail_ready[p] && d->solver.cycle == 1) {
             // this level and all coarser ones in one single-CTA launch
-            rc = launch_tail<D, T>(d->tail_desc[p], l, d->L, d->solver, d->bc, d->stream);
+            bool compose = d->solver.ghost_compose != 0;
+            for (int k = l; k < d->L && compose; k++) {
+                const LevelGeo& G = d->geo[k];
+                compose = G.ng == 0 || (G.gop_bc == d->bc &&
+                                        ghost_op_ready<T>(G, make_coef<T>(d, k).tau, d->solver.ghost_sweeps));
+            }
+            rc = launch_tail<D, T>(d->tail_desc[p], l, d->L, d->solver, d->bc, compose, d->stream);
             if (rc) return rc;
             d->launches += 1;
             return SULF_OK;
@@ -413,7 +461,8 @@ bool same_solver(const sulf_solver& a, const sulf_solver& b) {
     return a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.cycle == b.cycle && a.max_newton == b.max_newton &&
            a.max_cycles == b.max_cycles && a.ghost_sweeps == b.ghost_sweeps && a.newton_tol == b.newton_tol &&
            a.lin_rtol == b.lin_rtol && a.tau_s == b.tau_s && a.precision == b.precision && a.smoother == b.smoother &&
-           a.graphs == b.graphs && a.fuse_below == b.fuse_below && a.pdl == b.pdl;
+           a.graphs == b.graphs && a.fuse_below == b.fuse_below && a.pdl == b.pdl &&
+           a.ghost_compose == b.ghost_compose;
 }
 
 // launches of the calling thread use programmatic dependent launch while the
@@ -681,6 +730,7 @@ int sulf_create_domain(const double* levelset, int dim, const double* box, int N
             if (cudaStreamSynchronize(d->stream) != cudaSuccess) rc = sulf_fail(SULF_EDEVICE, "initialisation failed");
         }
     }
+    if (rc == SULF_OK) rc = refresh_ghost_ops(d);
     if (rc != SULF_OK) {
         std::string keep = g_err;
         sulf_destroy(d);
@@ -707,9 +757,10 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
     if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || (v.cycle != 1 && v.cycle != 2) || v.max_newton < 1 ||
         v.max_cycles < 1 || v.ghost_sweeps < 1 || !(v.tau_s > 0 && v.tau_s < 1) || !(v.newton_tol > 0) ||
         !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1) || v.fuse_below < -1 ||
-        (v.pdl != 0 && v.pdl != 1))
+        (v.pdl != 0 && v.pdl != 1) || (v.ghost_compose != 0 && v.ghost_compose != 1))
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
+    if (int rc = refresh_ghost_ops(h)) return rc;
     if (v.precision == 1) return ensure32(h);
     return SULF_OK;
 }
@@ -811,12 +862,8 @@ int sulf_set_bc(sulf_handle h, int type) {
     h->bc = type;
     // the captured cycles bake the relaxation parameter and the fused kernel's
     // boundary condition: capture them again
-    for (auto& g : h->graph)
-        if (g.exec) {
-            cudaGraphExecDestroy(g.exec);
-            g.exec = nullptr;
-        }
-    return SULF_OK;
+    drop_graphs(h);
+    return refresh_ghost_ops(h);
 }
 
 int sulf_set_sources(sulf_handle h, const double* f1_old, const double* f1_new, const double* f2_old,
@@ -911,6 +958,8 @@ int sulf_dbg_level_info(sulf_handle h, int l, int64_t* info) {
     info[4] = l == h->L - 1 ? G.nact : 0;
     info[5] = G.nin[0] + (int64_t)G.nin[1];
     for (int k = 0; k < 3; k++) info[6 + k] = G.kinds[k];
+    info[9] = G.gop_on ? G.gop_nnz : -1;
+    info[10] = G.gop_on ? G.gop_passes : 0;
     return SULF_OK;
 }
 

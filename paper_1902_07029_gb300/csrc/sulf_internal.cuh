@@ -80,6 +80,21 @@ struct LevelGeo {
     double* eval = nullptr;
     float* eval32 = nullptr;
     long long ne = 0;
+    // the P passes of the ghost relaxation composed into one affine map per
+    // ghost (CSR over ghosts): s_g after the passes is sum_j gop_val[j] *
+    // u(gop_code[j]) over j in [gop_ptr[gi], gop_ptr[gi+1]), u(code) the s of
+    // box node code (code >= 0), else with u = ~code: the s of ghost u >> 1
+    // before the passes (u even) or the right-hand side of box node u >> 1 (u
+    // odd).  Built for (gop_tau, gop_passes, gop_bc); gop_on false where the
+    // map would be too large (the passes then run one by one).
+    int* gop_ptr = nullptr;
+    int* gop_code = nullptr;
+    double* gop_val = nullptr;
+    float* gop_val32 = nullptr;
+    long long gop_nnz = 0, gop_cap = 0;
+    bool gop_on = false;
+    double gop_tau = 0;
+    int gop_passes = 0, gop_bc = -1;
     int nact = 0;            // coarsest level: active list and map
     int* act = nullptr;
     int* apos = nullptr;
@@ -146,15 +161,34 @@ int build_level_geometry(LevelGeo& L, const LevelGeo* finer, bool finest, bool c
 // (0 Dirichlet, Eq. BCs; 1 Neumann, Eq. BCsN): normals, orders, weights,
 // member tables; the finest level refuses identity rows (SULF_EGEOM)
 int build_ghost_rows(LevelGeo& L, int bc, bool finest, cudaStream_t s, std::string& err, long long& launches);
+// (re)build the composed ghost relaxation map of a level for relaxation
+// parameter tau, `passes` passes and the current rows (boundary condition bc);
+// leaves gop_on false where a row or the whole map exceeds its size bound
+int build_ghost_op(LevelGeo& L, double tau, int passes, int bc, DevMem& mem, cudaStream_t s, std::string& err,
+                   long long& launches);
+// entries per ghost the composed map may hold on average (device-memory bound)
+constexpr int kGopAvg2 = 24, kGopAvg3 = 27;
+// whether the level's composed map applies to relaxation parameter tau (in
+// the precision of the cycle) and `passes` passes
+template <typename T>
+inline bool ghost_op_ready(const LevelGeo& L, T tau, int passes) {
+    return L.gop_on && L.gop_passes == passes && (T)L.gop_tau == tau;
+}
 
 // ---- multigrid and Newton kernels (kernels.cu); each returns kernels launched ----
 template <int D, typename T>
 int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cudaStream_t s);
+// snap: when not null, the same launch also copies the s of every ghost of the
+// level into snap (ghost order); the inside update never writes a ghost
 template <int D, typename T>
 int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int colour, bool pointwise,
-                        cudaStream_t s);
+                        T* snap, cudaStream_t s);
+// the ghost relaxation of one sweep: the composed map when `composed` (the
+// caller checked ghost_op_ready and had the preceding inside launch copy the
+// ghosts' s into V.gbuf[0]), else pass by pass
 template <int D, typename T>
-int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, cudaStream_t s);
+int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, bool composed,
+                        cudaStream_t s);
 template <int D, typename T>
 int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, unsigned long long* norm,
                     cudaStream_t s);
@@ -204,8 +238,11 @@ int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double*
 size_t tail_desc_bytes(int L);
 template <typename T>
 int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, cudaStream_t s);
+// compose: every level from l0 down relaxes its ghosts by the composed map
+// (the descriptor's pointers are those of the maps built for the current
+// solver controls and boundary condition)
 template <int D, typename T>
-int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int bc, cudaStream_t s);
+int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int bc, bool compose, cudaStream_t s);
 
 // factor of tau_s for Neumann ghost rows on a level of spacing h (Eq.
 // CFLcondN): 4 h / (3 sqrt(dim)), i.e. 2 sqrt(2) h / 3 in 2-D

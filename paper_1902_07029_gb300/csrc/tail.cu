@@ -47,10 +47,15 @@ struct TailLevel {
     const T2* Ia;
     const T2* Ib;
     const T2* gc;
+    // composed ghost relaxation (null where the level has none)
+    const int* gop_ptr;
+    const int* gop_code;
+    const T* gop_val;
 };
 
 struct TailParams {
     int l0, L, nu1, nu2, passes, pointwise, bc;
+    int compose;  // every fused level relaxes its ghosts by the composed map
     double tau;
 };
 
@@ -80,7 +85,18 @@ __device__ void tail_relax(const TailLevel<T>& v, const TailParams& pr, int tid,
             else
                 stages::relax_node<D, T, false, false>(list[t], cf, v.rhs, v.x, st);
         }
+        // the composed ghost relaxation starts from the ghosts' s, which the
+        // inside update does not write
+        if (colour == 1 && pr.compose)
+            for (int gi = tid; gi < v.ls.ng; gi += nthr)
+                v.gbuf[0][gi] = reinterpret_cast<const T*>(v.x + v.ls.lg[gi])[0];
         __syncthreads();
+    }
+    if (pr.compose) {
+        for (int gi = tid; gi < v.ls.ng; gi += nthr)
+            stages::gop_node<T>(gi, v.ls.lg[gi], v.gop_ptr, v.gop_code, v.gop_val, v.gc[gi], v.rhs, v.x, v.gbuf[0]);
+        __syncthreads();
+        return;
     }
     const T tau = (T)(pr.bc ? pr.tau * tail_tau_scale(D, v.h) : pr.tau);
     for (int p = 0; p < pr.passes; p++) {
@@ -179,6 +195,9 @@ TailLevel<T> describe(const LevelGeo& G, const LevelVec<T>& V) {
     t.Ia = V.Ia;
     t.Ib = V.Ib;
     t.gc = V.gc;
+    t.gop_ptr = G.gop_on ? G.gop_ptr : nullptr;
+    t.gop_code = G.gop_on ? G.gop_code : nullptr;
+    t.gop_val = !G.gop_on ? nullptr : std::is_same<T, float>::value ? (const T*)G.gop_val32 : (const T*)G.gop_val;
     return t;
 }
 
@@ -199,8 +218,9 @@ int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, 
 
 namespace {
 
-TailParams make_params(int l0, int L, const sulf_solver& sv, int bc, int D) {
+TailParams make_params(int l0, int L, const sulf_solver& sv, int bc, bool compose, int D) {
     TailParams pr;
+    pr.compose = compose ? 1 : 0;
     pr.l0 = l0;
     pr.L = L;
     pr.nu1 = sv.nu1;
@@ -216,8 +236,9 @@ TailParams make_params(int l0, int L, const sulf_solver& sv, int bc, int D) {
 }  // namespace
 
 template <int D, typename T>
-int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int bc, cudaStream_t s) {
-    launch_k(k_tail<D, T>, 1, kTailThreads, 0, s, (const TailLevel<T>*)dev_desc, make_params(l0, L, sv, bc, D));
+int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int bc, bool compose, cudaStream_t s) {
+    launch_k(k_tail<D, T>, 1, kTailThreads, 0, s, (const TailLevel<T>*)dev_desc,
+             make_params(l0, L, sv, bc, compose, D));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sulf_fail_cuda(e, "fused coarse-level cycle launch");
     return SULF_OK;
@@ -225,9 +246,9 @@ int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int 
 
 template int upload_tail_desc<double>(const LevelGeo*, const LevelVec<double>*, int, void*, cudaStream_t);
 template int upload_tail_desc<float>(const LevelGeo*, const LevelVec<float>*, int, void*, cudaStream_t);
-template int launch_tail<2, double>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
-template int launch_tail<2, float>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
-template int launch_tail<3, double>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
-template int launch_tail<3, float>(const void*, int, int, const sulf_solver&, int, cudaStream_t);
+template int launch_tail<2, double>(const void*, int, int, const sulf_solver&, int, bool, cudaStream_t);
+template int launch_tail<2, float>(const void*, int, int, const sulf_solver&, int, bool, cudaStream_t);
+template int launch_tail<3, double>(const void*, int, int, const sulf_solver&, int, bool, cudaStream_t);
+template int launch_tail<3, float>(const void*, int, int, const sulf_solver&, int, bool, cudaStream_t);
 
 }  // namespace sulf

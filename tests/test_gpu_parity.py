@@ -86,8 +86,15 @@ def test_stages(sulfmg, oracle_mod, name, mk):
         tl = ref.level_type(l)
         Wc, x, rhs = _rand_state(rng, tl), _rand_vec(rng, tl), _rand_vec(rng, tl)
         _close(dom.apply_J(l, dt, Wc, x), ref.apply_J(l, dt, Wc, x), STAGE_TOL)
-        _close(dom.smooth(l, dt, Wc, rhs, x, 1), ref.smooth(l, dt, Wc, rhs, x, 1), STAGE_TOL)
-        _close(dom.smooth(l, dt, Wc, rhs, x, 3), ref.smooth(l, dt, Wc, rhs, x, 3), 1e-11)
+        # the ghost passes composed into one map per ghost (default) and pass by pass
+        info = dom.level_info(l)
+        if info["ng"] > 0:
+            assert info["ghost_map_passes"] == 4 and 0 < info["ghost_map_entries"] <= 27 * info["ng"]
+        for compose in (1, 0):
+            dom.set_solver(ghost_compose=compose)
+            _close(dom.smooth(l, dt, Wc, rhs, x, 1), ref.smooth(l, dt, Wc, rhs, x, 1), STAGE_TOL)
+            _close(dom.smooth(l, dt, Wc, rhs, x, 3), ref.smooth(l, dt, Wc, rhs, x, 3), 1e-11)
+        dom.set_solver()
         if l + 1 < ref.nlev:
             res = _rand_vec(rng, tl)
             cg, fg = dom.restrict(l, res)
@@ -154,10 +161,11 @@ def test_steps_fp64(sulfmg, oracle_mod, name, mk):
 def test_steps_unfused_and_w_cycle(sulfmg, oracle_mod, name, mk):
     """every level as separate kernels without graphs, and the paper's W-cycle"""
     phi, dim, N, cN, dt, nsteps = mk()
-    for kw in (dict(fuse_below=0, graphs=0), dict(cycle=2, nu1=2, nu2=1), dict(pdl=0)):
+    for kw in (dict(fuse_below=0, graphs=0), dict(cycle=2, nu1=2, nu2=1), dict(pdl=0), dict(ghost_compose=0),
+               dict(ghost_sweeps=2, tau_s=0.7)):
         dom, ref = _pair(sulfmg, oracle_mod, phi, dim, N, cN)
         dom.set_solver(**kw)
-        ref.set_solver(**{k: v for k, v in kw.items() if k in ("cycle", "nu1", "nu2")})
+        ref.set_solver(**{k: v for k, v in kw.items() if k in ("cycle", "nu1", "nu2", "ghost_sweeps", "tau_s")})
         dom.step(dt, nsteps)
         ref.step(dt, nsteps)
         s, c, t = dom.get_state()
