@@ -55,7 +55,7 @@ RELAX_FLOPS_3D = 30
 RELAX_BYTES = {2: RELAX_BYTES_2D, 3: RELAX_BYTES_3D}
 # DRAM bytes (read + write) of one finest-level relaxation launch from an ncu
 # capture of the current kernel (cold cache), per workload and precision
-RELAX_TRAFFIC = {("star1025", "fp64"): (31.31e6 + 10.5e3, "profiles/relax_inside_fp64_star1025.md")}
+RELAX_TRAFFIC = {("star1025", "fp64"): (31.30e6 + 17.0e3, "profiles/relax_inside_fp64_star1025.md")}
 RELAX_FLOPS = {2: RELAX_FLOPS_2D, 3: RELAX_FLOPS_3D}
 
 

@@ -11,6 +11,8 @@
 #include <atomic>
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "mg_stages.cuh"
 
 namespace sulf {
@@ -545,9 +547,12 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
                 A[(long long)pr * m + j] = tmp;
             }
         __syncthreads();
-        const T inv = (T)1 / A[(long long)k * m + k];
+        // the pivot's reciprocal once (every thread dividing would load the
+        // FP64 pipe, two lanes per SM per clock)
+        if (threadIdx.x == 0) fac[m] = (T)1 / A[(long long)k * m + k];
         for (int i = threadIdx.x; i < m; i += blockDim.x) fac[i] = A[(long long)i * m + k];
         __syncthreads();
+        const T inv = fac[m];
         for (int j = threadIdx.x; j < m; j += blockDim.x)
             A[(long long)k * m + j] = j == k ? inv : A[(long long)k * m + j] * inv;
         __syncthreads();
@@ -577,6 +582,175 @@ __global__ void __launch_bounds__(1024) k_coarsest_factor(int nact, const int* _
         __syncthreads();
     }
     for (long long i = threadIdx.x; i < mm; i += blockDim.x) Ainv_g[i] = A[i];
+}
+
+// The same assembly and Gauss-Jordan inversion spread over a thread-block
+// cluster: CTA r of C owns the columns j with j % C == r (m rows each, in its
+// shared memory).  Step k: the owner of column k finds the pivot row in it and
+// writes the column, after the row interchange, and the pivot row index into
+// every CTA's shared memory (double-buffered by the parity of k); one cluster
+// barrier; then each CTA interchanges, scales and eliminates in its own
+// columns.  Every matrix entry sees the operations of the single-CTA kernel in
+// the same order.  The inverse is written out with the final column
+// permutation applied.
+constexpr int kFacCluster = 8;
+constexpr int kFacThreads = 512;
+
+template <typename T>
+inline size_t factor_cluster_smem(int m) {
+    const size_t mc = ((size_t)m + kFacCluster - 1) / kFacCluster;
+    return sizeof(T) * ((size_t)m * mc + 2 * ((size_t)m + 1)) + sizeof(int) * 3 * (size_t)m;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kFacThreads) k_coarsest_factor_cluster(
+    int nact, const int* __restrict__ act, const int* __restrict__ apos, const int8_t* __restrict__ type,
+    const int* __restrict__ gpos, GhostTab<T> tb, const typename V2<T>::t* __restrict__ Wc, Offs<D> of, Coef<T> c,
+    T* Ainv_g, int* singular) {
+    namespace cg = cooperative_groups;
+    pdl_enter();
+    typedef typename V2<T>::t T2;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int me = (int)cl.block_rank();
+    const int m = 2 * nact;
+    const int mc = (m + C - 1) / C;  // local column jl is global column jl * C + me
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* A = reinterpret_cast<T*>(smem_raw);  // m x mc, row-major
+    T* fac = A + (size_t)m * mc;             // two buffers of m + 1
+    int* piv = reinterpret_cast<int*>(fac + 2 * (m + 1));
+    int* idx = piv + m;
+    int* pos = idx + m;
+    for (int i = threadIdx.x; i < m * mc; i += blockDim.x) A[i] = 0;
+    __syncthreads();
+    auto add = [&](int i, int j, T v) {
+        if (j % C == me) A[(size_t)i * mc + j / C] += v;
+    };
+    for (int r = threadIdx.x; r < nact; r += blockDim.x) {
+        long long p = act[r];
+        T2 w = Wc[p];
+        T s = w.x, cp = w.y;
+        T ph = c.alpha * cp + c.beta;
+        if (type[p] == T_IN) {
+            T ss = ph * c.idt + c.a2mc * ph * cp;
+            T sc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s);
+            for (int q = 0; q < 2 * D; q++) {
+                long long pq = p + of.o[q];
+                T2 wq = Wc[pq];
+                T g = c.kap * ((c.alpha * wq.y + c.beta) + ph);
+                T e = c.kap * c.alpha * (s - wq.x);
+                int qc = apos[pq];
+                add(2 * r, 2 * qc, -g);
+                add(2 * r, 2 * qc + 1, e);
+                ss += g;
+                sc += e;
+            }
+            add(2 * r, 2 * r, ss);
+            add(2 * r, 2 * r + 1, sc);
+        } else {
+            int gi = gpos[p];
+            const int K = D == 2 ? 9 : 27;
+            for (int kk = 0; kk < K; kk++) {
+                const long long o = (long long)kk * tb.ng + gi;
+                T wt = tb.w[o];
+                if (wt == (T)0) continue;
+                add(2 * r, 2 * apos[tb.node[o]], wt);
+            }
+        }
+        add(2 * r + 1, 2 * r, c.a2ms * ph * cp);
+        add(2 * r + 1, 2 * r + 1, c.idt + c.a2ms * (c.alpha * s * cp + ph * s));
+    }
+    __syncthreads();
+    __shared__ int s_piv;
+    __shared__ T s_inv;
+    for (int k = 0; k < m; k++) {
+        T* fb = fac + (size_t)(k & 1) * (m + 1);
+        if (k % C == me) {
+            const int kl = k / C;
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                T bv = -1;
+                int bi = k;
+                for (int i = k + lane; i < m; i += 32) {
+                    T v = fabs(A[(size_t)i * mc + kl]);
+                    if (v > bv) {
+                        bv = v;
+                        bi = i;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    T ov = __shfl_down_sync(0xffffffffu, bv, o);
+                    int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                    if (ov > bv || (ov == bv && oi < bi)) {
+                        bv = ov;
+                        bi = oi;
+                    }
+                }
+                if (lane == 0) {
+                    s_piv = bi;
+                    // the pivot's reciprocal once (every thread dividing
+                    // would load the FP64 pipe, two lanes per SM per clock)
+                    s_inv = (T)1 / A[(size_t)bi * mc + kl];
+                    if (!(bv > (T)0)) *singular = 1;
+                }
+            }
+            __syncthreads();
+            const int pr = s_piv;
+            for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
+                const int rk = t / m, i = t % m;
+                const int src = i == k ? pr : (i == pr ? k : i);
+                T* dst = cl.map_shared_rank(fb, rk);
+                dst[i] = A[(size_t)src * mc + kl];
+                if (i == 0) {
+                    dst[m] = s_inv;
+                    cl.map_shared_rank(piv, rk)[k] = pr;
+                }
+            }
+        }
+        cl.sync();  // column k, its reciprocal pivot and the pivot row in every CTA
+        const int pr = piv[k];
+        if (pr != k)
+            for (int jl = threadIdx.x; jl < mc; jl += blockDim.x) {
+                T tmp = A[(size_t)k * mc + jl];
+                A[(size_t)k * mc + jl] = A[(size_t)pr * mc + jl];
+                A[(size_t)pr * mc + jl] = tmp;
+            }
+        __syncthreads();
+        const T inv = fb[m];
+        for (int jl = threadIdx.x; jl < mc; jl += blockDim.x) {
+            const int j = jl * C + me;
+            if (j < m) A[(size_t)k * mc + jl] = j == k ? inv : A[(size_t)k * mc + jl] * inv;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < m * mc; t += blockDim.x) {
+            const int i = t / mc, jl = t % mc;
+            const int j = jl * C + me;
+            if (i == k || j == k || j >= m) continue;
+            A[(size_t)i * mc + jl] -= fb[i] * A[(size_t)k * mc + jl];
+        }
+        __syncthreads();
+        if (k % C == me)
+            for (int i = threadIdx.x; i < m; i += blockDim.x)
+                if (i != k) A[(size_t)i * mc + k / C] = -fb[i] * inv;
+        __syncthreads();
+    }
+    // the row interchanges undone as column interchanges, last first: final
+    // column j is column idx[j] of the eliminated matrix
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < m; j++) idx[j] = j;
+        for (int k = m - 1; k >= 0; k--) {
+            const int p = piv[k], t = idx[k];
+            idx[k] = idx[p];
+            idx[p] = t;
+        }
+        for (int j = 0; j < m; j++) pos[idx[j]] = j;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * mc; t += blockDim.x) {
+        const int i = t / mc, jl = t % mc;
+        const int j = jl * C + me;
+        if (j < m) Ainv_g[(size_t)i * m + pos[j]] = A[(size_t)i * mc + jl];
+    }
 }
 
 template <typename T>
@@ -906,10 +1080,10 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
     Offs<D> of = make_offs<D>(L.st[1], L.st[2]);
     const size_t m = 2 * (size_t)L.nact;
     const size_t piv_bytes = sizeof(T) * (m + 1) + sizeof(int) * (m + 1);  // column k and the interchanges
-    const size_t smem_full = m * m * sizeof(T) + piv_bytes;
+    const size_t smem_cluster = factor_cluster_smem<T>((int)m);
     constexpr size_t kMaxSmem = 220 * 1024;
-    if (smem_full <= kMaxSmem) {
-        auto kern = k_coarsest_factor<D, T, true>;
+    if (smem_cluster <= kMaxSmem) {
+        auto kern = k_coarsest_factor_cluster<D, T>;
         // The limit is a per-function attribute shared by every thread: set it
         // once to the largest size ever used (a per-launch value would race
         // with other threads' launches of different sizes).
@@ -924,8 +1098,24 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
                 if (dev >= 0 && dev < 64) raised[dev] = true;
             }
         }
-        launch_k(kern, 1, 1024, smem_full, s, L.nact, L.act, L.apos, L.type, L.gpos, tb, V.Wc, of, L.st[1], L.st[2],
-                                        c, V.A, V.Ainv, singular);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kFacCluster);
+        cfg.blockDim = dim3(kFacThreads);
+        cfg.dynamicSmemBytes = smem_cluster;
+        cfg.stream = s;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kFacCluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = launch_pdl() ? 1 : 0;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, (int)L.nact, (const int*)L.act, (const int*)L.apos,
+                                           (const int8_t*)L.type, (const int*)L.gpos, tb,
+                                           (const typename V2<T>::t*)V.Wc, of, c, V.Ainv, singular);
+        if (e != cudaSuccess) note_launch_error(e, kFacCluster, kFacThreads, smem_cluster);
     } else {
         launch_k(k_coarsest_factor<D, T, false>, 1, 1024, piv_bytes, s, L.nact, L.act, L.apos, L.type, L.gpos, tb,
                                                                   V.Wc, of, L.st[1], L.st[2], c, V.A, V.Ainv,

@@ -276,7 +276,7 @@ int read_norms(sulf_domain* d, int n) {
 int tail_level(const sulf_domain* d) {
     // automatic threshold: the fused kernel runs on one SM, whose FP64 rate is
     // two lanes per clock, so FP64 cycles fuse only the smallest levels
-    const int fb = d->solver.fuse_below >= 0 ? d->solver.fuse_below : (d->solver.precision == 0 ? 600 : 2000);
+    const int fb = d->solver.fuse_below >= 0 ? d->solver.fuse_below : (d->solver.precision == 0 ? 600 : 1000);
     if (fb <= 0 || d->solver.cycle != 1) return -1;
     for (int l = 0; l < d->L - 1; l++)
         if ((long long)d->geo[l].nin[0] + d->geo[l].nin[1] + d->geo[l].ng <= fb) return l;
