@@ -71,7 +71,7 @@ typedef struct {
    fuse_below    the first level with at most this many active nodes and all
                  coarser ones run as one single-CTA kernel per V-cycle;
                  0 = every level as separate kernels (W-cycles always are);
-                 -1 = automatic: 600 for FP64, 1000 for mixed precision
+                 -1 = automatic: 150 for FP64, 1000 for mixed precision
                  (the fused kernel runs on one SM)                       default -1
    pdl           1 = kernels of a step are launched as programmatic dependent
                  launches (each may be scheduled while its predecessor runs and

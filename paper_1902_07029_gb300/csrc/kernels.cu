@@ -126,7 +126,7 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2<T>::t* __restrict__ Wc,
                                                typename V2<T>::t* e0, typename V2<T>::t* e1, typename V2<T>::t* e2,
                                                typename V2<T>::t* Pa, typename V2<T>::t* Pb, typename V2<T>::t* Ia,
-                                               typename V2<T>::t* Ib, typename V2<T>::t* gc, Coef<T> c) {
+                                               typename V2<T>::t* Ib, typename V2<T>::t* gc, T* gci, Coef<T> c) {
     pdl_enter();
     typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
         v.x = Pcs;
         v.y = Pcc;
         gc[gi] = v;
+        gci[gi] = (T)1 / Pcc;
     }
 }
 
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_ghost_pass(const int* __restrict__ gidx, GhostTab<T> tb,
                                                     const typename V2<T>::t* __restrict__ gc,
+                                                    const T* __restrict__ gci,
                                                     const typename V2<T>::t* __restrict__ rhs,
                                                     typename V2<T>::t* x, const T* sin, T* sout, Coef<T> c, int first,
                                                     int last) {
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kT) k_ghost_pass(const int* __restrict__ gidx,
     if (on) {
         g = gidx[gi];
         q = gc[gi];
-        qinv = (T)1 / q.y;
+        qinv = gci[gi];
         if (D == 2) stages::fetch_members<T>(tb, gi, 0, m);
     }
     pdl_enter();
@@ -252,8 +254,8 @@ template <typename T>
 __global__ void __launch_bounds__(kT) k_ghost_op(int ng, const int* __restrict__ gidx, const int* __restrict__ ptr,
                                                   const int* __restrict__ code, const T* __restrict__ val,
                                                   const typename V2<T>::t* __restrict__ gc,
-                                                  const typename V2<T>::t* rhs, typename V2<T>::t* x,
-                                                  const T* snap) {
+                                                  const T* __restrict__ gci, const typename V2<T>::t* rhs,
+                                                  typename V2<T>::t* x, const T* snap) {
     typedef typename V2<T>::t T2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int gi = t / kGopLanes, ln = t % kGopLanes;
@@ -264,6 +266,7 @@ __global__ void __launch_bounds__(kT) k_ghost_op(int ng, const int* __restrict__
     T2 q;
     q.x = 0;
     q.y = 1;
+    T qinv = 1;
     if (on) {
         beg = ptr[gi];
         end = ptr[gi + 1];
@@ -276,6 +279,7 @@ __global__ void __launch_bounds__(kT) k_ghost_op(int ng, const int* __restrict__
         if (ln == 0) {
             g = gidx[gi];
             q = gc[gi];
+            qinv = gci[gi];
         }
     }
     pdl_enter();
@@ -290,12 +294,11 @@ __global__ void __launch_bounds__(kT) k_ghost_op(int ng, const int* __restrict__
         for (int i = 0; i < kGopPre; i++) acc = stages::fmadd(w[i], v[i], acc);
         for (int j = beg + ln + kGopPre * kGopLanes; j < end; j += kGopLanes) acc = stages::fmadd(val[j], u(code[j]), acc);
     }
-#pragma unroll
-    for (int o = kGopLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    acc = stages::gop_reduce<T>(acc);
     if (!on || ln != 0) return;
     T2 r;
     r.x = acc;
-    r.y = stages::fmadd(-q.x, acc, by) * ((T)1 / q.y);
+    r.y = stages::fmadd(-q.x, acc, by) * qinv;
     x[g] = r;
 }
 
@@ -754,14 +757,13 @@ __global__ void __launch_bounds__(kFacThreads) k_coarsest_factor_cluster(
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarsest_solve(int nact, const int* __restrict__ act, const T* __restrict__ Ainv,
+__global__ void __launch_bounds__(256) k_coarsest_solve(int nact, const int* __restrict__ act, const T* __restrict__ Ainv,
                                                          const typename V2<T>::t* __restrict__ rhs,
                                                          typename V2<T>::t* __restrict__ x) {
     pdl_enter();
     typedef typename V2<T>::t T2;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* b = reinterpret_cast<T*>(smraw);
-    T* out = b + 2 * nact;
     const int m = 2 * nact;
     for (int r = threadIdx.x; r < nact; r += blockDim.x) {
         T2 v = rhs[act[r]];
@@ -769,22 +771,17 @@ __global__ void __launch_bounds__(1024) k_coarsest_solve(int nact, const int* __
         b[2 * r + 1] = v.y;
     }
     __syncthreads();
-    // one warp per row of the inverse, lanes over its columns
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = warp; r < m; r += nw) {
-        const T* row = Ainv + (long long)r * m;
-        T acc = 0;
-        for (int j = lane; j < m; j += 32) acc += row[j] * b[j];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) out[r] = acc;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < nact; r += blockDim.x) {
-        T2 v;
-        v.x = out[2 * r];
-        v.y = out[2 * r + 1];
-        x[act[r]] = v;
-    }
+    // one warp per row of the inverse, lanes over its columns; the rows are
+    // spread over several CTAs (each warp-wide FP64 instruction costs 16
+    // issue cycles of one SM)
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= m) return;
+    const T* row = Ainv + (long long)r * m;
+    T acc = 0;
+    for (int j = lane; j < m; j += 32) acc += row[j] * b[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) reinterpret_cast<T*>(x + act[r >> 1])[r & 1] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -977,7 +974,7 @@ int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cuda
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
     launch_k(k_coefs<D, T>, grid_for(tot), block_for(tot), 0, s, ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa, V.Pb, V.Ia, V.Ib,
-                                            V.gc, c);
+                                            V.gc, V.gci, c);
     return 1;
 }
 
@@ -1007,7 +1004,7 @@ int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
         const long long nt = (long long)L.ng * kGopLanes;
         const T* val = std::is_same<T, float>::value ? (const T*)L.gop_val32 : (const T*)L.gop_val;
         launch_k(k_ghost_op<T>, grid_for(nt), block_for(nt), 0, s, L.ng, L.gidx, L.gop_ptr, L.gop_code, val, V.gc,
-                 V.rhs, V.x, V.gbuf[0]);
+                 V.gci, V.rhs, V.x, V.gbuf[0]);
         return 1;
     }
     int n = 0;
@@ -1015,7 +1012,7 @@ int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
         bool first = p == 0, last = p == passes - 1 && passes > 1;
         const T* sin = first ? nullptr : V.gbuf[(p - 1) & 1];
         T* sout = V.gbuf[p & 1];
-        launch_k(k_ghost_pass<D, T>, grid_for(L.ng), block_for(L.ng), 0, s, L.gidx, stages::ghost_tab<T>(L), V.gc,
+        launch_k(k_ghost_pass<D, T>, grid_for(L.ng), block_for(L.ng), 0, s, L.gidx, stages::ghost_tab<T>(L), V.gc, V.gci,
                  V.rhs, V.x, sin, sout, c, first, last);
         n++;
     }
@@ -1126,8 +1123,10 @@ int launch_coarsest_factor(const LevelGeo& L, const LevelVec<T>& V, const Coef<T
 
 template <int D, typename T>
 int launch_coarsest_solve(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s) {
-    size_t shm = sizeof(T) * (4 * (size_t)L.nact + 2);
-    launch_k(k_coarsest_solve<T>, 1, 1024, shm, s, L.nact, L.act, V.Ainv, V.rhs, V.x);
+    size_t shm = sizeof(T) * (2 * (size_t)L.nact + 2);
+    const int m = 2 * L.nact, rows_per_cta = 8;
+    launch_k(k_coarsest_solve<T>, (m + rows_per_cta - 1) / rows_per_cta, 32 * rows_per_cta, shm, s, L.nact, L.act,
+             V.Ainv, V.rhs, V.x);
     return 1;
 }
 

@@ -264,17 +264,16 @@ __device__ __forceinline__ void ghost_pass_apply(int gi, long long g, const Ghos
 
 template <int D, typename T, bool CG>
 __device__ __forceinline__ void ghost_pass_node(int gi, const int* gidx, const GhostTab<T>& tb,
-                                                const typename V2<T>::t* gc, const typename V2<T>::t* rhs,
-                                                typename V2<T>::t* x, const T* sin, T* sout, T tau, bool first,
-                                                bool last) {
+                                                const typename V2<T>::t* gc, const T* gci,
+                                                const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* sin,
+                                                T* sout, T tau, bool first, bool last) {
     Members<T> m;
     const Members<T>* pre = nullptr;
     if (D == 2) {
         fetch_members<T>(tb, gi, 0, m);
         pre = &m;
     }
-    typename V2<T>::t q = gc[gi];
-    ghost_pass_apply<D, T, CG>(gi, gidx[gi], tb, pre, q, (T)1 / q.y, rhs, x, sin, sout, tau, first, last);
+    ghost_pass_apply<D, T, CG>(gi, gidx[gi], tb, pre, gc[gi], gci[gi], rhs, x, sin, sout, tau, first, last);
 }
 
 // The composed ghost relaxation (all passes of a sweep as one affine map per
@@ -292,34 +291,39 @@ __device__ __forceinline__ T gop_input(int code, const typename V2<T>::t* x, con
     return (u & 1u) ? reinterpret_cast<const T*>(rhs + (u >> 1))[0] : snap[u >> 1];
 }
 
-// lane k of kGopLanes sums the entries beg + k, beg + k + kGopLanes, ... (one
-// FMA chain each); the lane sums are combined pairwise, lane 0 with lane 4,
-// then 2, then 1: the order of the per-level kernel's shuffle reduction, so
-// both give the same bits
+// The lanes of a group of kGopLanes (aligned within a warp) share one row:
+// lane k sums the entries beg + k, beg + k + kGopLanes, ... (one FMA chain
+// from zero), then the lane sums are combined by xor shuffles (lane 0 with 4,
+// then 2, then 1).  Every lane of the warp must call it.
 template <typename T>
-__device__ __forceinline__ T gop_lane_tree(const T (&p)[kGopLanes]) {
-    return ((p[0] + p[4]) + (p[2] + p[6])) + ((p[1] + p[5]) + (p[3] + p[7]));
+__device__ __forceinline__ T gop_reduce(T acc) {
+#pragma unroll
+    for (int o = kGopLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
 }
 
-// the whole row in one thread, then the ghost's c row with the new s_g (as in
-// ghost_pass_apply)
+// the row of ghost gi by the kGopLanes lanes of its group (lane ln; on:
+// whether the group has a row), then lane 0 solves the ghost's c row with the
+// new s_g (as in ghost_pass_apply); every lane of the warp must call it
+// the row of ghost gi by the kGopLanes lanes of its group (lane ln; on:
+// whether the group has a row), then lane 0 solves the ghost's c row with the
+// new s_g (as in ghost_pass_apply; gci = 1 / J^cc_gg); every lane of the warp
+// must call it
 template <typename T>
-__device__ __forceinline__ void gop_node(int gi, long long g, const int* ptr, const int* code, const T* val,
-                                         typename V2<T>::t q, const typename V2<T>::t* rhs, typename V2<T>::t* x,
-                                         const T* snap) {
-    const int beg = ptr[gi], end = ptr[gi + 1];
-    T p[kGopLanes];
-#pragma unroll
-    for (int k = 0; k < kGopLanes; k++) {
-        T a = 0;
-        for (int j = beg + k; j < end; j += kGopLanes) a = fmadd(val[j], gop_input<T>(code[j], x, rhs, snap), a);
-        p[k] = a;
-    }
-    const T sg = gop_lane_tree<T>(p);
-    const T by = reinterpret_cast<const T*>(rhs + g)[1];
+__device__ __forceinline__ void gop_group(bool on, int ln, int gi, const int* ptr, const int* code, const T* val,
+                                          const int* gidx, const typename V2<T>::t* gc, const T* gci,
+                                          const typename V2<T>::t* rhs, typename V2<T>::t* x, const T* snap) {
+    T acc = 0;
+    if (on)
+        for (int j = ptr[gi] + ln; j < ptr[gi + 1]; j += kGopLanes)
+            acc = fmadd(val[j], gop_input<T>(code[j], x, rhs, snap), acc);
+    acc = gop_reduce<T>(acc);
+    if (!on || ln != 0) return;
+    const long long g = gidx[gi];
+    const typename V2<T>::t q = gc[gi];
     typename V2<T>::t r;
-    r.x = sg;
-    r.y = fmadd(-q.x, sg, by) * ((T)1 / q.y);
+    r.x = acc;
+    r.y = fmadd(-q.x, acc, reinterpret_cast<const T*>(rhs + g)[1]) * gci[gi];
     x[g] = r;
 }
 

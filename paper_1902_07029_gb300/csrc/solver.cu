@@ -228,7 +228,8 @@ int alloc_vectors(sulf_domain* d, LevelVec<T>* V, bool share_state) {
         v.Ia = (T2*)d->mem.get(nb2);
         v.Ib = (T2*)d->mem.get(nb2);
         v.gc = (T2*)d->mem.get(sizeof(T2) * (G.ng + 1));
-        if (!v.Pa || !v.Pb || !v.Ia || !v.Ib || !v.gc || !v.edge[0] || !v.edge[1] || (G.dim == 3 && !v.edge[2]))
+        v.gci = (T*)d->mem.get(sizeof(T) * (G.ng + 1));
+        if (!v.Pa || !v.Pb || !v.Ia || !v.Ib || !v.gc || !v.gci || !v.edge[0] || !v.edge[1] || (G.dim == 3 && !v.edge[2]))
             return sulf_fail(SULF_ENOMEM, "out of device memory");
         if ((!share_state || l > 0) && !v.Wc) return sulf_fail(SULF_ENOMEM, "out of device memory");
         if (!v.rhs || !v.x || !v.res || !v.gbuf[0] || !v.gbuf[1])
@@ -276,7 +277,7 @@ int read_norms(sulf_domain* d, int n) {
 int tail_level(const sulf_domain* d) {
     // automatic threshold: the fused kernel runs on one SM, whose FP64 rate is
     // two lanes per clock, so FP64 cycles fuse only the smallest levels
-    const int fb = d->solver.fuse_below >= 0 ? d->solver.fuse_below : (d->solver.precision == 0 ? 600 : 1000);
+    const int fb = d->solver.fuse_below >= 0 ? d->solver.fuse_below : (d->solver.precision == 0 ? 150 : 1000);
     if (fb <= 0 || d->solver.cycle != 1) return -1;
     for (int l = 0; l < d->L - 1; l++)
         if ((long long)d->geo[l].nin[0] + d->geo[l].nin[1] + d->geo[l].ng <= fb) return l;
@@ -383,7 +384,7 @@ struct MG {
                 compose = G.ng == 0 || (G.gop_bc == d->bc &&
                                         ghost_op_ready<T>(G, make_coef<T>(d, k).tau, d->solver.ghost_sweeps));
             }
-            rc = launch_tail<D, T>(d->tail_desc[p], l, d->L, d->solver, d->bc, compose, d->stream);
+            rc = launch_tail<D, T>(d->tail_desc[p], d->geo, l, d->L, d->solver, d->bc, compose, d->stream);
             if (rc) return rc;
             d->launches += 1;
             return SULF_OK;

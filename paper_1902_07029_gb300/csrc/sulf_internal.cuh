@@ -121,6 +121,9 @@ struct LevelVec {
     T2* Ia = nullptr;  //               rows of the inverse of that 2x2 block
     T2* Ib = nullptr;
     T2* gc = nullptr;  // per ghost: (J^cs_gg, J^cc_gg)
+    T* gci = nullptr;  // per ghost: 1 / J^cc_gg (an FP64 division costs ~10 instructions
+                       // of a pipe with two lanes per SM per clock: divided once per
+                       // Newton iteration instead of at every use)
 };
 
 // Jacobian coefficients of a level (Sec. 3.4, exact derivative of F).
@@ -242,7 +245,8 @@ int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, 
 // (the descriptor's pointers are those of the maps built for the current
 // solver controls and boundary condition)
 template <int D, typename T>
-int launch_tail(const void* dev_desc, int l0, int L, const sulf_solver& sv, int bc, bool compose, cudaStream_t s);
+int launch_tail(const void* dev_desc, const LevelGeo* G, int l0, int L, const sulf_solver& sv, int bc, bool compose,
+                cudaStream_t s);
 
 // factor of tau_s for Neumann ghost rows on a level of spacing h (Eq.
 // CFLcondN): 4 h / (3 sqrt(dim)), i.e. 2 sqrt(2) h / 3 in 2-D
