@@ -103,6 +103,11 @@ typedef struct {
     long long n_inside, n_ghost; /* finest-level inside and ghost nodes (Eq. ghostdef) */
     int ghost_rows[3];      /* finest-level ghost rows: quadratic, linear, identity */
     unsigned long long device_bytes; /* device memory the handle holds */
+    int loop_graph;         /* 1: the last linear solve ran its cycles as one graph
+                               launch (a conditional while node with the
+                               convergence test on the device); 0: one launch and
+                               host test per cycle (graphs off, profiling on, or the
+                               runtime refused the conditional node) */
 } sulf_stats;
 
 /* Build a domain.  levelset: host array of (N+1)^dim node values of phi

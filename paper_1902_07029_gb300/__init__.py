@@ -36,7 +36,7 @@ class SulfStats(ctypes.Structure):
                 ("steps_total", ctypes.c_longlong), ("last_rho", ctypes.c_double), ("last_fnorm", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("levels", ctypes.c_int), ("n_inside", ctypes.c_longlong),
                 ("n_ghost", ctypes.c_longlong), ("ghost_rows", ctypes.c_int * 3),
-                ("device_bytes", ctypes.c_ulonglong)]
+                ("device_bytes", ctypes.c_ulonglong), ("loop_graph", ctypes.c_int)]
 
 
 class SulfJob(ctypes.Structure):

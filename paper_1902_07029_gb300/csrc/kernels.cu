@@ -1174,6 +1174,29 @@ int launch_to_float(const LevelGeo& L, const double2* src, float2* dst, cudaStre
     return 1;
 }
 
+// End of one cycle of the device-side linear-solve loop: counts the cycle,
+// records its defect norm and sets the enclosing conditional node to run
+// another cycle unless the defect met the threshold, is not a number, the
+// coarsest Jacobian was singular or the cycle cap is reached.
+__global__ void k_cycle_check(cudaGraphConditionalHandle h, const unsigned long long* __restrict__ norm,
+                              const int* __restrict__ singular, const double* __restrict__ thr, int max_cycles,
+                              int* cycles, double* rnorms) {
+    pdl_enter();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int c = *cycles + 1;
+    *cycles = c;
+    const double rn = __longlong_as_double((long long)norm[0]);
+    rnorms[c - 1] = rn;
+    const bool more = *singular == 0 && rn == rn && rn > *thr && c < max_cycles;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+int launch_cycle_check(cudaGraphConditionalHandle h, const unsigned long long* norm, const int* singular,
+                       const double* thr, int max_cycles, int* cycles, double* rnorms, cudaStream_t s) {
+    launch_k(k_cycle_check, 1, 32, 0, s, h, norm, singular, thr, max_cycles, cycles, rnorms);
+    return 1;
+}
+
 int launch_accumulate(const LevelGeo& L, double2* x, const float2* e, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;

@@ -120,6 +120,23 @@ struct sulf_domain {
         size_t ev0 = 0, ev1 = 0;
     } graph[2];
     bool capturing = false;
+    // The linear solve as one graph launch, per precision: a conditional
+    // while node whose body is one cycle and its convergence test on the
+    // device (no host round trip per cycle).  Rebuilt when anything baked
+    // into it changes; off for good on this handle if the runtime refuses it.
+    struct LoopGraph {
+        cudaGraphExec_t exec = nullptr;
+        double dt = 0;
+        sulf_solver sv{};
+        int max_cycles = 0;
+        long long kernels = 0;  // per cycle
+    } loop[2];
+    bool loop_off = false;
+    bool loop_used = false;  // the last linear solve ran as one loop-graph launch
+    int* dcyc = nullptr;      // cycles run by the device loop
+    double* drn = nullptr;    // their defect norms (kLoopMaxCycles)
+    double* dthr = nullptr;   // threshold rtol * |F|
+    double* hloop = nullptr;  // pinned: threshold, cycle count, norms
     // fused coarsest levels: device descriptors per precision
     void* tail_desc[2] = {nullptr, nullptr};
     bool tail_ready[2] = {false, false};
@@ -307,6 +324,11 @@ void drop_graphs(sulf_domain* d) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
         }
+    for (auto& g : d->loop)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
 }
 
 // (re)build the composed ghost relaxation of every level whose map was built
@@ -428,12 +450,20 @@ int accumulate_prof(sulf_domain* d, size_t from, size_t to) {
     return SULF_OK;
 }
 
+bool same_solver(const sulf_solver& a, const sulf_solver& b) {
+    return a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.cycle == b.cycle && a.max_newton == b.max_newton &&
+           a.max_cycles == b.max_cycles && a.ghost_sweeps == b.ghost_sweeps && a.newton_tol == b.newton_tol &&
+           a.lin_rtol == b.lin_rtol && a.tau_s == b.tau_s && a.precision == b.precision && a.smoother == b.smoother &&
+           a.graphs == b.graphs && a.fuse_below == b.fuse_below && a.pdl == b.pdl &&
+           a.ghost_compose == b.ghost_compose;
+}
+
 // One cycle of the linear solve on the finest level, then the FP64 defect
 // r = F - J dW, its max-norm and the coarsest-level singularity flag copied to
 // pinned host memory.  FP64: a multigrid cycle on J dW = F.  Mixed: an FP32
 // cycle on J e = r from e = 0, dW += e, then the next FP32 right-hand side.
 template <int D>
-int cycle_body(sulf_domain* d) {
+int cycle_body(sulf_domain* d, const cudaGraphConditionalHandle* loop = nullptr, int max_cycles = 0) {
     const LevelGeo& G0 = d->geo[0];
     LevelVec<double>& V0 = d->v64[0];
     if (d->solver.precision == 0) {
@@ -452,19 +482,121 @@ int cycle_body(sulf_domain* d) {
     }
     SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
     d->launches += launch_residual<D, double>(G0, V0, make_coef<double>(d, 0), d->dnorm, d->stream);
-    SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, d->stream));
-    SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    if (!loop) {
+        SULF_CUDA_TRY(
+            cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, d->stream));
+        SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    }
     if (d->solver.precision == 1) d->launches += launch_to_float(G0, V0.res, d->v32[0].rhs, d->stream);
+    if (loop) d->launches += launch_cycle_check(*loop, d->dnorm, d->dsing, d->dthr, max_cycles, d->dcyc, d->drn, d->stream);
     return SULF_OK;
 }
 
-bool same_solver(const sulf_solver& a, const sulf_solver& b) {
-    return a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.cycle == b.cycle && a.max_newton == b.max_newton &&
-           a.max_cycles == b.max_cycles && a.ghost_sweeps == b.ghost_sweeps && a.newton_tol == b.newton_tol &&
-           a.lin_rtol == b.lin_rtol && a.tau_s == b.tau_s && a.precision == b.precision && a.smoother == b.smoother &&
-           a.graphs == b.graphs && a.fuse_below == b.fuse_below && a.pdl == b.pdl &&
-           a.ghost_compose == b.ghost_compose;
+constexpr int kLoopMaxCycles = 256;
+
+// build the device-side loop graph of precision p: [cycle counter := 0] ->
+// while (condition) { cycle; test }.  Returns false (and turns the loop off
+// for this handle) where the runtime does not take it.
+template <int D>
+bool build_loop(sulf_domain* d, int max_cycles) {
+    const int p = d->solver.precision;
+    sulf_domain::LoopGraph& g = d->loop[p];
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    if (!d->dcyc) {
+        d->dcyc = (int*)d->mem.get(sizeof(int) * 4);
+        d->drn = (double*)d->mem.get(sizeof(double) * kLoopMaxCycles);
+        d->dthr = (double*)d->mem.get(sizeof(double) * 2);
+        if (!d->dcyc || !d->drn || !d->dthr) return false;
+    }
+    if (!d->hloop && cudaMallocHost(&d->hloop, sizeof(double) * (4 + kLoopMaxCycles)) != cudaSuccess) {
+        d->hloop = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t outer = nullptr;
+    if (cudaGraphCreate(&outer, 0) != cudaSuccess) return false;
+    bool ok = false;
+    do {
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, outer, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+        cudaMemsetParams mp = {};
+        mp.dst = d->dcyc;
+        mp.value = 0;
+        mp.elementSize = sizeof(int);
+        mp.width = 1;
+        mp.height = 1;
+        cudaGraphNode_t zero;
+        if (cudaGraphAddMemsetNode(&zero, outer, nullptr, 0, &mp) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        if (cudaGraphAddNode(&cn, outer, &zero, nullptr, 1, &cp) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(d->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess)
+            break;
+        d->capturing = true;
+        const long long l0 = d->launches;
+        int rc = cycle_body<D>(d, &h, max_cycles);
+        cudaGraph_t got = nullptr;
+        cudaError_t e = cudaStreamEndCapture(d->stream, &got);
+        d->capturing = false;
+        g.kernels = d->launches - l0;
+        d->launches = l0;
+        if (rc || e != cudaSuccess) break;
+        if (cudaGraphInstantiate(&g.exec, outer, 0) != cudaSuccess) {
+            g.exec = nullptr;
+            break;
+        }
+        ok = true;
+    } while (false);
+    cudaGraphDestroy(outer);
+    if (!ok) {
+        cudaGetLastError();
+        take_launch_error();
+        g_err.clear();
+        d->loop_off = true;
+        return false;
+    }
+    g.dt = d->dt;
+    g.sv = d->solver;
+    g.max_cycles = max_cycles;
+    return true;
 }
+
+// The cycles of one linear solve as one launch of the loop graph; same
+// results and statistics as the host loop.  Returns the number of cycles, 0
+// where the loop is unavailable (the caller runs the host loop), or a
+// negative error.
+template <int D>
+int device_loop(sulf_domain* d, double fnorm, int max_cycles, double rtol, double* rnorms) {
+    if (d->loop_off || !d->solver.graphs || d->prof || max_cycles > kLoopMaxCycles) return 0;
+    const int p = d->solver.precision;
+    sulf_domain::LoopGraph& g = d->loop[p];
+    if (!g.exec || g.dt != d->dt || !same_solver(g.sv, d->solver) || g.max_cycles != max_cycles)
+        if (!build_loop<D>(d, max_cycles)) return 0;
+    d->hloop[0] = rtol * fnorm;
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->dthr, d->hloop, sizeof(double), cudaMemcpyHostToDevice, d->stream));
+    SULF_CUDA_TRY(cudaGraphLaunch(g.exec, d->stream));
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->hloop + 1, d->dcyc, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->hloop + 4, d->drn, sizeof(double) * max_cycles, cudaMemcpyDeviceToHost,
+                                  d->stream));
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+    const int c = *(int*)(d->hloop + 1);
+    d->launches += g.kernels * c;
+    if (*(int*)(d->hnorm + 6)) return sulf_fail(SULF_ENOTCONV, "singular coarsest-level Jacobian");
+    const double* rn = d->hloop + 4;
+    for (int k = 0; k < c && rnorms; k++) rnorms[k] = rn[k];
+    const double prev = c >= 2 ? rn[c - 2] : fnorm;
+    d->last_rho = prev > 0 ? rn[c - 1] / prev : 0.0;
+    return c;
+}
+
 
 // launches of the calling thread use programmatic dependent launch while the
 // scope lives
@@ -550,6 +682,9 @@ int linear_solve(sulf_domain* d, double fnorm, int max_cycles, double rtol, doub
         d->launches += launch_to_float(G0, d->v64[0].rhs, d->v32[0].rhs, d->stream);
     }
     if (rc) return rc;
+    int c = device_loop<D>(d, fnorm, max_cycles, rtol, rnorms);
+    d->loop_used = c > 0;
+    if (c) return c;
     double rprev = fnorm;
     int cyc;
     for (cyc = 1; cyc <= max_cycles; cyc++) {
@@ -649,6 +784,9 @@ void sulf_destroy(sulf_handle h) {
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     h->mem.release();
     if (h->hnorm) cudaFreeHost(h->hnorm);
+    if (h->hloop) cudaFreeHost(h->hloop);
+    for (auto& g : h->loop)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -921,6 +1059,7 @@ int sulf_get_stats(sulf_handle h, sulf_stats* o) {
     o->n_ghost = h->geo[0].ng;
     for (int k = 0; k < 3; k++) o->ghost_rows[k] = h->geo[0].kinds[k];
     o->device_bytes = h->mem.bytes;
+    o->loop_graph = h->loop_used ? 1 : 0;
     return SULF_OK;
 }
 

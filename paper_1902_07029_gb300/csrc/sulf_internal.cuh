@@ -228,6 +228,12 @@ int launch_extrapolate(const LevelGeo& L, double* u, double* q, double* q2, doub
 // CN average of manufactured source terms: src = ((f1o+f1n)/2, (f2o+f2n)/2)
 int launch_average_sources(long long nn, const double* f4, double2* src, cudaStream_t s);
 
+// the convergence test at the end of a cycle of the device-side loop
+// (conditional graph node h): cycles counts, rnorms[cycle-1] records the
+// defect norm
+int launch_cycle_check(cudaGraphConditionalHandle h, const unsigned long long* norm, const int* singular,
+                       const double* thr, int max_cycles, int* cycles, double* rnorms, cudaStream_t s);
+
 // mixed precision transfers on the finest level (active nodes)
 int launch_to_float(const LevelGeo& L, const double2* src, float2* dst, cudaStream_t s);
 int launch_accumulate(const LevelGeo& L, double2* x, const float2* e, cudaStream_t s);

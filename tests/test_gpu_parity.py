@@ -175,6 +175,29 @@ def test_steps_unfused_and_w_cycle(sulfmg, oracle_mod, name, mk):
         _close(c[act], rc[act], RUN_TOL)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_device_cycle_loop_is_bitwise_neutral(sulfmg, precision):
+    """the cycles of a linear solve run as one graph launch (a conditional
+    while node, convergence tested on the device) compute exactly what one
+    launch and host test per cycle compute, with the same cycle counts"""
+    phi, dim, N, cN, dt, nsteps = RUNS[2][1]()
+    out, stats = [], []
+    for prof in (0, 1):  # profiling events force the per-cycle host loop
+        dom = sulfmg.Domain(phi, dim, (-1.0, 1.0), N, coarsest_N=cN)
+        dom.set_model(workloads.PAPER_MODEL)
+        dom.set_solver(precision=precision)
+        dom.set_profiling(prof)
+        dom.step(dt, nsteps)
+        out.append(dom.get_state()[:2])
+        stats.append(dom.stats())
+        dom.close()
+    assert stats[0]["loop_graph"] == 1 and stats[1]["loop_graph"] == 0
+    assert stats[0]["cycles_total"] == stats[1]["cycles_total"]
+    assert stats[0]["newton_total"] == stats[1]["newton_total"]
+    assert abs(stats[0]["last_rho"] - stats[1]["last_rho"]) <= 1e-12
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 @pytest.mark.parametrize("name,mk", RUNS[:3], ids=[r[0] for r in RUNS[:3]])
 def test_steps_mixed(sulfmg, oracle_mod, name, mk):
     phi, dim, N, cN, dt, nsteps = mk()
