@@ -336,8 +336,8 @@ def run_gpu(args):
                     "avg_launch_us": avg_us, "launches": relax_n,
                     "algorithmic": f"{RELAX_BYTES[dim][args.precision]} B and {RELAX_FLOPS[dim]} flop per "
                                    f"inside-node update; {nodes_per_launch:.0f} nodes per launch",
-                    "sample": "the two colour launches of the first finest-level sweep of every cycle of the last "
-                              "timed step",
+                    "sample": "one event bracket around the two back-to-back colour launches of the first "
+                              "finest-level sweep of every cycle of the last timed step",
                     "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); the finest level's working "
                                  "set is partly L2-resident, so the fraction can exceed what HBM alone allows"}
         if prec == 1:

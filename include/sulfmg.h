@@ -212,10 +212,14 @@ int sulf_get_stats(sulf_handle h, sulf_stats* out);
 
 /* Kernel timing for measurement: the library brackets launches of the
    finest-level inside relaxation (the dominant kernel) with CUDA events on its
-   stream.  on = 0 off; 1 the two colour launches of the first finest-level
-   sweep of every cycle (a sample that keeps the event overhead small); 2 every
-   finest-level launch.  sulf_kernel_time returns the summed device time in ms
-   and the number of bracketed launches since the last reset (synchronises). */
+   stream, one bracket around the two back-to-back colour launches of a sweep
+   (between them the second launch's fetch of fixed data overlaps the first,
+   as in the untimed pipeline).  on = 0 off; 1 the first finest-level sweep of
+   every cycle (a sample that keeps the event overhead small); 2 every
+   finest-level sweep.  While on, the cycles run one graph launch each (event
+   nodes cannot sit in the device-side cycle loop).  sulf_kernel_time returns
+   the summed device time in ms and the number of launches inside the
+   brackets since the last reset (synchronises). */
 int sulf_set_profiling(sulf_handle h, int on);
 int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
 

@@ -358,20 +358,29 @@ __global__ void k_extend(int nb, const int* __restrict__ eptr, const int* __rest
 // inside rule at coarse inside nodes, outside rule (ghost or band) at coarse
 // ghosts; per-axis mirrored weights, invalid diagonal weight moved to the
 // centre.  Also zeroes the coarse error at the coarse active nodes.
-
-template <int D, typename T>
+// first_red: the coarse level's first relaxation starts from this zero
+// error, and its red half-sweep (which then reads only zeros) is done here
+// for the red inside nodes (list positions below ls.n0)
+template <int D, typename T, bool PW>
 __global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restrict__ ctype, int cn,
                                                   const int8_t* __restrict__ ftype, int fn,
                                                   const typename V2<T>::t* __restrict__ fres,
                                                   typename V2<T>::t* __restrict__ crhs,
-                                                  typename V2<T>::t* __restrict__ cx) {
+                                                  typename V2<T>::t* __restrict__ cx, CoefPtr<D, T> ccf,
+                                                  int first_red) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool on = t < ls.n0 + ls.n1 + ls.ng;
+    const bool red = on && first_red && t < ls.n0;
     stages::RestrictGeo<D, T> g;
+    stages::InsideCoef<D, T> k;
     if (on) g = stages::fetch_restrict<D, T>(t, ls, ctype, cn, ftype, fn);  // fixed geometry, fetched ahead
+    if (red) {
+        const long long cst[3] = {1, cn, (long long)cn * cn};
+        k = stages::fetch_inside<D, T, PW>(g.I, ccf, cst);  // fixed coefficients, fetched ahead
+    }
     pdl_enter();
     if (!on) return;
-    stages::restrict_apply<D, T, false>(g, fn, fres, crhs, cx);
+    stages::restrict_apply<D, T, false, PW>(g, fn, fres, crhs, cx, red ? &k : nullptr);
 }
 
 // (bi/tri)linear interpolation of the coarse error to every fine active node,
@@ -1045,10 +1054,16 @@ int launch_extend(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s) {
 
 template <int D, typename T>
 int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
-                    cudaStream_t s) {
+                    bool first_red, bool pointwise, cudaStream_t s) {
     Lists ls = make_lists(C);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_restrict<D, T>, grid_for(tot), block_for(tot), 0, s, ls, C.type, C.n, F.type, F.n, FV.res, CV.rhs, CV.x);
+    CoefPtr<D, T> ccf = coef_ptr<D, T>(CV);
+    if (pointwise)
+        launch_k(k_restrict<D, T, true>, grid_for(tot), block_for(tot), 0, s, ls, C.type, C.n, F.type, F.n, FV.res,
+                 CV.rhs, CV.x, ccf, first_red ? 1 : 0);
+    else
+        launch_k(k_restrict<D, T, false>, grid_for(tot), block_for(tot), 0, s, ls, C.type, C.n, F.type, F.n, FV.res,
+                 CV.rhs, CV.x, ccf, first_red ? 1 : 0);
     return 1;
 }
 
@@ -1229,7 +1244,7 @@ int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double*
                                        cudaStream_t);                                                            \
     template int launch_extend<D, T>(const LevelGeo&, const LevelVec<T>&, cudaStream_t);                         \
     template int launch_restrict<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&, \
-                                       cudaStream_t);                                                            \
+                                       bool, bool, cudaStream_t);                                                \
     template int launch_prolong<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&,  \
                                       cudaStream_t);                                                             \
     template int launch_inject<D, T>(const LevelGeo&, const LevelVec<T>&, const LevelGeo&, const LevelVec<T>&,   \

@@ -154,6 +154,31 @@ __device__ __forceinline__ void relax_apply(long long p, const InsideCoef<D, T>&
     x[p] = out;
 }
 
+// relax_value when every x is zero (the coarse-grid error right after
+// restriction): the same operations with zero operands, so the same bits
+template <int D, typename T, bool PW>
+__device__ __forceinline__ typename V2<T>::t relax_value_zero(typename V2<T>::t b, const InsideCoef<D, T>& k) {
+    typedef typename V2<T>::t T2;
+    const T z = 0;
+    T r = b.x;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        r = fmadd(k.ge[a].x, z, r);
+        r = fmadd(-k.ge[a].y, z, r);
+        r = fmadd(k.gw[a].x, z, r);
+        r = fmadd(k.gw[a].y, z, r);
+    }
+    T2 out;
+    if (PW) {
+        out.x = fmadd(-k.m0.y, z, r) / k.m0.x;
+        out.y = fmadd(-k.m1.x, z, b.y) / k.m1.y;
+    } else {
+        out.x = fmadd(k.m0.x, r, k.m0.y * b.y);
+        out.y = fmadd(k.m1.x, r, k.m1.y * b.y);
+    }
+    return out;
+}
+
 template <int D, typename T, bool PW, bool CG>
 __device__ __forceinline__ void relax_node(long long p, const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
                                            typename V2<T>::t* x, const long long* st) {
@@ -523,10 +548,13 @@ __device__ __forceinline__ RestrictGeo<D, T> fetch_restrict(int t, const Lists& 
     return g;
 }
 
-// the weighting applied to the fine defect; also zeroes the coarse error
-template <int D, typename T, bool CG>
+// the weighting applied to the fine defect; also zeroes the coarse error,
+// or, for a red inside node whose coefficients red holds, sets it to the
+// first red relaxation from zero (relax_value_zero)
+template <int D, typename T, bool CG, bool PW = false>
 __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int fn, const typename V2<T>::t* fres,
-                                               typename V2<T>::t* crhs, typename V2<T>::t* cx) {
+                                               typename V2<T>::t* crhs, typename V2<T>::t* cx,
+                                               const InsideCoef<D, T>* red = nullptr) {
     typedef typename V2<T>::t T2;
     const long long fst[3] = {1, fn, (long long)fn * fn};
     const int K = D == 2 ? 9 : 27;
@@ -568,7 +596,7 @@ __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int f
     T2 z;
     z.x = 0;
     z.y = 0;
-    cx[g.I] = z;  // the coarse-grid error starts from zero
+    cx[g.I] = red ? relax_value_zero<D, T, PW>(out, *red) : z;  // the coarse-grid error starts from zero
 }
 
 template <int D, typename T, bool CG>

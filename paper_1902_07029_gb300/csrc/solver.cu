@@ -360,7 +360,8 @@ struct MG {
     LevelVec<T>* V;
     int fine_sweeps = 0;  // finest-level sweeps issued so far in this cycle
 
-    int relax(int l) {
+    // skip_red: the red half-sweep was done by the restriction (from zero)
+    int relax(int l, bool skip_red = false) {
         const LevelGeo& G = d->geo[l];
         Coef<T> c = make_coef<T>(d, l);
         bool pw = d->solver.smoother == 1;
@@ -370,28 +371,22 @@ struct MG {
         // taken by the second colour's launch
         const bool gop =
             d->solver.ghost_compose && G.gop_bc == d->bc && ghost_op_ready<T>(G, c.tau, d->solver.ghost_sweeps);
-        for (int colour = 0; colour < 2; colour++) {
-            bool timed = timed_sweep;
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            // inside stream capture a plain record only adds a dependency; the
-            // external flag makes it an event-record node of the graph
-            unsigned fl = d->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-            if (timed) {
-                e0 = next_event(d);
-                cudaEventRecordWithFlags(e0, d->stream, fl);
-            }
+        // one event bracket around the two colour launches of a timed sweep
+        // (inside stream capture a plain record only adds a dependency; the
+        // external flag makes it an event-record node of the graph)
+        const unsigned fl = d->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (timed_sweep) cudaEventRecordWithFlags(next_event(d), d->stream, fl);
+        for (int colour = skip_red ? 1 : 0; colour < 2; colour++)
             d->launches += launch_relax_inside<D, T>(G, V[l], c, colour, pw,
                                                      gop && colour == 1 ? V[l].gbuf[0] : nullptr, d->stream);
-            if (timed) {
-                e1 = next_event(d);
-                cudaEventRecordWithFlags(e1, d->stream, fl);
-            }
-        }
+        if (timed_sweep) cudaEventRecordWithFlags(next_event(d), d->stream, fl);
         d->launches += launch_relax_ghosts<D, T>(G, V[l], c, d->solver.ghost_sweeps, gop, d->stream);
         return SULF_OK;
     }
 
-    int cycle(int l) {
+    // red_done: level l's error was just restricted to zero and its first
+    // red half-sweep done with it
+    int cycle(int l, bool red_done = false) {
         if (l == d->L - 1) {
             d->launches += launch_coarsest_solve<D, T>(d->geo[l], V[l], d->stream);
             return SULF_OK;
@@ -412,13 +407,20 @@ struct MG {
             return SULF_OK;
         }
         for (int k = 0; k < d->solver.nu1; k++)
-            if ((rc = relax(l))) return rc;
+            if ((rc = relax(l, red_done && k == 0))) return rc;
         d->launches += launch_residual<D, T>(d->geo[l], V[l], make_coef<T>(d, l), nullptr, d->stream);
         d->launches += launch_extend<D, T>(d->geo[l], V[l], d->stream);
-        d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
+        // the next level starts from a zero error: where it runs as separate
+        // kernels and pre-relaxes, the restriction also does its first red
+        // half-sweep (which would read only zeros)
+        const int lc = l + 1;
+        const bool fused_tail = lc == tail_level(d) && d->tail_ready[p] && d->solver.cycle == 1;
+        const bool fr = d->solver.nu1 >= 1 && lc < d->L - 1 && !fused_tail;
+        d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[lc], V[lc], fr, d->solver.smoother == 1,
+                                             d->stream);
         int gam = d->solver.cycle == 2 ? 2 : 1;
         for (int g = 0; g < gam; g++)
-            if ((rc = cycle(l + 1))) return rc;
+            if ((rc = cycle(lc, fr && g == 0))) return rc;
         d->launches += launch_prolong<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
         for (int k = 0; k < d->solver.nu2; k++)
             if ((rc = relax(l))) return rc;
@@ -445,7 +447,7 @@ int accumulate_prof(sulf_domain* d, size_t from, size_t to) {
         float e = 0;
         SULF_CUDA_TRY(cudaEventElapsedTime(&e, d->evpool[k], d->evpool[k + 1]));
         d->prof_ms += e;
-        d->prof_n++;
+        d->prof_n += 2;  // a bracket holds the two colour launches of a sweep
     }
     return SULF_OK;
 }
@@ -1227,10 +1229,10 @@ int sulf_dbg_restrict(sulf_handle h, int l, double* res, double* rhs_coarse) {
     if (rc) return rc;
     if (h->dim == 2) {
         h->launches += launch_extend<2, double>(G, h->v64[l], h->stream);
-        h->launches += launch_restrict<2, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
+        h->launches += launch_restrict<2, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], false, false, h->stream);
     } else {
         h->launches += launch_extend<3, double>(G, h->v64[l], h->stream);
-        h->launches += launch_restrict<3, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], h->stream);
+        h->launches += launch_restrict<3, double>(G, h->v64[l], h->geo[l + 1], h->v64[l + 1], false, false, h->stream);
     }
     rc = dbg_copy_out(h, l, h->v64[l].res, res, true);
     if (rc) return rc;

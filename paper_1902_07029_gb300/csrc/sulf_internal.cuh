@@ -197,9 +197,11 @@ int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, u
                     cudaStream_t s);
 template <int D, typename T>
 int launch_extend(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s);
+// first_red: also the red half of the coarse level's first relaxation from
+// the zero error, for the red inside nodes (the caller then skips that launch)
 template <int D, typename T>
 int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
-                    cudaStream_t s);
+                    bool first_red, bool pointwise, cudaStream_t s);
 template <int D, typename T>
 int launch_prolong(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C, const LevelVec<T>& CV,
                    cudaStream_t s);
