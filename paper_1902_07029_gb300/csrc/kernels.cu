@@ -679,6 +679,7 @@ __global__ void __launch_bounds__(kFacThreads) k_coarsest_factor_cluster(
         T* fb = fac + (size_t)(k & 1) * (m + 1);
         if (k % C == me) {
             const int kl = k / C;
+            __syncthreads();  // this CTA's updates of column k in the previous step
             if (threadIdx.x < 32) {
                 const int lane = threadIdx.x;
                 T bv = -1;
@@ -721,31 +722,35 @@ __global__ void __launch_bounds__(kFacThreads) k_coarsest_factor_cluster(
         }
         cl.sync();  // column k, its reciprocal pivot and the pivot row in every CTA
         const int pr = piv[k];
-        if (pr != k)
-            for (int jl = threadIdx.x; jl < mc; jl += blockDim.x) {
-                T tmp = A[(size_t)k * mc + jl];
-                A[(size_t)k * mc + jl] = A[(size_t)pr * mc + jl];
-                A[(size_t)pr * mc + jl] = tmp;
-            }
-        __syncthreads();
         const T inv = fb[m];
+        // interchange rows k and pr and scale row k, one local column per thread
         for (int jl = threadIdx.x; jl < mc; jl += blockDim.x) {
             const int j = jl * C + me;
-            if (j < m) A[(size_t)k * mc + jl] = j == k ? inv : A[(size_t)k * mc + jl] * inv;
+            if (j >= m) continue;
+            T rowk = A[(size_t)k * mc + jl];
+            if (pr != k) {
+                const T rowp = A[(size_t)pr * mc + jl];
+                A[(size_t)pr * mc + jl] = rowk;
+                rowk = rowp;
+            }
+            A[(size_t)k * mc + jl] = j == k ? inv : rowk * inv;
         }
         __syncthreads();
+        // eliminate column k from every other row; column k itself (in its
+        // owner) becomes -a_ik / a_kk
         for (int t = threadIdx.x; t < m * mc; t += blockDim.x) {
             const int i = t / mc, jl = t % mc;
             const int j = jl * C + me;
-            if (i == k || j == k || j >= m) continue;
-            A[(size_t)i * mc + jl] -= fb[i] * A[(size_t)k * mc + jl];
+            if (i == k || j >= m) continue;
+            if (j == k)
+                A[(size_t)i * mc + jl] = -fb[i] * inv;
+            else
+                A[(size_t)i * mc + jl] -= fb[i] * A[(size_t)k * mc + jl];
         }
-        __syncthreads();
-        if (k % C == me)
-            for (int i = threadIdx.x; i < m; i += blockDim.x)
-                if (i != k) A[(size_t)i * mc + k / C] = -fb[i] * inv;
-        __syncthreads();
+        // the next owner synchronises before its pivot search; every other
+        // CTA meets the others at the next cluster barrier
     }
+    __syncthreads();
     // the row interchanges undone as column interchanges, last first: final
     // column j is column idx[j] of the eliminated matrix
     if (threadIdx.x == 0) {
