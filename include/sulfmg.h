@@ -223,31 +223,35 @@ int sulf_get_stats(sulf_handle h, sulf_stats* out);
 int sulf_set_profiling(sulf_handle h, int on);
 int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
 
-/* Newton residual F(W; W^n) (Eqs. FDs, FDc, BCs) of the finest level and its
-   max-norm, computed on caller-owned DEVICE buffers without allocating any
-   device memory.  The paper has no counterpart: this entry point exists for
-   callers that cannot call cudaMalloc at that moment -- code recording a CUDA
-   graph (allocation is not allowed during stream capture) or a loop that must
-   not pay the device-wide synchronisation of an allocation.
+/* The Newton residual of sulf_step's Crank-Nicolson step on the finest level
+   and its max-norm, computed on caller-owned DEVICE buffers without
+   allocating any device memory.  The paper has no counterpart: this entry
+   point is for callers that cannot allocate device memory when they need a
+   residual -- an application whose own memory manager has already reserved
+   the device memory it may use, or a time-critical loop that must not take
+   the device-wide synchronisation of a cudaMalloc/cudaFree.
      W_dev, Wn_dev  interleaved (s, c) per node, 2*(N+1)^dim doubles: the
                     iterate and the state at t_n (values at inactive nodes are
-                    not read)
-     F_dev          output, same layout; written on active nodes only
-     fnorm_dev      output, one double: |F|_inf over the active nodes
+                    not read); 16-byte aligned
+     F_dev          output, same layout and alignment; written on active nodes
+                    only
+     fnorm_dev      output, one double (8-byte aligned): |F|_inf over the
+                    active nodes
    It evaluates the model's equations with the constant s_ext and Dirichlet
    boundary rows: the optional inputs of sulf_set_sources and
-   sulf_set_ghost_values are not applied, and after sulf_set_bc(h, 1) the call
-   returns SULF_EINVAL.
+   sulf_set_ghost_values are not applied.  SULF_EINVAL after sulf_set_bc(h, 1),
+   for a misaligned pointer, or when the current device is not the one the
+   handle was created on; no work is queued then.
    Work is queued on the handle's stream and the call returns without waiting.
    Scratch: a static array inside the library holding 65536 partial maxima
    (512 KiB), kept by every GPU that loads the library until the process exits;
    the call fails with SULF_EINVAL when the finest level has more than
-   16,777,216 active nodes.  The first call on a device looks up the array's
-   device address (cudaGetSymbolAddress), so make that first call before any
-   stream capture.  Every call shares the array, and each call overwrites the
-   slots it uses before reading them (nothing has to start at zero); calls
-   that overlap on the GPU -- on different streams at the same time -- race on
-   it. */
+   16,777,216 active nodes.  The first call on each handle looks up the
+   array's device address (cudaGetSymbolAddress) with the handle's device
+   current and keeps it in the handle; make that first call before any stream
+   capture.  Every call shares the array, and each call overwrites the slots it
+   uses before reading them (nothing has to start at zero); calls that overlap
+   on the GPU -- on different streams at the same time -- race on it. */
 int sulf_newton_residual_noalloc(sulf_handle h, double dt, const double* W_dev, const double* Wn_dev, double* F_dev,
                                  double* fnorm_dev);
 

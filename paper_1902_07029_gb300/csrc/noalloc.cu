@@ -1,13 +1,14 @@
 // Newton residual without device allocation.
 //
 // Some callers cannot allocate device memory at the moment they need a
-// residual: code that is recording a CUDA graph (cudaMalloc is not allowed
-// during stream capture), or a serving loop that must not take the device-wide
-// synchronisation a cudaMalloc/cudaFree can imply.  sulf_newton_residual_noalloc
-// lets them evaluate F(W; W^n) and |F|_inf on their own device buffers: its
-// only scratch memory -- the per-block partial maxima of a two-pass max-norm
-// reduction -- lives in the file-scope array below, which every GPU that loads
-// this library holds until the process exits.
+// residual: a host application whose own memory manager has already reserved
+// the device memory it may use (cudaMalloc would fail or break its budget),
+// or a time-critical loop that must not take the device-wide synchronisation
+// a cudaMalloc/cudaFree can imply.  sulf_newton_residual_noalloc lets them
+// evaluate F(W; W^n) and |F|_inf on their own device buffers: its only scratch
+// memory -- the per-block partial maxima of a two-pass max-norm reduction --
+// lives in the file-scope array below, which every GPU that loads this library
+// holds until the process exits.
 #include <mutex>
 
 #include "sulf_internal.cuh"
@@ -22,24 +23,28 @@ constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 65536;
 static __device__ __align__(256) unsigned long long g_partial[kMaxBlocks];
 
-constexpr int kMaxDevices = 64;
+// device address of g_partial for the handle's device, looked up on the
+// handle's first call with that device current and kept in the handle (a
+// handle lives on one device; a handle created after a device reset looks the
+// address up again)
 std::mutex g_setup_mutex;
-unsigned long long* g_partial_addr[kMaxDevices] = {nullptr};
 
-// device address of g_partial on the current device, looked up once per device
-int partial_address(unsigned long long** out) {
-    int dev = 0;
+int partial_address(sulf_handle h, unsigned long long** out) {
+    int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return sulf_fail_cuda(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return sulf_fail(SULF_EDEVICE, "device index out of range");
+    if (dev != handle_device(h))
+        return sulf_fail(SULF_EINVAL, "sulf_newton_residual_noalloc: the current CUDA device is not the one the "
+                                      "handle was created on");
+    void** slot = handle_noalloc_slot(h);
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partial_addr[dev]) {
+    if (!*slot) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_partial);
         if (e != cudaSuccess) return sulf_fail_cuda(e, "cudaGetSymbolAddress");
-        g_partial_addr[dev] = static_cast<unsigned long long*>(p);
+        *slot = p;
     }
-    *out = g_partial_addr[dev];
+    *out = static_cast<unsigned long long*>(*slot);
     return SULF_OK;
 }
 
@@ -163,6 +168,11 @@ extern "C" int sulf_newton_residual_noalloc(sulf_handle h, double dt, const doub
         return sulf_fail(SULF_EINVAL, "invalid arguments");
     if (handle_bc(h) != 0)
         return sulf_fail(SULF_EINVAL, "sulf_newton_residual_noalloc evaluates Dirichlet boundary rows only");
+    // the kernel moves each node's (s, c) pair with one 16-byte access
+    auto misaligned = [](const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; };
+    if (misaligned(W_dev, 16) || misaligned(Wn_dev, 16) || misaligned(F_dev, 16) || misaligned(fnorm_dev, 8))
+        return sulf_fail(SULF_EINVAL, "sulf_newton_residual_noalloc: W_dev, Wn_dev and F_dev must be 16-byte "
+                                      "aligned and fnorm_dev 8-byte aligned");
     long long nact = (long long)G->nin[0] + G->nin[1] + G->ng;
     long long nblocks = (nact + kThreads - 1) / kThreads;
     if (nblocks > kMaxBlocks)
@@ -170,7 +180,7 @@ extern "C" int sulf_newton_residual_noalloc(sulf_handle h, double dt, const doub
                                       "holds 65536 partial maxima of 256 nodes each)");
     if (nblocks < 1) nblocks = 1;
     unsigned long long* partial = nullptr;
-    int rc = partial_address(&partial);
+    int rc = partial_address(h, &partial);
     if (rc) return rc;
     ResidualArgs a;
     a.l0 = G->inl[0];

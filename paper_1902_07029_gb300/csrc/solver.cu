@@ -96,6 +96,9 @@ struct sulf_domain {
     sulf_solver solver{};
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
+    int device = 0;                    // the CUDA device current at creation
+    void* noalloc_scratch = nullptr;   // device address of noalloc.cu's static scratch, looked up on
+                                       // this handle's first sulf_newton_residual_noalloc call
     DevMem mem;
     double t = 0, dt = 0;
     // statistics
@@ -769,6 +772,8 @@ cudaStream_t handle_stream(sulf_handle h) { return h ? h->stream : nullptr; }
 void handle_count_launches(sulf_handle h, int n) {
     if (h) h->launches += n;
 }
+int handle_device(sulf_handle h) { return h ? h->device : -1; }
+void** handle_noalloc_slot(sulf_handle h) { return h ? &h->noalloc_scratch : nullptr; }
 }  // namespace sulf
 
 // ===========================================================================
@@ -806,7 +811,10 @@ int sulf_create_domain(const double* levelset, int dim, const double* box, int N
     if (Nl != coarsest_N || nl > SULF_MAXLEV) return sulf_fail(SULF_EINVAL, "N must be coarsest_N times a power of two");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return sulf_fail(SULF_EDEVICE, "no CUDA device");
+    int cur_dev = 0;
+    if (cudaGetDevice(&cur_dev) != cudaSuccess) return sulf_fail(SULF_EDEVICE, "cudaGetDevice failed");
     sulf_domain* d = new sulf_domain();
+    d->device = cur_dev;
     d->dim = dim;
     d->N = N;
     d->L = nl;

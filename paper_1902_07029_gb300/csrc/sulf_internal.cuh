@@ -308,6 +308,8 @@ const sulf_model* handle_model(sulf_handle h);
 int handle_bc(sulf_handle h);
 cudaStream_t handle_stream(sulf_handle h);
 void handle_count_launches(sulf_handle h, int n);
+int handle_device(sulf_handle h);       // the device the handle was created on
+void** handle_noalloc_slot(sulf_handle h);  // per-handle cache of a device address (noalloc.cu)
 
 }  // namespace sulf
 

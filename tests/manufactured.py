@@ -153,3 +153,96 @@ def rel_errors(params, s, c, ty, X, Y, T, h):
         out["g" + name + "_inf"] = eg.max() / np.abs(ge[ok]).max()
         out["g" + name + "_1"] = eg.sum() / np.abs(ge[ok]).sum()
     return out
+
+
+# ---- 3-D: the same construction on a rounded box (the dimension-by-dimension
+# extension of the method; the paper's tests are 2-D) ----
+
+def exact3(params, X, Y, Z, t):
+    """s = 2 + sin x cos y cos z sin(t + sqrt 2),
+    c = 3 + sin(x/2) cos 3y cos 2z sin(2t + sqrt 3)."""
+    X, Y, Z = (np.asarray(A, dtype=np.float64) for A in (X, Y, Z))
+    s = 2.0 + np.sin(X) * np.cos(Y) * np.cos(Z) * np.sin(t + R2)
+    c = 3.0 + np.sin(0.5 * X) * np.cos(3.0 * Y) * np.cos(2.0 * Z) * np.sin(2.0 * t + R3)
+    return s, c
+
+
+def sources3(params, X, Y, Z, t):
+    """f1 = d/dt(phi s) + (a/m_c) phi s c - d div(phi grad s),
+    f2 = dc/dt + (a/m_s) phi s c, written out by hand in 3-D."""
+    a, d, m_s, m_c, alpha, beta = params
+    X, Y, Z = (np.asarray(A, dtype=np.float64) for A in (X, Y, Z))
+    s, c = exact3(params, X, Y, Z, t)
+    st, ct = np.sin(t + R2), np.sin(2.0 * t + R3)
+    sx, cy, cz = np.sin(X), np.cos(Y), np.cos(Z)
+    s_t = sx * cy * cz * np.cos(t + R2)
+    s_x = np.cos(X) * cy * cz * st
+    s_y = -sx * np.sin(Y) * cz * st
+    s_z = -sx * cy * np.sin(Z) * st
+    lap_s = -3.0 * sx * cy * cz * st
+    hx, c3y, c2z = np.sin(0.5 * X), np.cos(3.0 * Y), np.cos(2.0 * Z)
+    c_t = 2.0 * hx * c3y * c2z * np.cos(2.0 * t + R3)
+    c_x = 0.5 * np.cos(0.5 * X) * c3y * c2z * ct
+    c_y = -3.0 * hx * np.sin(3.0 * Y) * c2z * ct
+    c_z = -2.0 * hx * c3y * np.sin(2.0 * Z) * ct
+    phi = alpha * c + beta
+    div = alpha * (c_x * s_x + c_y * s_y + c_z * s_z) + phi * lap_s
+    f1 = alpha * c_t * s + phi * s_t + (a / m_c) * phi * s * c - d * div
+    f2 = c_t + (a / m_s) * phi * s * c
+    return f1, f2
+
+
+def symbolic3(params):
+    """exact3 and sources3 derived symbolically (sympy): numpy callables of
+    (x, y, z, t)."""
+    import sympy as sp
+
+    a, d, m_s, m_c, alpha, beta = params
+    x, y, z, t = sp.symbols("x y z t", real=True)
+    s = 2 + sp.sin(x) * sp.cos(y) * sp.cos(z) * sp.sin(t + sp.sqrt(2))
+    c = 3 + sp.sin(x / 2) * sp.cos(3 * y) * sp.cos(2 * z) * sp.sin(2 * t + sp.sqrt(3))
+    phi = alpha * c + beta
+    div = sum(sp.diff(phi * sp.diff(s, v), v) for v in (x, y, z))
+    f1 = sp.diff(phi * s, t) + (a / m_c) * phi * s * c - d * div
+    f2 = sp.diff(c, t) + (a / m_s) * phi * s * c
+    mk = lambda e: sp.lambdify((x, y, z, t), e, "numpy")  # noqa: E731
+    return mk(s), mk(c), mk(f1), mk(f2)
+
+
+def run_oracle3(oracle_mod, phi, N, lo, hi, params, T, coarsest_N=4):
+    """Advance the oracle in 3-D from the exact data at t = 0 to t = T with
+    dt = h, Dirichlet data s_b = exact s at each ghost's boundary point B_g
+    and t_{n+1}, CN-averaged sources.  Returns (s, c, type, (X, Y, Z), T)."""
+    import workloads
+
+    X, Y, Z = workloads.node_coords(3, lo, hi, N)
+    h = (hi - lo) / N
+    nsteps = max(1, int(round(T / h)))
+    dt = T / nsteps
+    o = oracle_mod.Oracle(phi, 3, lo, hi, N, coarsest_N)
+    o.set_model(tuple(params) + (1.0, 0.0, 0.0))
+    o.set_solver(newton_tol=1e-11)
+    s0, c0 = exact3(params, X, Y, Z, 0.0)
+    o.set_state(s0, c0, 0.0)
+    B = o.level_ghosts(0)["B"]
+    for k in range(nsteps):
+        t0, t1 = k * dt, (k + 1) * dt
+        f1o, f2o = sources3(params, X, Y, Z, t0)
+        f1n, f2n = sources3(params, X, Y, Z, t1)
+        o.set_sources(f1o, f1n, f2o, f2n)
+        o.set_ghost_sb(exact3(params, B[:, 0], B[:, 1], B[:, 2], t1)[0])
+        o.step(dt, 1)
+    s, c, ty = o.get_state()
+    return s, c, ty, (X, Y, Z), nsteps * dt
+
+
+def rel_errors3(params, s, c, ty, XYZ, T):
+    """Relative L1 and Linf errors of s and c on the inside nodes (3-D)."""
+    se, ce = exact3(params, *XYZ, T)
+    ins = ty == 1
+    out = {}
+    for name, num, ex in (("s", s, se), ("c", c, ce)):
+        e = np.abs(num - ex)[ins]
+        out[name + "_inf"] = e.max() / np.abs(ex[ins]).max()
+        out[name + "_1"] = e.sum() / np.abs(ex[ins]).sum()
+    return out

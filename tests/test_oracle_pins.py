@@ -317,20 +317,6 @@ def test_reaction_invariant_without_diffusion(oracle_mod):
     assert np.abs(inv(s1, c1)[ins] - i0).max() <= 1e-12 * np.abs(i0).max()
 
 
-def test_convergence_factor_bounded_independent_of_h(oracle_mod):
-    """Multigrid efficiency (Sec. 4.2): the per-cycle residual reduction stays
-    bounded away from 1 as the grid is refined."""
-    worst = []
-    for N in (128, 256, 512):
-        o = _oracle(oracle_mod, workloads.disk(N), 2, N)
-        o.step(2.0 / N, 2)
-        rho, first = o.rho_history()
-        late = rho[len(rho) // 2:]
-        late = late[late > 0]
-        worst.append(np.median(late))
-    assert max(worst) <= 0.3, worst
-
-
 def test_transfer_operators_closed_forms(oracle_mod):
     """Restriction weights sum to one (a constant defect restricts to the same
     constant at every coarse node), and prolongation reproduces a linear
