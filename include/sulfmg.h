@@ -54,7 +54,11 @@ typedef struct {
 
 /* Solver controls.
    nu1, nu2      pre- and post-relaxation sweeps (Sec. 3.5)            default 2, 2
-   cycle         1 = V-cycle, 2 = W-cycle                              default 1
+   cycle         1 = V-cycle, 2 = W-cycle, 3 = full multigrid (Sec. 3.5's
+                 transfers: the right-hand side restricted to every level,
+                 the coarsest level solved, each finer level started from the
+                 interpolated coarse solution with one V-cycle) as the first
+                 cycle of every linear solve, V-cycles after it   default 1
    max_newton    Newton iteration cap per step                         default 20
    max_cycles    multigrid cycle cap per linear solve                  default 30
    ghost_sweeps  passes of the ghost relaxation (Eq. RelGhost) per sweep default 4
@@ -65,7 +69,15 @@ typedef struct {
                  defect correction (Newton residual, boundary rows of F and
                  the convergence tests stay FP64)                        default 0
    smoother      0 = collective (2x2 block, Eq. matrixP) red-black Gauss-Seidel,
-                 1 = pointwise (Eq. matrixPclassical) red-black            default 0
+                 1 = pointwise (Eq. matrixPclassical) red-black,
+                 2 = collective lexicographic Gauss-Seidel, the paper's
+                 ordering (Sec. 3.5.1): the inside nodes are visited wavefront
+                 by wavefront (i+j(+k) = const, increasing), which gives the
+                 box-order sweep's values exactly; one CTA per sweep, for
+                 comparison with the paper, not for speed           default 0
+                 (fuse_below does not apply to W-cycles, full multigrid or
+                 the lexicographic smoother: every level runs as separate
+                 kernels)
    graphs        1 = each multigrid cycle is captured once as a CUDA graph and
                  replayed; 0 = kernels launched one by one               default 1
    fuse_below    the first level with at most this many active nodes and all
@@ -255,6 +267,26 @@ int sulf_kernel_time(sulf_handle h, double* ms, long long* launches);
 int sulf_newton_residual_noalloc(sulf_handle h, double dt, const double* W_dev, const double* Wn_dev, double* F_dev,
                                  double* fnorm_dev);
 
+/* Autotuning of the solver controls that change only speed, not results
+   beyond rounding order: fuse_below (the fused coarse-level threshold; only
+   for V-cycles with red-black sweeps), ghost_compose and pdl.  Each candidate
+   is timed on this handle's own problem -- the Newton system of a CN step of
+   size dt from the current state -- as a linear solve of 6 cycles (built
+   once, then timed); the fused-level thresholds {0, 60, 150, 400, 1000, 3000,
+   10000} are tried first, then the other two switches at the best one.  The
+   fastest candidate is written into the handle's solver controls (the state
+   is unchanged).  With use_cache != 0 a result found earlier in this process
+   for the same problem class (dim, N, coarsest N, precision, cycle, smoother,
+   nu1, nu2, boundary condition) is applied without timing.  Blocks. */
+typedef struct {
+    int fuse_below, ghost_compose, pdl; /* the chosen controls */
+    double ms_per_cycle;                /* their time per cycle */
+    double ms_per_cycle_default;        /* the defaults' (fuse_below -1, ghost_compose 1, pdl 1) */
+    int candidates;                     /* candidates timed */
+    int cached;                         /* 1: taken from the process cache, nothing timed */
+} sulf_tune_result;
+int sulf_autotune(sulf_handle h, double dt, int use_cache, sulf_tune_result* out);
+
 /* Release the handle and its device memory. */
 void sulf_destroy(sulf_handle h);
 
@@ -270,6 +302,10 @@ int sulf_batch_create(const sulf_handle* handles, int n, int nstreams, sulf_batc
    failing instance's error (all instances are attempted) */
 int sulf_batch_step(sulf_batch b, const double* dt, const int* nsteps);
 int sulf_batch_status(sulf_batch b, int* status); /* per-instance return codes of the last step */
+/* sulf_autotune of every instance (dt[i] its step), through the process cache:
+   one timing per problem class (dim, N, precision, ...), the others take the
+   result; out (may be NULL) receives one result per instance */
+int sulf_batch_autotune(sulf_batch b, const double* dt, sulf_tune_result* out);
 void sulf_batch_destroy(sulf_batch b);             /* the handles return to their own streams */
 
 /* ---- serving: continuous batching of time-stepping jobs under an HBM budget ---- */

@@ -1102,6 +1102,35 @@ static void cycle(Oracle *O, int l)
     for (int k = 0; k < O->nu2; k++) smooth(O, L);
 }
 
+/* Full multigrid (cycle type 3, the first cycle of every linear solve): the
+   right-hand side is carried down the hierarchy with the same boundary-aware
+   restriction the cycles use (defect of x = 0 is the right-hand side itself,
+   ghost defects extended into the band first), the coarsest system is solved
+   directly, and on the way up each level starts from the interpolated coarse
+   solution and takes one V-cycle (Sec. 3.5's transfers and smoother). */
+static void fmg(Oracle *O)
+{
+    for (int l = 0; l + 1 < O->L; l++) {
+        OLevel *L = &O->lev[l];
+        for (long i = 0; i < 2 * L->nn; i++) L->x[i] = 0.0;
+        residual(O, L);
+        extend_defect(O, L);
+        restrict_defect(L, &O->lev[l + 1]);
+    }
+    OLevel *C = &O->lev[O->L - 1];
+    for (long i = 0; i < 2 * C->nn; i++) C->x[i] = 0.0;
+    coarsest_solve(C);
+    int saved = O->cycle;
+    O->cycle = 1;
+    for (int l = O->L - 2; l >= 0; l--) {
+        OLevel *L = &O->lev[l];
+        for (long i = 0; i < 2 * L->nn; i++) L->x[i] = 0.0;
+        prolong_add(&O->lev[l + 1], L);
+        cycle(O, l);
+    }
+    O->cycle = saved;
+}
+
 /* prepare coarse coefficients and the coarsest factorisation from lev[0].Wc */
 static int prepare_hierarchy(Oracle *O)
 {
@@ -1127,7 +1156,14 @@ static int linear_solve(Oracle *O, double rnorm0)
     double rprev = rnorm0;
     int cyc;
     for (cyc = 1; cyc <= O->max_cycles; cyc++) {
-        cycle(O, 0);
+        if (O->cycle == 3 && cyc == 1) {
+            fmg(O);
+        } else {
+            int saved = O->cycle;
+            if (O->cycle == 3) O->cycle = 1;
+            cycle(O, 0);
+            O->cycle = saved;
+        }
         residual(O, L);
         double rn = maxabs_active(L, L->res);
         double rho = rprev > 0.0 ? rn / rprev : 0.0;
@@ -1334,12 +1370,13 @@ int oracle_set_model(void *h, const double *p)
     return OR_OK;
 }
 
-/* smoother: 0 red-black collective GS, 1 red-black pointwise GS, 2 lexicographic collective GS */
+/* smoother: 0 red-black collective GS, 1 red-black pointwise GS, 2 lexicographic collective GS;
+   cycle_type: 1 V, 2 W, 3 full multigrid first, then V-cycles */
 int oracle_set_solver(void *h, int nu1, int nu2, int cycle_type, int max_newton, int max_cycles,
                       double newton_tol, double lin_rtol, double tau_s, int smoother, int ghost_sweeps)
 {
     Oracle *O = (Oracle *)h;
-    if (nu1 < 0 || nu2 < 0 || (cycle_type != 1 && cycle_type != 2) || max_newton < 1 || max_cycles < 1 ||
+    if (nu1 < 0 || nu2 < 0 || cycle_type < 1 || cycle_type > 3 || max_newton < 1 || max_cycles < 1 ||
         !(tau_s > 0.0 && tau_s < 1.0) || smoother < 0 || smoother > 2 || ghost_sweeps < 1)
         return OR_EINVAL;
     O->ghost_sweeps = ghost_sweeps;
@@ -1657,6 +1694,8 @@ int oracle_cycles(void *h, double dt, const double *Wc0, const double *rhs, doub
     for (int k = 0; k < ncycles; k++) {
         if (O->L == 1)
             coarsest_solve(L);
+        else if (O->cycle == 3 && k == 0)
+            fmg(O); /* full multigrid starts from x = 0 */
         else
             cycle(O, 0);
         residual(O, L);

@@ -51,6 +51,12 @@ class SulfJobResult(ctypes.Structure):
                 ("device_bytes", ctypes.c_ulonglong), ("newton", ctypes.c_longlong), ("cycles", ctypes.c_longlong)]
 
 
+class SulfTuneResult(ctypes.Structure):
+    _fields_ = [("fuse_below", ctypes.c_int), ("ghost_compose", ctypes.c_int), ("pdl", ctypes.c_int),
+                ("ms_per_cycle", ctypes.c_double), ("ms_per_cycle_default", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("cached", ctypes.c_int)]
+
+
 class SulfServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("queued", ctypes.c_longlong),
                 ("running", ctypes.c_longlong), ("max_running", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
@@ -89,6 +95,8 @@ _SIGS = {
     "sulf_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]),
     "sulf_batch_step": (ctypes.c_int, [P, _dp, ctypes.POINTER(ctypes.c_int)]),
     "sulf_batch_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
+    "sulf_batch_autotune": (ctypes.c_int, [P, _dp, ctypes.POINTER(SulfTuneResult)]),
+    "sulf_autotune": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SulfTuneResult)]),
     "sulf_batch_destroy": (None, [P]),
     "sulf_estimate_device_bytes": (ctypes.c_ulonglong, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "sulf_server_create": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_int, ctypes.POINTER(P)]),
@@ -258,6 +266,13 @@ class Domain:
         _chk(self.lib, self.lib.sulf_newton_residual_noalloc(self.h, dt, P(W_ptr), P(Wn_ptr), P(F_ptr),
                                                              P(fnorm_ptr)))
 
+    def autotune(self, dt, use_cache=True):
+        """Time the speed-only solver controls on this domain's Newton system
+        and keep the fastest (sulf_autotune); returns the result as a dict."""
+        r = SulfTuneResult()
+        _chk(self.lib, self.lib.sulf_autotune(self.h, dt, int(bool(use_cache)), ctypes.byref(r)))
+        return {f[0]: getattr(r, f[0]) for f in r._fields_}
+
     def set_bc(self, bc):
         """0: Dirichlet s = s_b (Eq. BCs); 1: Neumann ds/dn = s_b (Eq. BCsN)."""
         _chk(self.lib, self.lib.sulf_set_bc(self.h, int(bc)))
@@ -401,6 +416,14 @@ class Batch:
         dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
         ns = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int32), (n,)))
         _chk(self.lib, self.lib.sulf_batch_step(self.b, _d(dts), ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+
+    def autotune(self, dt):
+        """sulf_batch_autotune: one timing per problem class; per-instance results"""
+        n = len(self.domains)
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        res = (SulfTuneResult * n)()
+        _chk(self.lib, self.lib.sulf_batch_autotune(self.b, _d(dts), res))
+        return [{f[0]: getattr(r, f[0]) for f in r._fields_} for r in res]
 
     def status(self):
         st = np.zeros(len(self.domains), dtype=np.int32)

@@ -212,6 +212,30 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
     stages::relax_apply<D, T, PW, false>(p, k, rhs, x, st);
 }
 
+// lexicographic collective Gauss-Seidel (Sec. 3.5.1, the paper's smoother):
+// one CTA walks the wavefronts i+j(+k) = const in increasing order; the
+// nodes of one wavefront are independent, and when a node is updated its
+// lower axis neighbours (previous wavefront) hold new values and its upper
+// ones old values, as in a sweep in box order.  Values written in one
+// wavefront are read in the next through L2 (ld.global.cg).
+constexpr int kLexThreads = 512;
+template <int D, typename T>
+__global__ void __launch_bounds__(kLexThreads) k_relax_lex(const int* __restrict__ lex, const int* __restrict__ ptr,
+                                                            int nd, CoefPtr<D, T> cf,
+                                                            const typename V2<T>::t* __restrict__ rhs,
+                                                            typename V2<T>::t* x, long long st1, long long st2,
+                                                            const int* __restrict__ sidx, int snap_n, T* snap) {
+    const long long st[3] = {1, st1, st2};
+    pdl_enter();
+    for (int dg = 0; dg < nd; dg++) {
+        const int a = ptr[dg], b = ptr[dg + 1];
+        for (int i = a + threadIdx.x; i < b; i += blockDim.x)
+            stages::relax_node<D, T, false, true>(lex[i], cf, rhs, x, st);
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < snap_n; i += blockDim.x) snap[i] = __ldcg(reinterpret_cast<const T*>(x + sidx[i]));
+}
+
 // one Jacobi pass of the ghost relaxation of Eq. RelGhost over all ghosts
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_ghost_pass(const int* __restrict__ gidx, GhostTab<T> tb,
@@ -1011,6 +1035,15 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
 }
 
 template <int D, typename T>
+int launch_relax_lex(const LevelGeo& L, const LevelVec<T>& V, T* snap, cudaStream_t s) {
+    if (!L.lex) return 0;
+    const int sn = snap ? L.ng : 0;
+    launch_k(k_relax_lex<D, T>, 1, kLexThreads, 0, s, L.lex, L.lexptr, L.nlexd, coef_ptr<D, T>(V), V.rhs, V.x,
+             L.st[1], L.st[2], L.gidx, sn, snap);
+    return 1;
+}
+
+template <int D, typename T>
 int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int passes, bool composed,
                         cudaStream_t s) {
     if (L.ng == 0 || passes < 1) return 0;
@@ -1243,6 +1276,7 @@ int launch_export_state(const LevelGeo& L, const double2* W, double* sv, double*
     template int launch_coefs<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, cudaStream_t);          \
     template int launch_relax_inside<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, bool, T*,   \
                                            cudaStream_t);                                                        \
+    template int launch_relax_lex<D, T>(const LevelGeo&, const LevelVec<T>&, T*, cudaStream_t);                     \
     template int launch_relax_ghosts<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, int, bool,          \
                                            cudaStream_t);                                                        \
     template int launch_residual<D, T>(const LevelGeo&, const LevelVec<T>&, const Coef<T>&, unsigned long long*,  \

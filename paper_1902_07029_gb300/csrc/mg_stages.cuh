@@ -482,17 +482,41 @@ __device__ __forceinline__ bool valid_for(int8_t rule, int8_t t) {
 
 // The fixed part of the boundary-aware full weighting (Eqs. Fstencil,
 // Fstencilgen, Fig. Neigh) at coarse node I: the fine twin f, the per-axis
-// mirrored 1-D weights, the members that hold a value of the rule's kind
-// (bit kk), and the weight moved to the centre (the centre's own plus that of
-// every member without a value), summed in member order.
+// mirrored 1-D weights times 4 -- (1,2,1), (2,2,0), (0,2,2) or (0,4,0) --, the
+// members that hold a value of the rule's kind (bit kk), and the weight moved
+// to the centre (the centre's own plus that of every member without a value).
+// A member's weight is the product of its axes' weights over 4^D: a power of
+// two, built from its exponent with integer operations, so the weights cost
+// no FP64 instruction (FP64 issues at two lanes per SM and clock on this GPU)
+// and are exactly the products the paper's per-axis rule gives.
 template <int D, typename T>
 struct RestrictGeo {
     long long I, f;
-    T w1[3][3];
+    unsigned char e1[3][3];  // per-axis weight times 4 as log2 + 1 (0: weight 0)
     unsigned valid;
-    T wc;
-    T w[D == 2 ? 9 : 1];  // 2-D: the member weights, kept from the fetch
+    int iwc;                 // centre weight times 4^D
+    bool full;               // (1,2,1) on every axis and every member valid
 };
+
+// 2^(e - 2D) in T for a member whose per-axis exponents sum to e
+template <int D, typename T>
+__device__ __forceinline__ T pow2_weight(int e);
+template <>
+__device__ __forceinline__ double pow2_weight<2, double>(int e) {
+    return __longlong_as_double((long long)(1023 + e - 4) << 52);
+}
+template <>
+__device__ __forceinline__ double pow2_weight<3, double>(int e) {
+    return __longlong_as_double((long long)(1023 + e - 6) << 52);
+}
+template <>
+__device__ __forceinline__ float pow2_weight<2, float>(int e) {
+    return __int_as_float((127 + e - 4) << 23);
+}
+template <>
+__device__ __forceinline__ float pow2_weight<3, float>(int e) {
+    return __int_as_float((127 + e - 6) << 23);
+}
 
 template <int D, typename T>
 __device__ __forceinline__ RestrictGeo<D, T> fetch_restrict(int t, const Lists& ls, const int8_t* ctype, int cn,
@@ -511,46 +535,51 @@ __device__ __forceinline__ RestrictGeo<D, T> fetch_restrict(int t, const Lists& 
 #pragma unroll
     for (int a = 0; a < D; a++) f += 2LL * ii[a] * fst[a];
     g.f = f;
+    bool std_axes = true;
 #pragma unroll
     for (int a = 0; a < D; a++) {
         bool vl = ii[a] > 0 && valid_for(rule, ftype[f - fst[a]]);
         bool vr = 2 * ii[a] < fn - 1 && valid_for(rule, ftype[f + fst[a]]);
-        T l = 1, m = 2, r = 1;
+        // log2(weight * 4) + 1: 1 -> 1, 2 -> 2, 4 -> 3, 0 -> 0
+        unsigned char l = 1, m = 2, r = 1;
         if (vl && !vr) {
             l = 2; m = 2; r = 0;
         } else if (!vl && vr) {
             l = 0; m = 2; r = 2;
         } else if (!vl && !vr) {
-            l = 0; m = 4; r = 0;
+            l = 0; m = 3; r = 0;
         }
-        g.w1[a][0] = l / (T)4;
-        g.w1[a][1] = m / (T)4;
-        g.w1[a][2] = r / (T)4;
+        std_axes = std_axes && vl && vr;
+        g.e1[a][0] = l;
+        g.e1[a][1] = m;
+        g.e1[a][2] = r;
     }
     const int K = D == 2 ? 9 : 27;
     g.valid = 0;
-    g.wc = 0;
+    g.iwc = 0;
 #pragma unroll
     for (int kk = 0; kk < K; kk++) {
-        const int k0 = kk % 3 - 1, k1 = (kk / 3) % 3 - 1, k2 = kk / 9 - 1;
-        T w = g.w1[0][k0 + 1] * g.w1[1][k1 + 1];
-        if (D == 3) w = w * g.w1[2][k2 + 1];
-        if (w == (T)0) continue;
-        bool centre = k0 == 0 && k1 == 0 && (D == 2 || k2 == 0);
-        long long node = f + k0 * fst[0] + k1 * fst[1];
-        if (D == 3) node += k2 * fst[2];
+        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+        const int e0 = g.e1[0][k0], ea = g.e1[1][k1], eb = D == 3 ? g.e1[2][k2] : 1;
+        if (e0 == 0 || ea == 0 || eb == 0) continue;
+        const int iw = 1 << (e0 + ea + eb - 3);  // weight times 4^D
+        bool centre = k0 == 1 && k1 == 1 && (D == 2 || k2 == 1);
+        long long node = f + (k0 - 1) * fst[0] + (k1 - 1) * fst[1];
+        if (D == 3) node += (k2 - 1) * fst[2];
         if (centre || !valid_for(rule, ftype[node]))
-            g.wc += w;
+            g.iwc += iw;
         else
             g.valid |= 1u << kk;
-        if (D == 2) g.w[kk % 9] = w;
     }
+    const unsigned all = (D == 2 ? 0x1ffu : 0x7ffffffu) & ~(1u << (D == 2 ? 4 : 13));
+    g.full = std_axes && g.valid == all;
     return g;
 }
 
-// the weighting applied to the fine defect; also zeroes the coarse error,
-// or, for a red inside node whose coefficients red holds, sets it to the
-// first red relaxation from zero (relax_value_zero)
+// the weighting applied to the fine defect (members in box order, then the
+// centre with the weight moved to it); also zeroes the coarse error, or, for a
+// red inside node whose coefficients red holds, sets it to the first red
+// relaxation from zero (relax_value_zero)
 template <int D, typename T, bool CG, bool PW = false>
 __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int fn, const typename V2<T>::t* fres,
                                                typename V2<T>::t* crhs, typename V2<T>::t* cx,
@@ -573,25 +602,35 @@ __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int f
             v[j].y = 0;
             if ((g.valid >> kk) & 1u) v[j] = ldx<CG>(fres + node);
         }
+        if (g.full) {
+            // interior: the standard full weighting, weights known at compile time
 #pragma unroll
-        for (int j = 0; j < 9; j++) {
-            const int kk = c0 + j;
-            if (!((g.valid >> kk) & 1u)) continue;
-            const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
-            T w;
-            if (D == 2) {
-                w = g.w[kk % 9];
-            } else {
-                w = g.w1[0][k0] * g.w1[1][k1];
-                w = w * g.w1[2][k2];
+            for (int j = 0; j < 9; j++) {
+                const int kk = c0 + j;
+                const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+                if (k0 == 1 && k1 == 1 && (D == 2 || k2 == 1)) continue;
+                const int e = (k0 == 1) + (k1 == 1) + (D == 3 ? (k2 == 1) : 0);
+                const T w = (T)(1 << e) / (T)(D == 2 ? 16 : 64);
+                as += w * v[j].x;
+                ac += w * v[j].y;
             }
-            as += w * v[j].x;
-            ac += w * v[j].y;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 9; j++) {
+                const int kk = c0 + j;
+                if (!((g.valid >> kk) & 1u)) continue;
+                const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+                const int e = g.e1[0][k0] + g.e1[1][k1] + (D == 3 ? g.e1[2][k2] : 1) - 3;
+                const T w = pow2_weight<D, T>(e);
+                as += w * v[j].x;
+                ac += w * v[j].y;
+            }
         }
     }
+    const T wc = g.full ? (T)(1 << D) / (T)(D == 2 ? 16 : 64) : (T)g.iwc / (T)(D == 2 ? 16 : 64);
     T2 out;
-    out.x = as + g.wc * vc.x;
-    out.y = ac + g.wc * vc.y;
+    out.x = as + wc * vc.x;
+    out.y = ac + wc * vc.y;
     crhs[g.I] = out;
     T2 z;
     z.x = 0;
@@ -608,21 +647,22 @@ __device__ __forceinline__ void restrict_node(int t, const Lists& ls, const int8
 }
 
 // The fixed part of the (bi/tri)linear interpolation to fine active node i
-// (Sec. 3.5.3): the coarse corners that are active (bit cc) with their nodes,
-// and the sum of their weights, renormalising over the active corners.
+// (Sec. 3.5.3): the coarse corners that are active (bit cc) with their nodes.
+// Every corner of a fine node carries the same weight 2^-k (k its odd
+// coordinates), so the weights renormalised over the active corners are
+// 1/n each (n of them): the interpolated value is the corners' sum times the
+// correctly rounded 1/n -- the same number the weighted sum divided by the
+// summed weights gives, without FP64 multiplies or a division.
 template <int D, typename T>
 struct ProlongGeo {
     long long i;
     long long node[1 << D];
-    T w[1 << D];  // corner weights
     unsigned use;
-    T ws, iws;  // sum of the active corners' weights and its reciprocal
 };
 
-template <int D, typename T>
-__device__ __forceinline__ T corner(const int* ii, int cc, const long long* cst, long long& node, bool& dup) {
-    node = 0;
-    T w = 1;
+template <int D>
+__device__ __forceinline__ long long corner_node(const int* ii, int cc, const long long* cst, bool& dup) {
+    long long node = 0;
     dup = false;
 #pragma unroll
     for (int a = 0; a < D; a++) {
@@ -632,11 +672,10 @@ __device__ __forceinline__ T corner(const int* ii, int cc, const long long* cst,
             if (pick) dup = true;
             node += lo * cst[a];
         } else {
-            w *= (T)0.5;
             node += (pick ? hi : lo) * cst[a];
         }
     }
-    return w;
+    return node;
 }
 
 template <int D, typename T>
@@ -652,28 +691,39 @@ __device__ __forceinline__ ProlongGeo<D, T> fetch_prolong(int t, const Lists& ls
     if (D == 3) ii[2] = (int)(i / ((long long)fn * fn));
     const long long cst[3] = {1, cn, (long long)cn * cn};
     g.use = 0;
-    g.ws = 0;
     const int NC = 1 << D;
 #pragma unroll
     for (int cc = 0; cc < NC; cc++) {
         bool dup;
-        T w = corner<D, T>(ii, cc, cst, g.node[cc], dup);
-        g.w[cc] = w;
+        g.node[cc] = corner_node<D>(ii, cc, cst, dup);
         if (dup) continue;
         int8_t tc = ctype[g.node[cc]];
         if (tc != T_IN && tc != T_GHOST) continue;
         g.use |= 1u << cc;
-        g.ws += w;
     }
-    g.iws = g.ws > (T)0 ? (T)1 / g.ws : (T)0;
     return g;
+}
+
+// 1/n correctly rounded in T, n = 1..8 (constants folded at compile time)
+template <typename T>
+__device__ __forceinline__ T inv_count(int n) {
+    switch (n) {
+        case 1: return (T)1;
+        case 2: return (T)1 / (T)2;
+        case 3: return (T)1 / (T)3;
+        case 4: return (T)1 / (T)4;
+        case 5: return (T)1 / (T)5;
+        case 6: return (T)1 / (T)6;
+        case 7: return (T)1 / (T)7;
+        default: return (T)1 / (T)8;
+    }
 }
 
 template <int D, typename T, bool CG>
 __device__ __forceinline__ void prolong_apply(const ProlongGeo<D, T>& g, int fn, const typename V2<T>::t* cx,
                                               typename V2<T>::t* fx) {
     typedef typename V2<T>::t T2;
-    if (!(g.ws > (T)0)) return;
+    if (!g.use) return;
     const int NC = 1 << D;
     T2 v[1 << D];
 #pragma unroll
@@ -687,11 +737,12 @@ __device__ __forceinline__ void prolong_apply(const ProlongGeo<D, T>& g, int fn,
 #pragma unroll
     for (int cc = 0; cc < NC; cc++) {
         if (!((g.use >> cc) & 1u)) continue;
-        as += g.w[cc] * v[cc].x;
-        ac += g.w[cc] * v[cc].y;
+        as += v[cc].x;
+        ac += v[cc].y;
     }
-    xf.x = fmadd(as, g.iws, xf.x);
-    xf.y = fmadd(ac, g.iws, xf.y);
+    const T r = inv_count<T>(__popc(g.use));
+    xf.x = fmadd(as, r, xf.x);
+    xf.y = fmadd(ac, r, xf.y);
     fx[g.i] = xf;
 }
 

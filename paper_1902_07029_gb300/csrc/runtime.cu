@@ -139,6 +139,21 @@ extern "C" int sulf_batch_step(sulf_batch b, const double* dt, const int* nsteps
     return SULF_OK;
 }
 
+// tune each instance through the process cache: the first instance of a
+// problem class is timed on the GPU alone (stream of worker 0), the others of
+// the class take its result
+extern "C" int sulf_batch_autotune(sulf_batch b, const double* dt, sulf_tune_result* out) {
+    if (!b || !dt) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    for (size_t i = 0; i < b->h.size(); i++) {
+        int rc = sulf_set_stream(b->h[i], b->streams[0]);
+        sulf_tune_result r{};
+        if (rc == SULF_OK) rc = sulf_autotune(b->h[i], dt[i], 1, &r);
+        if (rc != SULF_OK) return rc;
+        if (out) out[i] = r;
+    }
+    return SULF_OK;
+}
+
 extern "C" int sulf_batch_status(sulf_batch b, int* status) {
     if (!b || !status) return sulf_fail(SULF_EINVAL, "invalid arguments");
     for (size_t i = 0; i < b->status.size(); i++) status[i] = b->status[i];

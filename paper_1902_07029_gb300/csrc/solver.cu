@@ -2,7 +2,11 @@
 // the multigrid hierarchy resident on the device, Crank-Nicolson steps solved
 // by Newton-Raphson (arXiv:1902.07029, Sec. 3.1 and 3.4) with level-set
 // multigrid cycles (Sec. 3.5) issued as kernels on the handle's stream.
+#include <array>
+#include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -96,6 +100,7 @@ struct sulf_domain {
     sulf_solver solver{};
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
+    bool fmg_now = false;              // the next cycle_body is the full-multigrid cycle
     int device = 0;                    // the CUDA device current at creation
     void* noalloc_scratch = nullptr;   // device address of noalloc.cu's static scratch, looked up on
                                        // this handle's first sulf_newton_residual_noalloc call
@@ -184,6 +189,11 @@ sulf_model default_model() {
     m.s0 = 0.0;
     m.c0 = 10.0;
     return m;
+}
+
+double host_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
 double bits_to_double(unsigned long long b) {
@@ -298,7 +308,7 @@ int tail_level(const sulf_domain* d) {
     // automatic threshold: the fused kernel runs on one SM, whose FP64 rate is
     // two lanes per clock, so FP64 cycles fuse only the smallest levels
     const int fb = d->solver.fuse_below >= 0 ? d->solver.fuse_below : (d->solver.precision == 0 ? 150 : 1000);
-    if (fb <= 0 || d->solver.cycle != 1) return -1;
+    if (fb <= 0 || d->solver.cycle != 1 || d->solver.smoother == 2) return -1;
     for (int l = 0; l < d->L - 1; l++)
         if ((long long)d->geo[l].nin[0] + d->geo[l].nin[1] + d->geo[l].ng <= fb) return l;
     return -1;
@@ -379,9 +389,12 @@ struct MG {
         // external flag makes it an event-record node of the graph)
         const unsigned fl = d->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (timed_sweep) cudaEventRecordWithFlags(next_event(d), d->stream, fl);
-        for (int colour = skip_red ? 1 : 0; colour < 2; colour++)
-            d->launches += launch_relax_inside<D, T>(G, V[l], c, colour, pw,
-                                                     gop && colour == 1 ? V[l].gbuf[0] : nullptr, d->stream);
+        if (d->solver.smoother == 2)
+            d->launches += launch_relax_lex<D, T>(G, V[l], gop ? V[l].gbuf[0] : nullptr, d->stream);
+        else
+            for (int colour = skip_red ? 1 : 0; colour < 2; colour++)
+                d->launches += launch_relax_inside<D, T>(G, V[l], c, colour, pw,
+                                                         gop && colour == 1 ? V[l].gbuf[0] : nullptr, d->stream);
         if (timed_sweep) cudaEventRecordWithFlags(next_event(d), d->stream, fl);
         d->launches += launch_relax_ghosts<D, T>(G, V[l], c, d->solver.ghost_sweeps, gop, d->stream);
         return SULF_OK;
@@ -418,7 +431,7 @@ struct MG {
         // half-sweep (which would read only zeros)
         const int lc = l + 1;
         const bool fused_tail = lc == tail_level(d) && d->tail_ready[p] && d->solver.cycle == 1;
-        const bool fr = d->solver.nu1 >= 1 && lc < d->L - 1 && !fused_tail;
+        const bool fr = d->solver.nu1 >= 1 && lc < d->L - 1 && !fused_tail && d->solver.smoother != 2;
         d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[lc], V[lc], fr, d->solver.smoother == 1,
                                              d->stream);
         int gam = d->solver.cycle == 2 ? 2 : 1;
@@ -427,6 +440,27 @@ struct MG {
         d->launches += launch_prolong<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
         for (int k = 0; k < d->solver.nu2; k++)
             if ((rc = relax(l))) return rc;
+        return SULF_OK;
+    }
+
+    // Full multigrid, the first cycle of a linear solve with cycle = 3: the
+    // right-hand side goes down the hierarchy by the cycles' own residual (of
+    // the zero start), band extension and restriction; the coarsest level is
+    // solved directly; each finer level starts from the interpolated coarse
+    // solution and takes one V-cycle.  Every level's x is zero on entry (the
+    // finest by the caller, the coarse ones by the restriction).
+    int fmg() {
+        const bool pw = d->solver.smoother == 1;
+        for (int l = 0; l + 1 < d->L; l++) {
+            d->launches += launch_residual<D, T>(d->geo[l], V[l], make_coef<T>(d, l), nullptr, d->stream);
+            d->launches += launch_extend<D, T>(d->geo[l], V[l], d->stream);
+            d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], false, pw, d->stream);
+        }
+        d->launches += launch_coarsest_solve<D, T>(d->geo[d->L - 1], V[d->L - 1], d->stream);
+        for (int l = d->L - 2; l >= 0; l--) {
+            d->launches += launch_prolong<D, T>(d->geo[l], V[l], d->geo[l + 1], V[l + 1], d->stream);
+            if (int rc = cycle(l)) return rc;
+        }
         return SULF_OK;
     }
 
@@ -471,17 +505,18 @@ template <int D>
 int cycle_body(sulf_domain* d, const cudaGraphConditionalHandle* loop = nullptr, int max_cycles = 0) {
     const LevelGeo& G0 = d->geo[0];
     LevelVec<double>& V0 = d->v64[0];
+    const bool fmg = d->fmg_now && d->L > 1;
     if (d->solver.precision == 0) {
         if (d->L == 1)
             d->launches += launch_coarsest_solve<D, double>(G0, V0, d->stream);
-        else if (int rc = MG<D, double>{d, d->v64}.cycle(0))
+        else if (int rc = fmg ? MG<D, double>{d, d->v64}.fmg() : MG<D, double>{d, d->v64}.cycle(0))
             return rc;
     } else {
         LevelVec<float>& U0 = d->v32[0];
         SULF_CUDA_TRY(cudaMemsetAsync(U0.x, 0, sizeof(float2) * G0.nn, d->stream));
         if (d->L == 1)
             d->launches += launch_coarsest_solve<D, float>(G0, U0, d->stream);
-        else if (int rc = MG<D, float>{d, d->v32}.cycle(0))
+        else if (int rc = fmg ? MG<D, float>{d, d->v32}.fmg() : MG<D, float>{d, d->v32}.cycle(0))
             return rc;
         d->launches += launch_accumulate(G0, V0.x, U0.x, d->stream);
     }
@@ -579,7 +614,7 @@ bool build_loop(sulf_domain* d, int max_cycles) {
 // negative error.
 template <int D>
 int device_loop(sulf_domain* d, double fnorm, int max_cycles, double rtol, double* rnorms) {
-    if (d->loop_off || !d->solver.graphs || d->prof || max_cycles > kLoopMaxCycles) return 0;
+    if (d->loop_off || !d->solver.graphs || d->prof || max_cycles > kLoopMaxCycles || d->solver.cycle == 3) return 0;
     const int p = d->solver.precision;
     sulf_domain::LoopGraph& g = d->loop[p];
     if (!g.exec || g.dt != d->dt || !same_solver(g.sv, d->solver) || g.max_cycles != max_cycles)
@@ -693,7 +728,20 @@ int linear_solve(sulf_domain* d, double fnorm, int max_cycles, double rtol, doub
     double rprev = fnorm;
     int cyc;
     for (cyc = 1; cyc <= max_cycles; cyc++) {
-        rc = run_cycle<D>(d);
+        if (d->solver.cycle == 3 && cyc == 1) {
+            // the full-multigrid cycle, launched directly (the cycles after it
+            // are V-cycles, replayed from their graph)
+            size_t e0 = d->evused;
+            d->fmg_now = true;
+            rc = cycle_body<D>(d);
+            d->fmg_now = false;
+            if (rc) return rc;
+            SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+            rc = accumulate_prof(d, e0, d->evused);
+            d->evused = e0;
+        } else {
+            rc = run_cycle<D>(d);
+        }
         if (rc) return rc;
         if (*(int*)(d->hnorm + 6)) return sulf_fail(SULF_ENOTCONV, "singular coarsest-level Jacobian");
         double rn = bits_to_double(d->hnorm[0]);
@@ -755,6 +803,37 @@ int cn_step(sulf_domain* d) {
 }
 
 bool valid(sulf_handle h) { return h != nullptr; }
+
+// wavefront lists of the lexicographic smoother, built once per level on the
+// host from the node types: inside nodes ordered by i+j(+k), then box order
+int ensure_lex(sulf_domain* d) {
+    for (int l = 0; l < d->L; l++) {
+        LevelGeo& G = d->geo[l];
+        if (G.lex) continue;
+        std::vector<int8_t> t(G.nn);
+        SULF_CUDA_TRY(cudaMemcpyAsync(t.data(), G.type, G.nn, cudaMemcpyDeviceToHost, d->stream));
+        SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+        const int nd = G.dim * (G.n - 1) + 1;
+        std::vector<int> ptr(nd + 1, 0), list;
+        for (long long p = 0; p < G.nn; p++)
+            if (t[p] == T_IN) ptr[p % G.n + (p / G.n) % G.n + p / ((long long)G.n * G.n) + 1]++;
+        for (int k = 0; k < nd; k++) ptr[k + 1] += ptr[k];
+        list.resize(ptr[nd] > 0 ? ptr[nd] : 1);
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (long long p = 0; p < G.nn; p++)
+            if (t[p] == T_IN) list[fill[p % G.n + (p / G.n) % G.n + p / ((long long)G.n * G.n)]++] = (int)p;
+        int* dl = (int*)d->mem.get(sizeof(int) * list.size());
+        int* dp = (int*)d->mem.get(sizeof(int) * (nd + 1));
+        if (!dl || !dp) return sulf_fail(SULF_ENOMEM, "out of device memory");
+        SULF_CUDA_TRY(cudaMemcpyAsync(dl, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, d->stream));
+        SULF_CUDA_TRY(cudaMemcpyAsync(dp, ptr.data(), sizeof(int) * (nd + 1), cudaMemcpyHostToDevice, d->stream));
+        SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+        G.lex = dl;
+        G.lexptr = dp;
+        G.nlexd = nd;
+    }
+    return SULF_OK;
+}
 
 int copy_in(sulf_domain* d, void* dst, const void* src, size_t n) {
     SULF_CUDA_TRY(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, d->stream));
@@ -903,13 +982,16 @@ int sulf_set_model(sulf_handle h, const sulf_model* m) {
 int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
     if (!valid(h)) return sulf_fail(SULF_EINVAL, "invalid handle");
     sulf_solver v = s ? *s : default_solver();
-    if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || (v.cycle != 1 && v.cycle != 2) || v.max_newton < 1 ||
+    if (v.nu1 < 0 || v.nu2 < 0 || v.nu1 + v.nu2 < 1 || v.cycle < 1 || v.cycle > 3 || v.max_newton < 1 ||
         v.max_cycles < 1 || v.ghost_sweeps < 1 || !(v.tau_s > 0 && v.tau_s < 1) || !(v.newton_tol > 0) ||
-        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || (v.smoother != 0 && v.smoother != 1) || (v.graphs != 0 && v.graphs != 1) || v.fuse_below < -1 ||
+        !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || v.smoother < 0 || v.smoother > 2 ||
+        (v.graphs != 0 && v.graphs != 1) || v.fuse_below < -1 ||
         (v.pdl != 0 && v.pdl != 1) || (v.ghost_compose != 0 && v.ghost_compose != 1))
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
     if (int rc = refresh_ghost_ops(h)) return rc;
+    if (v.smoother == 2)
+        if (int rc = ensure_lex(h)) return rc;
     if (v.precision == 1) return ensure32(h);
     return SULF_OK;
 }
@@ -1287,6 +1369,144 @@ int sulf_dbg_coarsest_solve(sulf_handle h, double dt, const double* Wc0, const d
     else
         h->launches += launch_coarsest_solve<3, double>(h->geo[lc], h->v64[lc], h->stream);
     return dbg_copy_out(h, lc, h->v64[lc].x, x_c, false);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuning of the controls that change only speed: the fused-level
+// threshold, the composed ghost relaxation and dependent launch.  A candidate
+// is timed on the handle's own problem -- the Newton system of a CN step of
+// size dt from the current state -- as a linear solve of a fixed number of
+// cycles (the defect test is off), once to build its graphs and once timed.
+// The state is not changed.  Results are kept per problem class for the
+// process, so same-size instances of a batch tune once.
+namespace {
+
+typedef std::array<int, 9> TuneKey;  // dim, N, coarsest N, precision, cycle, smoother, nu1, nu2, bc
+std::mutex g_tune_mu;
+std::map<TuneKey, sulf_tune_result> g_tune_cache;
+
+TuneKey tune_key(const sulf_domain* d) {
+    return {d->dim, d->N, d->N >> (d->L - 1), d->solver.precision, d->solver.cycle, d->solver.smoother,
+            d->solver.nu1, d->solver.nu2, d->bc};
+}
+
+// ms per cycle of the current controls (the fixed set-up of the solve --
+// injection, coefficients, coarsest inverse -- is included, as in a step)
+template <int D>
+int time_solve(sulf_domain* d, double fnorm, int ncycles, double* ms) {
+    PdlScope pdl(d->solver.pdl != 0);
+    int c = linear_solve<D>(d, fnorm, ncycles, 0.0, nullptr);  // builds the graphs of this candidate
+    if (c < 0) return c;
+    SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+    const double t0 = host_ms();
+    c = linear_solve<D>(d, fnorm, ncycles, 0.0, nullptr);
+    if (c < 0) return c;
+    SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+    *ms = (host_ms() - t0) / ncycles;
+    return SULF_OK;
+}
+
+template <int D>
+int autotune(sulf_domain* d, double dt, sulf_tune_result* out) {
+    const LevelGeo& G0 = d->geo[0];
+    d->dt = dt;
+    FConst fc = make_fconst(d);
+    SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, d->stream));
+    d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, d->stream);
+    SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, d->stream));
+    d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm, d->stream);
+    if (int rc = read_norms(d, 1)) return rc;
+    double fn = bits_to_double(d->hnorm[0]);
+    if (!(fn > 0)) fn = 1.0;
+    const sulf_solver base = d->solver;
+    const int ncyc = 6;
+    auto trial = [&](int fuse, int compose, int pdl, double* ms) {
+        d->solver = base;
+        d->solver.fuse_below = fuse;
+        d->solver.ghost_compose = compose;
+        d->solver.pdl = pdl;
+        if (int rc = refresh_ghost_ops(d)) return rc;
+        return time_solve<D>(d, fn, ncyc, ms);
+    };
+    sulf_tune_result r{};
+    double best = 0;
+    if (int rc = trial(-1, 1, 1, &best)) return rc;
+    r.ms_per_cycle_default = best;
+    r.fuse_below = -1;
+    r.ghost_compose = 1;
+    r.pdl = 1;
+    r.candidates = 1;
+    // the fused-level threshold (only V-cycles with red-black sweeps fuse)
+    if (base.cycle == 1 && base.smoother != 2) {
+        const int fuse[] = {0, 60, 150, 400, 1000, 3000, 10000};
+        for (int f : fuse) {
+            double ms = 0;
+            if (int rc = trial(f, 1, 1, &ms)) return rc;
+            r.candidates++;
+            if (ms < best) {
+                best = ms;
+                r.fuse_below = f;
+            }
+        }
+    }
+    for (int compose = 0; compose < 2; compose++)
+        for (int pdl = 0; pdl < 2; pdl++) {
+            if (compose == 1 && pdl == 1) continue;
+            double ms = 0;
+            if (int rc = trial(r.fuse_below, compose, pdl, &ms)) return rc;
+            r.candidates++;
+            if (ms < best) {
+                best = ms;
+                r.ghost_compose = compose;
+                r.pdl = pdl;
+            }
+        }
+    r.ms_per_cycle = best;
+    d->solver = base;
+    d->solver.fuse_below = r.fuse_below;
+    d->solver.ghost_compose = r.ghost_compose;
+    d->solver.pdl = r.pdl;
+    if (int rc = refresh_ghost_ops(d)) return rc;
+    *out = r;
+    return SULF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sulf_autotune(sulf_handle h, double dt, int use_cache, sulf_tune_result* out) {
+    if (!valid(h) || !(dt > 0)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    const TuneKey key = tune_key(h);
+    sulf_tune_result r{};
+    bool hit = false;
+    if (use_cache) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            r = it->second;
+            r.cached = 1;
+            hit = true;
+        }
+    }
+    if (hit) {
+        h->solver.fuse_below = r.fuse_below;
+        h->solver.ghost_compose = r.ghost_compose;
+        h->solver.pdl = r.pdl;
+        if (int rc = refresh_ghost_ops(h)) return rc;
+    } else {
+        const double dt0 = h->dt;
+        int rc = h->dim == 2 ? autotune<2>(h, dt, &r) : autotune<3>(h, dt, &r);
+        h->dt = dt0;
+        cudaStreamSynchronize(h->stream);
+        if (rc) return rc;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = r;
+    }
+    if (out) *out = r;
+    return SULF_OK;
 }
 
 int sulf_dbg_cycles(sulf_handle h, double dt, const double* Wc0, const double* rhs, double* x, int ncycles,

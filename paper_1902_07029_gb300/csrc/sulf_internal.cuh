@@ -95,6 +95,12 @@ struct LevelGeo {
     bool gop_on = false;
     double gop_tau = 0;
     int gop_passes = 0, gop_bc = -1;
+    // lexicographic smoother (built on first use): the inside nodes ordered by
+    // the index sum i+j(+k) (a wavefront), then box order; lexptr[d] is the
+    // first position of wavefront d, nlexd wavefronts
+    int* lex = nullptr;
+    int* lexptr = nullptr;
+    int nlexd = 0;
     int nact = 0;            // coarsest level: active list and map
     int* act = nullptr;
     int* apos = nullptr;
@@ -186,6 +192,12 @@ int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cuda
 template <int D, typename T>
 int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, int colour, bool pointwise,
                         T* snap, cudaStream_t s);
+// one lexicographic collective Gauss-Seidel sweep over the inside nodes,
+// wavefront by wavefront in one CTA (nodes of a wavefront do not couple; its
+// lower neighbours are already updated, its upper ones not: exactly the box
+// order of a lexicographic sweep); snap as in launch_relax_inside
+template <int D, typename T>
+int launch_relax_lex(const LevelGeo& L, const LevelVec<T>& V, T* snap, cudaStream_t s);
 // the ghost relaxation of one sweep: the composed map when `composed` (the
 // caller checked ghost_op_ready and had the preceding inside launch copy the
 // ghosts' s into V.gbuf[0]), else pass by pass

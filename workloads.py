@@ -94,15 +94,26 @@ def paper_test2(N: int, lo: float = -2.0, hi: float = 2.0) -> np.ndarray:
 
 
 # The workloads the library is measured on.  N counts intervals per axis, so
-# "1025^2 nodes" is N = 1024.  dt = h on [-1, 1] means dt = 2 / N.  coarsest is
-# the N of the coarsest multigrid level: 4 in 3-D keeps the dense direct solve
-# there at 2 x 81 unknowns (a 9^3 coarsest box of the rounded box has ~600
-# active nodes, whose dense FP64 factorisation per Newton iteration costs more
-# than the cycles).
+# "1025^2 nodes" is N = 1024.  dt = dt_factor * h on [-1, 1], h = 2 / N.
+# coarsest is the N of the coarsest multigrid level: 4 in 3-D keeps the dense
+# direct solve there at 2 x 81 unknowns (a 9^3 coarsest box of the rounded box
+# has ~600 active nodes, whose dense FP64 factorisation per Newton iteration
+# costs more than the cycles).  The 65^2 disk has no discrete solution at its
+# second step with dt = h (the ghost c-equation loses its real roots), so it
+# runs with dt = h/4.  oracle_step_s_estimate: seconds one CN step of the CPU
+# oracle takes (one core of the build host); oracle_cycles_per_step: multigrid
+# cycles the oracle counted on the workload's first CN step (used to scale a
+# sampled oracle cycle to a step where a step is too long to time).
 WORKLOADS = {
-    "disk65": dict(dim=2, N=64, coarsest=8, geometry="disk", steps=10, precision="fp64"),
-    "star1025": dict(dim=2, N=1024, coarsest=8, geometry="star", steps=200, precision="fp64"),
-    "rbox257": dict(dim=3, N=256, coarsest=4, geometry="rounded_box", steps=50, precision="fp64"),
+    "disk65": dict(dim=2, N=64, coarsest=8, geometry="disk", steps=10, precision="fp64", dt_factor=0.25,
+                   oracle_step_s_estimate=0.05),
+    "star1025": dict(dim=2, N=1024, coarsest=8, geometry="star", steps=200, precision="fp64", dt_factor=1.0,
+                     oracle_step_s_estimate=2.4),
+    "rbox257": dict(dim=3, N=256, coarsest=4, geometry="rounded_box", steps=50, precision="fp64", dt_factor=1.0,
+                    oracle_step_s_estimate=225.0, oracle_cycles_per_step=55),
+    # the same box at half the resolution: parity tests and small profiles
+    "rbox129": dict(dim=3, N=128, coarsest=4, geometry="rounded_box", steps=50, precision="fp64", dt_factor=1.0,
+                    oracle_step_s_estimate=38.0, oracle_cycles_per_step=59),
 }
 
 
