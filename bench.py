@@ -570,7 +570,8 @@ def run_batch(args):
                 tuned = {}
                 for N, r in zip(sizes, res):
                     if N not in tuned or not r["cached"]:
-                        tuned[N] = {kk: r[kk] for kk in ("fuse_below", "ghost_compose", "pdl", "ms_per_cycle",
+                        tuned[N] = {kk: r[kk] for kk in ("fuse_below", "ghost_compose", "pdl", "relax_occupancy",
+                                                          "ms_per_cycle",
                                                           "ms_per_cycle_default")}
             b.step(dts, 1)  # warm-up: graphs
             for i, d in enumerate(doms):

@@ -27,11 +27,14 @@ using stages::make_lists;
 
 namespace {
 thread_local bool t_pdl = false;
+thread_local int t_occ = 0;
 thread_local std::string t_launch_err;
 }  // namespace
 
 void set_launch_pdl(bool on) { t_pdl = on; }
 bool launch_pdl() { return t_pdl; }
+void set_launch_occupancy(int occ) { t_occ = occ; }
+int launch_occupancy() { return t_occ; }
 
 void note_launch_error(cudaError_t e, unsigned grid, unsigned block, size_t smem) {
     if (!t_launch_err.empty()) return;
@@ -134,7 +137,8 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
     int kind, gi = 0;
     long long p = list_node(ls, t, kind, gi);
     const long long st[3] = {1, n, (long long)n * n};
-    int ii[3] = {(int)(p % n), (int)((p / n) % n), D == 3 ? (int)(p / ((long long)n * n)) : 0};
+    int ii[3];
+    stages::box_coords<D>(p, n, ii);
     T2* edge[3] = {e0, e1, e2};
     T2 w = Wc[p];
     T s = w.x, cp = w.y;
@@ -190,8 +194,12 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
 
 // one colour of inside nodes; with snap_n > 0 also the copy of the ghosts' s
 // (nodes sidx) into snap that the composed ghost relaxation starts from
-template <int D, typename T, bool PW>
-__global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
+// HO: the register budget is set for five resident CTAs per SM instead of
+// the four that the FP64 update's 52 registers (prefetched coefficients)
+// allow: more warps to hide the load latency, at the price of a few spilled
+// values (sulf_solver::relax_occupancy; FP32 runs eight CTAs either way)
+template <int D, typename T, bool PW, bool HO>
+__global__ void __launch_bounds__(kT, HO ? 5 : 1) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
                                                       const typename V2<T>::t* __restrict__ rhs,
                                                       typename V2<T>::t* __restrict__ x, long long st1, long long st2,
                                                       const int* __restrict__ sidx, int snap_n, T* snap) {
@@ -434,10 +442,8 @@ __global__ void __launch_bounds__(kT) k_inject(Lists ls, int cn, const int8_t* _
     if (t >= ls.n0 + ls.n1 + ls.ng) return;
     int kind, gi;
     long long I = list_node(ls, t, kind, gi);
-    int ii[3] = {0, 0, 0};
-    ii[0] = (int)(I % cn);
-    ii[1] = (int)((I / cn) % cn);
-    if (D == 3) ii[2] = (int)(I / ((long long)cn * cn));
+    int ii[3];
+    stages::box_coords<D>(I, cn, ii);
     long long fst[3] = {1, fn, (long long)fn * fn};
     long long f = 0;
 #pragma unroll
@@ -1026,10 +1032,12 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
     (void)c;
     CoefPtr<D, T> cf = coef_ptr<D, T>(V);
     if (pointwise)
-        launch_k(k_relax_inside<D, T, true>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
+        launch_k(k_relax_inside<D, T, true, false>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
                  V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     else
-        launch_k(k_relax_inside<D, T, false>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
+        launch_k(std::is_same<T, double>::value && launch_occupancy() ? k_relax_inside<D, T, false, true>
+                                                                       : k_relax_inside<D, T, false, false>,
+                 grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
                  V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     return 1;
 }

@@ -19,6 +19,24 @@ __device__ __forceinline__ V ldx(const V* p) {
     return *p;
 }
 
+// box coordinates of node p on a grid of n nodes per axis: node indices fit
+// in 32 bits, and unsigned 32-bit division costs a small fraction of the
+// 64-bit one
+template <int D>
+__device__ __forceinline__ void box_coords(long long p, int n, int* ii) {
+    const unsigned u = (unsigned)p, un = (unsigned)n;
+    const unsigned q = u / un;
+    ii[0] = (int)(u - q * un);
+    if (D == 3) {
+        const unsigned r = q / un;
+        ii[1] = (int)(q - r * un);
+        ii[2] = (int)r;
+    } else {
+        ii[1] = (int)q;
+        ii[2] = 0;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ unsigned long long abs_bits(T v) {
     double d = fabs((double)v);
@@ -526,10 +544,8 @@ __device__ __forceinline__ RestrictGeo<D, T> fetch_restrict(int t, const Lists& 
     g.I = list_node(ls, t, kind, gi);
     const long long I = g.I;
     int8_t rule = ctype[I];
-    int ii[3] = {0, 0, 0};
-    ii[0] = (int)(I % cn);
-    ii[1] = (int)((I / cn) % cn);
-    if (D == 3) ii[2] = (int)(I / ((long long)cn * cn));
+    int ii[3];
+    box_coords<D>(I, cn, ii);
     const long long fst[3] = {1, fn, (long long)fn * fn};
     long long f = 0;
 #pragma unroll
@@ -685,10 +701,8 @@ __device__ __forceinline__ ProlongGeo<D, T> fetch_prolong(int t, const Lists& ls
     int kind, gi;
     g.i = list_node(ls, t, kind, gi);
     const long long i = g.i;
-    int ii[3] = {0, 0, 0};
-    ii[0] = (int)(i % fn);
-    ii[1] = (int)((i / fn) % fn);
-    if (D == 3) ii[2] = (int)(i / ((long long)fn * fn));
+    int ii[3];
+    box_coords<D>(i, fn, ii);
     const long long cst[3] = {1, cn, (long long)cn * cn};
     g.use = 0;
     const int NC = 1 << D;

@@ -291,6 +291,10 @@ __device__ __forceinline__ void pdl_enter() {
 // switches it per call from sulf_solver::pdl)
 void set_launch_pdl(bool on);
 bool launch_pdl();
+// the FP64 inside relaxation's register budget (sulf_solver::relax_occupancy)
+// for launches made by the calling thread
+void set_launch_occupancy(int occ);
+int launch_occupancy();
 
 // the first failed launch of the calling thread is remembered (a failed launch
 // inside stream capture only surfaces later, as an invalidated capture) and

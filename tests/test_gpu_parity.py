@@ -220,7 +220,7 @@ def test_dependent_launch_is_bitwise_neutral(sulfmg, name, mk, precision):
     same with it on and off, with and without graphs"""
     phi, dim, N, cN, dt, nsteps = mk()
     out = []
-    for kw in (dict(pdl=1), dict(pdl=0), dict(pdl=1, graphs=0, fuse_below=0)):
+    for kw in (dict(pdl=1), dict(pdl=0), dict(pdl=1, graphs=0, fuse_below=0), dict(pdl=1, relax_occupancy=1)):
         dom = sulfmg.Domain(phi, dim, (-1.0, 1.0), N, coarsest_N=cN)
         dom.set_model(workloads.PAPER_MODEL)
         dom.set_solver(precision=precision, **kw)
@@ -228,6 +228,8 @@ def test_dependent_launch_is_bitwise_neutral(sulfmg, name, mk, precision):
         out.append(dom.get_state()[:2])
         dom.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    # the higher-occupancy build of the FP64 relaxation computes the same bits
+    assert np.array_equal(out[0][0], out[3][0]) and np.array_equal(out[0][1], out[3][1])
     # launched one by one, every level as separate kernels: same up to the
     # summation order of the coarsest solve
     for a, b in zip(out[0], out[2]):
