@@ -99,11 +99,16 @@ typedef struct {
    relax_occupancy 1 = the FP64 inside relaxation is compiled for five
                  resident CTAs per SM (a few spilled values) instead of four:
                  more warps hide the load latency; no effect in FP32.
-                 Same results either way.                          default 0 */
+                 Same results either way.                          default 0
+   relax_matrix_free 1 = the FP32 red-black collective relaxation of the
+                 mixed form recomputes each node's stencil coefficients from
+                 (s, c) instead of reading the stored ones (same expressions:
+                 fewer bytes per update, more FP32 arithmetic); no effect in
+                 FP64 or with the pointwise or lexicographic smoother.   default 0 */
 typedef struct {
     int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;
-    int precision, smoother, graphs, fuse_below, pdl, ghost_compose, relax_occupancy;
+    int precision, smoother, graphs, fuse_below, pdl, ghost_compose, relax_occupancy, relax_matrix_free;
 } sulf_solver;
 
 /* Counters and timings of the handle. */
@@ -273,13 +278,13 @@ int sulf_newton_residual_noalloc(sulf_handle h, double dt, const double* W_dev, 
 
 /* Autotuning of the solver controls that change only speed, not results
    beyond rounding order: fuse_below (the fused coarse-level threshold; only
-   for V-cycles with red-black sweeps), ghost_compose, pdl and
-   relax_occupancy.  Each candidate
+   for V-cycles with red-black sweeps), ghost_compose, pdl,
+   relax_occupancy and relax_matrix_free.  Each candidate
    is timed on this handle's own problem -- the Newton system of a CN step of
    size dt from the current state -- as a linear solve of 6 cycles (built
    once, then timed); the fused-level thresholds {0, 60, 150, 400, 1000, 3000,
    10000} are tried first, then ghost_compose and pdl at the best one, then
-   (FP64) relax_occupancy.  The
+   relax_occupancy (FP64) or relax_matrix_free (mixed precision).  The
    fastest candidate is written into the handle's solver controls (the state
    is unchanged).  With use_cache != 0 a result found earlier in this process
    for the same problem class (dim, N, coarsest N, precision, cycle, smoother,
@@ -287,6 +292,7 @@ int sulf_newton_residual_noalloc(sulf_handle h, double dt, const double* W_dev, 
 typedef struct {
     int fuse_below, ghost_compose, pdl; /* the chosen controls */
     int relax_occupancy;                /* (timed in FP64 only) */
+    int relax_matrix_free;              /* (timed in mixed precision only) */
     double ms_per_cycle;                /* their time per cycle */
     double ms_per_cycle_default;        /* the defaults' (fuse_below -1, ghost_compose 1, pdl 1) */
     int candidates;                     /* candidates timed */

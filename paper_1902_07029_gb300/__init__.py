@@ -27,7 +27,8 @@ class SulfSolver(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("ghost_sweeps", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("lin_rtol", ctypes.c_double), ("tau_s", ctypes.c_double), ("precision", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("graphs", ctypes.c_int), ("fuse_below", ctypes.c_int),
-                ("pdl", ctypes.c_int), ("ghost_compose", ctypes.c_int), ("relax_occupancy", ctypes.c_int)]
+                ("pdl", ctypes.c_int), ("ghost_compose", ctypes.c_int), ("relax_occupancy", ctypes.c_int),
+                ("relax_matrix_free", ctypes.c_int)]
 
 
 class SulfStats(ctypes.Structure):
@@ -53,7 +54,8 @@ class SulfJobResult(ctypes.Structure):
 
 class SulfTuneResult(ctypes.Structure):
     _fields_ = [("fuse_below", ctypes.c_int), ("ghost_compose", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("relax_occupancy", ctypes.c_int), ("ms_per_cycle", ctypes.c_double), ("ms_per_cycle_default", ctypes.c_double),
+                ("relax_occupancy", ctypes.c_int), ("relax_matrix_free", ctypes.c_int),
+                ("ms_per_cycle", ctypes.c_double), ("ms_per_cycle_default", ctypes.c_double),
                 ("candidates", ctypes.c_int), ("cached", ctypes.c_int)]
 
 
@@ -156,7 +158,7 @@ def _chk(lib, rc):
 def default_solver(**kw) -> SulfSolver:
     s = SulfSolver(nu1=2, nu2=2, cycle=1, max_newton=20, max_cycles=30, ghost_sweeps=4, newton_tol=1e-10,
                    lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1, fuse_below=-1, pdl=1,
-                   ghost_compose=1, relax_occupancy=0)
+                   ghost_compose=1, relax_occupancy=0, relax_matrix_free=0)
     for k, v in kw.items():
         setattr(s, k, v)
     return s

@@ -28,6 +28,7 @@ using stages::make_lists;
 namespace {
 thread_local bool t_pdl = false;
 thread_local int t_occ = 0;
+thread_local int t_mf = 0;
 thread_local std::string t_launch_err;
 }  // namespace
 
@@ -35,6 +36,8 @@ void set_launch_pdl(bool on) { t_pdl = on; }
 bool launch_pdl() { return t_pdl; }
 void set_launch_occupancy(int occ) { t_occ = occ; }
 int launch_occupancy() { return t_occ; }
+void set_launch_matrix_free(int mf) { t_mf = mf; }
+int launch_matrix_free() { return t_mf; }
 
 void note_launch_error(cudaError_t e, unsigned grid, unsigned block, size_t smem) {
     if (!t_launch_err.empty()) return;
@@ -242,6 +245,73 @@ __global__ void __launch_bounds__(kLexThreads) k_relax_lex(const int* __restrict
         __syncthreads();
     }
     for (int i = threadIdx.x; i < snap_n; i += blockDim.x) snap[i] = __ldcg(reinterpret_cast<const T*>(x + sidx[i]));
+}
+
+// FP32 collective update with the stencil coefficients recomputed from the
+// coefficient source Wc, with the expressions and summation order of k_coefs
+// (so the same numbers as the stored ones): FP32 arithmetic is plentiful on
+// this GPU while bytes are not, and per update this reads the (s, c) and x of
+// the node and its axis neighbours and the right-hand side -- no edge, block
+// or inverse arrays.  Wc is fixed during the linear solve, so the
+// coefficients are formed before the dependent-launch wait.
+template <int D>
+__global__ void __launch_bounds__(kT) k_relax_mf(const int* __restrict__ list, int cnt,
+                                                  const float2* __restrict__ Wc, const float2* __restrict__ rhs,
+                                                  float2* __restrict__ x, Coef<float> c, long long st1, long long st2,
+                                                  const int* __restrict__ sidx, int snap_n, float* snap) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long st[3] = {1, st1, st2};
+    long long p = 0;
+    float g[2 * D], e[2 * D];
+    float i00 = 0, i01 = 0, i10 = 0, i11 = 0;
+    if (t < cnt) {
+        p = list[t];
+        const float2 w = Wc[p];
+        const float s = w.x, cp = w.y;
+        const float ph = c.alpha * cp + c.beta;
+        float sg = 0, se = 0;
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+#pragma unroll
+            for (int dir = 0; dir < 2; dir++) {
+                const float2 wq = Wc[dir ? p - st[a] : p + st[a]];
+                const float gq = c.kap * ((c.alpha * wq.y + c.beta) + ph);
+                const float eq = c.kap * c.alpha * (s - wq.x);
+                g[2 * a + dir] = gq;
+                e[2 * a + dir] = eq;
+                sg += gq;
+                se += eq;
+            }
+        }
+        const float Pcs = c.a2ms * ph * cp;
+        const float Pcc = c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
+        const float Pss = ph * c.idt + c.a2mc * ph * cp + sg;
+        const float Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s) + se;
+        const float inv = 1.0f / (Pss * Pcc - Psc * Pcs);
+        i00 = Pcc * inv;
+        i01 = -Psc * inv;
+        i10 = -Pcs * inv;
+        i11 = Pss * inv;
+    }
+    const int sg = t < snap_n ? sidx[t] : 0;
+    pdl_enter();
+    if (t < snap_n) snap[t] = reinterpret_cast<const float*>(x + sg)[0];
+    if (t >= cnt) return;
+    const float2 b = rhs[p];
+    float r = b.x;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        const float2 xe = x[p + st[a]];
+        const float2 xw = x[p - st[a]];
+        r = __fmaf_rn(g[2 * a], xe.x, r);
+        r = __fmaf_rn(-e[2 * a], xe.y, r);
+        r = __fmaf_rn(g[2 * a + 1], xw.x, r);
+        r = __fmaf_rn(-e[2 * a + 1], xw.y, r);
+    }
+    float2 out;
+    out.x = __fmaf_rn(i00, r, i01 * b.y);
+    out.y = __fmaf_rn(i10, r, i11 * b.y);
+    x[p] = out;
 }
 
 // one Jacobi pass of the ghost relaxation of Eq. RelGhost over all ghosts
@@ -1029,8 +1099,22 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
     const int sn = snap ? L.ng : 0;
     const int tot = cnt > sn ? cnt : sn;
     if (tot == 0) return 0;
-    (void)c;
     CoefPtr<D, T> cf = coef_ptr<D, T>(V);
+    if (std::is_same<T, float>::value && !pointwise && launch_matrix_free()) {
+        Coef<float> cc;
+        cc.alpha = (float)c.alpha;
+        cc.beta = (float)c.beta;
+        cc.a2mc = (float)c.a2mc;
+        cc.a2ms = (float)c.a2ms;
+        cc.idt = (float)c.idt;
+        cc.kap = (float)c.kap;
+        cc.tau = (float)c.tau;
+        launch_k(k_relax_mf<D>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt,
+                 reinterpret_cast<const float2*>(V.Wc), reinterpret_cast<const float2*>(V.rhs),
+                 reinterpret_cast<float2*>(V.x), cc, L.st[1], L.st[2], L.gidx, sn,
+                 reinterpret_cast<float*>(snap));
+        return 1;
+    }
     if (pointwise)
         launch_k(k_relax_inside<D, T, true, false>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
                  V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);

@@ -175,6 +175,7 @@ sulf_solver default_solver() {
     s.pdl = 1;
     s.ghost_compose = 1;
     s.relax_occupancy = 0;
+    s.relax_matrix_free = 0;
     return s;
 }
 
@@ -495,7 +496,8 @@ bool same_solver(const sulf_solver& a, const sulf_solver& b) {
            a.max_cycles == b.max_cycles && a.ghost_sweeps == b.ghost_sweeps && a.newton_tol == b.newton_tol &&
            a.lin_rtol == b.lin_rtol && a.tau_s == b.tau_s && a.precision == b.precision && a.smoother == b.smoother &&
            a.graphs == b.graphs && a.fuse_below == b.fuse_below && a.pdl == b.pdl &&
-           a.ghost_compose == b.ghost_compose && a.relax_occupancy == b.relax_occupancy;
+           a.ghost_compose == b.ghost_compose && a.relax_occupancy == b.relax_occupancy &&
+           a.relax_matrix_free == b.relax_matrix_free;
 }
 
 // One cycle of the linear solve on the finest level, then the FP64 defect
@@ -643,14 +645,17 @@ int device_loop(sulf_domain* d, double fnorm, int max_cycles, double rtol, doubl
 // scope lives
 struct PdlScope {
     bool old;
-    int old_occ;
-    explicit PdlScope(bool on, int occ = 0) : old(launch_pdl()), old_occ(launch_occupancy()) {
+    int old_occ, old_mf;
+    explicit PdlScope(bool on, int occ = 0, int mf = 0)
+        : old(launch_pdl()), old_occ(launch_occupancy()), old_mf(launch_matrix_free()) {
         set_launch_pdl(on);
         set_launch_occupancy(occ);
+        set_launch_matrix_free(mf);
     }
     ~PdlScope() {
         set_launch_pdl(old);
         set_launch_occupancy(old_occ);
+        set_launch_matrix_free(old_mf);
     }
 };
 
@@ -995,7 +1000,7 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
         !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || v.smoother < 0 || v.smoother > 2 ||
         (v.graphs != 0 && v.graphs != 1) || v.fuse_below < -1 ||
         (v.pdl != 0 && v.pdl != 1) || (v.ghost_compose != 0 && v.ghost_compose != 1) ||
-        (v.relax_occupancy != 0 && v.relax_occupancy != 1))
+        (v.relax_occupancy != 0 && v.relax_occupancy != 1) || (v.relax_matrix_free != 0 && v.relax_matrix_free != 1))
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
     if (int rc = refresh_ghost_ops(h)) return rc;
@@ -1017,7 +1022,7 @@ int sulf_set_stream(sulf_handle h, void* stream) {
 int sulf_step(sulf_handle h, double dt, int nsteps) {
     if (!valid(h) || !(dt > 0) || nsteps < 0) return sulf_fail(SULF_EINVAL, "invalid arguments");
     h->dt = dt;
-    PdlScope pdl(h->solver.pdl != 0, h->solver.relax_occupancy);
+    PdlScope pdl(h->solver.pdl != 0, h->solver.relax_occupancy, h->solver.relax_matrix_free);
     for (int k = 0; k < nsteps; k++) {
         int rc = h->dim == 2 ? cn_step<2>(h) : cn_step<3>(h);
         if (rc) {
@@ -1405,7 +1410,7 @@ TuneKey tune_key(const sulf_domain* d) {
 // injection, coefficients, coarsest inverse -- is included, as in a step)
 template <int D>
 int time_solve(sulf_domain* d, double fnorm, int ncycles, double* ms) {
-    PdlScope pdl(d->solver.pdl != 0, d->solver.relax_occupancy);
+    PdlScope pdl(d->solver.pdl != 0, d->solver.relax_occupancy, d->solver.relax_matrix_free);
     int c = linear_solve<D>(d, fnorm, ncycles, 0.0, nullptr);  // builds the graphs of this candidate
     if (c < 0) return c;
     SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
@@ -1431,12 +1436,13 @@ int autotune(sulf_domain* d, double dt, sulf_tune_result* out) {
     if (!(fn > 0)) fn = 1.0;
     const sulf_solver base = d->solver;
     const int ncyc = 6;
-    auto trial = [&](int fuse, int compose, int pdl, double* ms, int occ = -1) {
+    auto trial = [&](int fuse, int compose, int pdl, double* ms, int occ = -1, int mf = -1) {
         d->solver = base;
         d->solver.fuse_below = fuse;
         d->solver.ghost_compose = compose;
         d->solver.pdl = pdl;
         d->solver.relax_occupancy = occ < 0 ? base.relax_occupancy : occ;
+        d->solver.relax_matrix_free = mf < 0 ? base.relax_matrix_free : mf;
         if (int rc = refresh_ghost_ops(d)) return rc;
         return time_solve<D>(d, fn, ncyc, ms);
     };
@@ -1474,6 +1480,7 @@ int autotune(sulf_domain* d, double dt, sulf_tune_result* out) {
             }
         }
     r.relax_occupancy = base.relax_occupancy;
+    r.relax_matrix_free = base.relax_matrix_free;
     if (base.precision == 0) {
         double ms = 0;
         const int occ = 1 - base.relax_occupancy;
@@ -1483,6 +1490,15 @@ int autotune(sulf_domain* d, double dt, sulf_tune_result* out) {
             best = ms;
             r.relax_occupancy = occ;
         }
+    } else if (base.smoother == 0) {
+        double ms = 0;
+        const int mf = 1 - base.relax_matrix_free;
+        if (int rc = trial(r.fuse_below, r.ghost_compose, r.pdl, &ms, -1, mf)) return rc;
+        r.candidates++;
+        if (ms < best) {
+            best = ms;
+            r.relax_matrix_free = mf;
+        }
     }
     r.ms_per_cycle = best;
     d->solver = base;
@@ -1490,6 +1506,7 @@ int autotune(sulf_domain* d, double dt, sulf_tune_result* out) {
     d->solver.ghost_compose = r.ghost_compose;
     d->solver.pdl = r.pdl;
     d->solver.relax_occupancy = r.relax_occupancy;
+    d->solver.relax_matrix_free = r.relax_matrix_free;
     if (int rc = refresh_ghost_ops(d)) return rc;
     *out = r;
     return SULF_OK;
@@ -1518,6 +1535,7 @@ int sulf_autotune(sulf_handle h, double dt, int use_cache, sulf_tune_result* out
         h->solver.ghost_compose = r.ghost_compose;
         h->solver.pdl = r.pdl;
         h->solver.relax_occupancy = r.relax_occupancy;
+        h->solver.relax_matrix_free = r.relax_matrix_free;
         if (int rc = refresh_ghost_ops(h)) return rc;
     } else {
         const double dt0 = h->dt;
@@ -1546,7 +1564,7 @@ int sulf_dbg_cycles(sulf_handle h, double dt, const double* Wc0, const double* r
     bool nonzero = false;
     for (double v : x0) nonzero |= v != 0.0;
     if (nonzero) return sulf_fail(SULF_EINVAL, "sulf_dbg_cycles starts from x = 0");
-    PdlScope pdl(h->solver.pdl != 0, h->solver.relax_occupancy);
+    PdlScope pdl(h->solver.pdl != 0, h->solver.relax_occupancy, h->solver.relax_matrix_free);
     int nc = h->dim == 2 ? linear_solve<2>(h, 1.0, ncycles, 0.0, rnorms) : linear_solve<3>(h, 1.0, ncycles, 0.0, rnorms);
     if (nc < 0) return nc;
     return dbg_copy_out(h, 0, h->v64[0].x, x, false);

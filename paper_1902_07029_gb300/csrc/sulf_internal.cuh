@@ -295,6 +295,10 @@ bool launch_pdl();
 // for launches made by the calling thread
 void set_launch_occupancy(int occ);
 int launch_occupancy();
+// FP32 inside relaxation with the coefficients recomputed from (s, c)
+// (sulf_solver::relax_matrix_free) for launches made by the calling thread
+void set_launch_matrix_free(int mf);
+int launch_matrix_free();
 
 // the first failed launch of the calling thread is remembered (a failed launch
 // inside stream capture only surfaces later, as an invalidated capture) and

@@ -234,3 +234,30 @@ def test_dependent_launch_is_bitwise_neutral(sulfmg, name, mk, precision):
     # summation order of the coarsest solve
     for a, b in zip(out[0], out[2]):
         assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(b)), 1.0)
+
+
+@pytest.mark.parametrize("name,mk", [RUNS[2], RUNS[4]], ids=[RUNS[2][0], RUNS[4][0]])
+def test_matrix_free_fp32_relaxation(sulfmg, oracle_mod, name, mk):
+    """the FP32 relaxation that recomputes its coefficients from (s, c) forms
+    the stored coefficients' numbers: the mixed-precision steps agree with the
+    stored-coefficient kernel and with the oracle (1e-8)"""
+    phi, dim, N, cN, dt, nsteps = mk()
+    out = []
+    for mf in (0, 1):
+        dom = sulfmg.Domain(phi, dim, (-1.0, 1.0), N, coarsest_N=cN)
+        dom.set_model(workloads.PAPER_MODEL)
+        dom.set_solver(precision=1, relax_matrix_free=mf)
+        dom.step(dt, nsteps)
+        out.append(dom.get_state())
+        dom.close()
+    ref = oracle_mod.Oracle(phi, dim, -1.0, 1.0, N, cN)
+    ref.set_model(workloads.PAPER_MODEL)
+    ref.set_solver()
+    ref.step(dt, nsteps)
+    rs, rc, rt = ref.get_state()
+    act = (rt == 1) | (rt == 2)
+    for s, c, _ in out:
+        _close(s[act], rs[act], MIXED_TOL)
+        _close(c[act], rc[act], MIXED_TOL)
+    _close(out[1][0][act], out[0][0][act], 1e-12)
+    _close(out[1][1][act], out[0][1][act], 1e-12)
