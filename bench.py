@@ -688,12 +688,15 @@ def run_serve(args):
     budget = int(args.budget_gb * 2 ** 30)
     cap = _serve_once(pkg, jobs, float("inf"), budget, args.streams, gaps)
     capacity = cap["jobs_per_s"]
-    rates = [f * capacity for f in (0.5, 1.0, 2.0)] if args.rate == "auto" else \
-        [float(r) for r in str(args.rate).split(",")]
-    runs = [_serve_once(pkg, jobs, r, budget, args.streams, gaps) for r in rates]
-    tight = _serve_once(pkg, jobs, rates[-1], int(args.tight_budget_gb * 2 ** 30), args.streams, gaps)
+    if args.no_sweep:
+        rates, runs, tight = [], [], None
+    else:
+        rates = [f * capacity for f in (0.5, 1.0, 2.0)] if args.rate == "auto" else \
+            [float(r) for r in str(args.rate).split(",")]
+        runs = [_serve_once(pkg, jobs, r, budget, args.streams, gaps) for r in rates]
+        tight = _serve_once(pkg, jobs, rates[-1], int(args.tight_budget_gb * 2 ** 30), args.streams, gaps)
     est = [pkg.estimate_device_bytes(dim, N, cN, 1) / 2 ** 30 for (_, dim, N, cN, _, _, _) in jobs]
-    r0 = runs[1] if len(runs) > 1 else runs[0]
+    r0 = runs[1] if len(runs) > 1 else (runs[0] if runs else cap)
     line = {"metric": "jobs/s and p50/p99 job latency", "value": r0["jobs_per_s"], "unit": "jobs/s",
             "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
@@ -767,6 +770,7 @@ def main():
     ap.add_argument("--max-steps", type=int, default=200, help="serve: CN steps per job uniform in 20..max")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: HBM budget")
     ap.add_argument("--tight-budget-gb", type=float, default=16.0, help="serve: budget of the admission run")
+    ap.add_argument("--no-sweep", action="store_true", help="serve: the saturated run only (every job at once)")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
                     help="both: the FP64 form as the headline and the mixed form beside it")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle CPU work for cpu_baseline")
