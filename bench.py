@@ -70,7 +70,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 CYCLE_BYTES = {2: 344.0 * 4 / 3, 3: 344.0 * 8 / 7}
 # DRAM bytes (read + write) of one finest-level relaxation launch from an ncu
 # capture of the current kernel (cold cache), per workload and precision
-RELAX_TRAFFIC = {}
+RELAX_TRAFFIC = {
+    # 129^3 capture (profiles/relax_inside_fp64_rbox129.md): 133.8 MB per
+    # 521 488 updates = 258 B per update, scaled to the 257^3 launch
+    ("rbox257", "fp64"): (258.0 * 4142122, "profiles/relax_inside_fp64_rbox129.md (258 B per update measured at "
+                                           "129^3, scaled to the 4 142 122 updates of a 257^3 launch)"),
+    ("star1025", "fp64"): (31.30e6 + 17.0e3, "profiles/relax_inside_fp64_star1025.md"),
+}
 
 
 def whole_job_value(elapsed_ms_local: float, units_local: int, device=None) -> tuple[float, float]:
