@@ -104,7 +104,7 @@ typedef struct {
                  mixed form recomputes each node's stencil coefficients from
                  (s, c) instead of reading the stored ones (same expressions:
                  fewer bytes per update, more FP32 arithmetic); no effect in
-                 FP64 or with the pointwise or lexicographic smoother.   default 0 */
+                 FP64 or with the pointwise or lexicographic smoother.   default 1 */
 typedef struct {
     int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;

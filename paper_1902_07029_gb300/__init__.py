@@ -158,7 +158,7 @@ def _chk(lib, rc):
 def default_solver(**kw) -> SulfSolver:
     s = SulfSolver(nu1=2, nu2=2, cycle=1, max_newton=20, max_cycles=30, ghost_sweeps=4, newton_tol=1e-10,
                    lin_rtol=1e-10, tau_s=0.9, precision=0, smoother=0, graphs=1, fuse_below=-1, pdl=1,
-                   ghost_compose=1, relax_occupancy=0, relax_matrix_free=0)
+                   ghost_compose=1, relax_occupancy=0, relax_matrix_free=1)
     for k, v in kw.items():
         setattr(s, k, v)
     return s

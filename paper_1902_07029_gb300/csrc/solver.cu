@@ -175,7 +175,7 @@ sulf_solver default_solver() {
     s.pdl = 1;
     s.ghost_compose = 1;
     s.relax_occupancy = 0;
-    s.relax_matrix_free = 0;
+    s.relax_matrix_free = 1;
     return s;
 }
 
