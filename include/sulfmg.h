@@ -103,8 +103,13 @@ typedef struct {
    relax_matrix_free 1 = the FP32 red-black collective relaxation of the
                  mixed form recomputes each node's stencil coefficients from
                  (s, c) instead of reading the stored ones (same expressions:
-                 fewer bytes per update, more FP32 arithmetic); no effect in
-                 FP64 or with the pointwise or lexicographic smoother.   default 1 */
+                 fewer bytes per update, more FP32 arithmetic); 2 = the same,
+                 and on 3-D levels with at least 100000 inside nodes both
+                 colours of a sweep run as one kernel temporally blocked in
+                 shared memory (32 x 8 x 16-node tiles streamed along z, the
+                 red ring around each tile recomputed; needs even nu1 and
+                 nu2); 0 = stored coefficients.  No effect in FP64 or with
+                 the pointwise or lexicographic smoother.            default 1 */
 typedef struct {
     int nu1, nu2, cycle, max_newton, max_cycles, ghost_sweeps;
     double newton_tol, lin_rtol, tau_s;

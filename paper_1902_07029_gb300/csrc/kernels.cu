@@ -314,6 +314,147 @@ __global__ void __launch_bounds__(kT) k_relax_mf(const int* __restrict__ list, i
     x[p] = out;
 }
 
+// ---------------------------------------------------------------------------
+// One whole red-black sweep of the FP32 collective smoother (both colours)
+// in one kernel, temporally blocked in shared memory (3-D levels of the mixed
+// form).  A CTA owns a tile of kTileX x kTileY nodes in (x, y) and kTileZ
+// planes in z, and streams through z with a four-plane ring in shared
+// memory: plane z+1 is staged (x, the coefficient source (s, c) and the node
+// types of the tile and a two-node halo), the red nodes of plane z are
+// updated over the tile and a one-node ring (the ring's updates, which the
+// neighbouring tile owns, are recomputed here from the old black values so
+// that no tile waits for another), then the black nodes of plane z-1 over
+// the tile from those red values.  The stencil coefficients are recomputed
+// from (s, c) with the expressions and order of k_relax_mf / k_coefs, so every
+// update equals the two colour launches'.  x is read from xin and written to
+// xout (a neighbour tile may still be reading the old values); ghosts are
+// copied across and their s also into snap (the composed ghost relaxation
+// starts from it).  Only inside nodes and ghosts of xout are defined after the
+// sweep, which is all that any later stage reads.
+constexpr int kTileX = 32, kTileY = 8, kTileZ = 16;
+constexpr int kTileRX = kTileX + 4, kTileRY = kTileY + 4, kTileRN = kTileRX * kTileRY;
+constexpr int kTileThreads = 256;
+
+// the collective update of the node at ring position r of slot sl, its
+// neighbour values in X (slots of planes z-1, z, z+1), coefficients from W
+__device__ __forceinline__ float2 tile_update(const float2 (*X)[kTileRN], const float2 (*W)[kTileRN], int sl, int r,
+                                              int zl, int zh, float2 b, const Coef<float>& c) {
+    const float2 w = W[sl][r];
+    const float s = w.x, cp = w.y;
+    const float ph = c.alpha * cp + c.beta;
+    // neighbours in the order +x, -x, +y, -y, +z, -z (as k_relax_mf)
+    const int ns[6] = {sl, sl, sl, sl, zh, zl};
+    const int nr[6] = {r + 1, r - 1, r + kTileRX, r - kTileRX, r, r};
+    float g[6], e[6];
+    float sg = 0, se = 0;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        const float2 wq = W[ns[q]][nr[q]];
+        g[q] = c.kap * ((c.alpha * wq.y + c.beta) + ph);
+        e[q] = c.kap * c.alpha * (s - wq.x);
+        sg += g[q];
+        se += e[q];
+    }
+    const float Pcs = c.a2ms * ph * cp;
+    const float Pcc = c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
+    const float Pss = ph * c.idt + c.a2mc * ph * cp + sg;
+    const float Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s) + se;
+    const float inv = 1.0f / (Pss * Pcc - Psc * Pcs);
+    float r_s = b.x;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        const float2 xq = X[ns[q]][nr[q]];
+        r_s = __fmaf_rn(g[q], xq.x, r_s);
+        r_s = __fmaf_rn(-e[q], xq.y, r_s);
+    }
+    float2 out;
+    out.x = __fmaf_rn(Pcc * inv, r_s, (-Psc * inv) * b.y);
+    out.y = __fmaf_rn(-Pcs * inv, r_s, (Pss * inv) * b.y);
+    return out;
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_sweep_tile(const int* __restrict__ tiles, int ntx, int nty, int n,
+                                                             const int8_t* __restrict__ type,
+                                                             const float2* __restrict__ Wc,
+                                                             const float2* __restrict__ rhs,
+                                                             const float2* __restrict__ xin, float2* __restrict__ xout,
+                                                             Coef<float> c, const int* __restrict__ gidx, int ng,
+                                                             float* snap) {
+    __shared__ float2 XO[4][kTileRN];
+    __shared__ float2 XR[4][kTileRN];
+    __shared__ float2 WS[4][kTileRN];
+    __shared__ int8_t TS[4][kTileRN];
+    const int tile = tiles[blockIdx.x];
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int X0 = tx * kTileX, Y0 = ty * kTileY, Z0 = tz * kTileZ;
+    const long long st1 = n, st2 = (long long)n * n;
+    pdl_enter();
+    // the ghosts: unchanged by the inside sweep, copied to xout (and their s
+    // to snap) by all CTAs together
+    for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += gridDim.x * blockDim.x) {
+        const int g = gidx[gi];
+        const float2 v = xin[g];
+        xout[g] = v;
+        if (snap) snap[gi] = v.x;
+    }
+    for (int z = Z0 - 3; z <= Z0 + kTileZ; z++) {
+        // stage plane z + 1 with its halo (outside the box: inactive)
+        {
+            const int zl = z + 1, sl = zl & 3;
+            for (int t = threadIdx.x; t < kTileRN; t += kTileThreads) {
+                const int gx = X0 - 2 + t % kTileRX, gy = Y0 - 2 + t / kTileRX;
+                float2 xo = make_float2(0.f, 0.f), wc = make_float2(0.f, 0.f);
+                int8_t ty8 = T_OUT;
+                if (zl >= 0 && zl < n && gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                    const long long p = gx + gy * st1 + zl * st2;
+                    ty8 = type[p];
+                    if (ty8 == T_IN || ty8 == T_GHOST) {
+                        xo = xin[p];
+                        wc = Wc[p];
+                    }
+                }
+                XO[sl][t] = xo;
+                WS[sl][t] = wc;
+                TS[sl][t] = ty8;
+            }
+        }
+        __syncthreads();
+        // red nodes of plane z over the tile and a one-node ring
+        if (z >= Z0 - 1) {
+            const int sl = z & 3, zl = (z - 1) & 3, zh = (z + 1) & 3;
+            for (int t = threadIdx.x; t < (kTileX + 2) * (kTileY + 2); t += kTileThreads) {
+                const int li = 1 + t % (kTileX + 2), lj = 1 + t / (kTileX + 2);
+                const int r = li + lj * kTileRX;
+                const int gx = X0 - 2 + li, gy = Y0 - 2 + lj;
+                float2 v = XO[sl][r];
+                if (TS[sl][r] == T_IN && ((gx + gy + z) & 1) == 0) {
+                    const long long p = gx + gy * st1 + z * st2;
+                    v = tile_update(XO, WS, sl, r, zl, zh, rhs[p], c);
+                }
+                XR[sl][r] = v;
+            }
+        }
+        __syncthreads();
+        // black nodes of plane z - 1 over the tile; the tile's inside nodes
+        // of that plane go to xout
+        const int zb = z - 1;
+        if (zb >= Z0 && zb < Z0 + kTileZ && zb < n) {
+            const int sl = zb & 3, zl = (zb - 1) & 3, zh = (zb + 1) & 3;
+            for (int t = threadIdx.x; t < kTileX * kTileY; t += kTileThreads) {
+                const int li = 2 + t % kTileX, lj = 2 + t / kTileX;
+                const int r = li + lj * kTileRX;
+                const int gx = X0 - 2 + li, gy = Y0 - 2 + lj;
+                if (gx >= n || gy >= n || TS[sl][r] != T_IN) continue;
+                const long long p = gx + gy * st1 + zb * st2;
+                float2 v = XR[sl][r];
+                if (((gx + gy + zb) & 1) == 1) v = tile_update(XR, WS, sl, r, zl, zh, rhs[p], c);
+                xout[p] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // one Jacobi pass of the ghost relaxation of Eq. RelGhost over all ghosts
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_ghost_pass(const int* __restrict__ gidx, GhostTab<T> tb,
@@ -1132,6 +1273,14 @@ int launch_relax_lex(const LevelGeo& L, const LevelVec<T>& V, T* snap, cudaStrea
     const int sn = snap ? L.ng : 0;
     launch_k(k_relax_lex<D, T>, 1, kLexThreads, 0, s, L.lex, L.lexptr, L.nlexd, coef_ptr<D, T>(V), V.rhs, V.x,
              L.st[1], L.st[2], L.gidx, sn, snap);
+    return 1;
+}
+
+int launch_sweep_tiled(const LevelGeo& L, const float2* Wc, const float2* rhs, const float2* xin, float2* xout,
+                       const Coef<float>& c, float* snap, cudaStream_t s) {
+    if (!L.tiles || L.ntiles == 0) return 0;
+    launch_k(k_sweep_tile, (unsigned)L.ntiles, kTileThreads, 0, s, L.tiles, L.tile_nx, L.tile_ny, L.n, L.type, Wc, rhs,
+             xin, xout, c, L.gidx, L.ng, snap);
     return 1;
 }
 

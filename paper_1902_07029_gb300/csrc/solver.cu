@@ -368,6 +368,17 @@ int refresh_ghost_ops(sulf_domain* d) {
     return SULF_OK;
 }
 
+// levels (3-D, FP32 cycles) whose red-black sweeps run as one temporally
+// blocked kernel (sulf_solver::relax_matrix_free = 2): those with at least
+// kTileMinInside inside nodes; the sweep writes the other unknown buffer, so
+// it needs an even number of sweeps per relaxation (nu1, nu2 even)
+constexpr long long kTileMinInside = 100000;
+bool tiled_level(const sulf_domain* d, int l) {
+    const LevelGeo& G = d->geo[l];
+    return d->solver.relax_matrix_free == 2 && d->solver.precision == 1 && d->solver.smoother == 0 && G.dim == 3 &&
+           d->solver.nu1 % 2 == 0 && d->solver.nu2 % 2 == 0 && G.tiles != nullptr && d->v32[l].x2 != nullptr;
+}
+
 // ---- multigrid on precision T ----
 template <int D, typename T>
 struct MG {
@@ -391,7 +402,21 @@ struct MG {
         // external flag makes it an event-record node of the graph)
         const unsigned fl = d->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (timed_sweep) cudaEventRecordWithFlags(next_event(d), d->stream, fl);
-        if (d->solver.smoother == 2)
+        if (std::is_same<T, float>::value && !skip_red && tiled_level(d, l)) {
+            // both colours in one temporally blocked launch into the other
+            // buffer, which then becomes the level's unknown
+            LevelVec<float>& U = reinterpret_cast<LevelVec<float>&>(V[l]);
+            Coef<float> cf;
+            cf.alpha = (float)c.alpha;
+            cf.beta = (float)c.beta;
+            cf.a2mc = (float)c.a2mc;
+            cf.a2ms = (float)c.a2ms;
+            cf.idt = (float)c.idt;
+            cf.kap = (float)c.kap;
+            cf.tau = (float)c.tau;
+            d->launches += launch_sweep_tiled(G, U.Wc, U.rhs, U.x, U.x2, cf, gop ? U.gbuf[0] : nullptr, d->stream);
+            std::swap(U.x, U.x2);
+        } else if (d->solver.smoother == 2)
             d->launches += launch_relax_lex<D, T>(G, V[l], gop ? V[l].gbuf[0] : nullptr, d->stream);
         else
             for (int colour = skip_red ? 1 : 0; colour < 2; colour++)
@@ -433,7 +458,8 @@ struct MG {
         // half-sweep (which would read only zeros)
         const int lc = l + 1;
         const bool fused_tail = lc == tail_level(d) && d->tail_ready[p] && d->solver.cycle == 1;
-        const bool fr = d->solver.nu1 >= 1 && lc < d->L - 1 && !fused_tail && d->solver.smoother != 2;
+        const bool fr = d->solver.nu1 >= 1 && lc < d->L - 1 && !fused_tail && d->solver.smoother != 2 &&
+                        !(std::is_same<T, float>::value && tiled_level(d, lc));
         d->launches += launch_restrict<D, T>(d->geo[l], V[l], d->geo[lc], V[lc], fr, d->solver.smoother == 1,
                                              d->stream);
         int gam = d->solver.cycle == 2 ? 2 : 1;
@@ -817,6 +843,42 @@ int cn_step(sulf_domain* d) {
 
 bool valid(sulf_handle h) { return h != nullptr; }
 
+// tile lists of the temporally blocked sweep (tiles holding an inside node)
+// and the second unknown buffer, for the 3-D levels with enough inside nodes
+int ensure_tiles(sulf_domain* d) {
+    if (d->dim != 3 || !d->have32) return SULF_OK;
+    for (int l = 0; l < d->L; l++) {
+        LevelGeo& G = d->geo[l];
+        if (G.tiles || (long long)G.nin[0] + G.nin[1] < kTileMinInside) continue;
+        std::vector<int8_t> t(G.nn);
+        SULF_CUDA_TRY(cudaMemcpyAsync(t.data(), G.type, G.nn, cudaMemcpyDeviceToHost, d->stream));
+        SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+        const int tx = 32, ty = 8, tz = 16;  // the kernel's tile (kTileX, kTileY, kTileZ)
+        const int nx = (G.n + tx - 1) / tx, ny = (G.n + ty - 1) / ty, nz = (G.n + tz - 1) / tz;
+        std::vector<char> has((size_t)nx * ny * nz, 0);
+        for (long long p = 0; p < G.nn; p++)
+            if (t[p] == T_IN) {
+                const int i = (int)(p % G.n), j = (int)((p / G.n) % G.n), k = (int)(p / ((long long)G.n * G.n));
+                has[((size_t)(k / tz) * ny + j / ty) * nx + i / tx] = 1;
+            }
+        std::vector<int> list;
+        for (size_t q = 0; q < has.size(); q++)
+            if (has[q]) list.push_back((int)q);
+        int* dl = (int*)d->mem.get(sizeof(int) * (list.size() + 1));
+        float2* x2 = (float2*)d->mem.get(sizeof(float2) * G.nn);
+        if (!dl || !x2) return sulf_fail(SULF_ENOMEM, "out of device memory");
+        SULF_CUDA_TRY(cudaMemcpyAsync(dl, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, d->stream));
+        SULF_CUDA_TRY(cudaMemsetAsync(x2, 0, sizeof(float2) * G.nn, d->stream));
+        SULF_CUDA_TRY(cudaStreamSynchronize(d->stream));
+        G.tiles = dl;
+        G.ntiles = (int)list.size();
+        G.tile_nx = nx;
+        G.tile_ny = ny;
+        d->v32[l].x2 = x2;
+    }
+    return SULF_OK;
+}
+
 // wavefront lists of the lexicographic smoother, built once per level on the
 // host from the node types: inside nodes ordered by i+j(+k), then box order
 int ensure_lex(sulf_domain* d) {
@@ -1000,13 +1062,16 @@ int sulf_set_solver(sulf_handle h, const sulf_solver* s) {
         !(v.lin_rtol > 0) || (v.precision != 0 && v.precision != 1) || v.smoother < 0 || v.smoother > 2 ||
         (v.graphs != 0 && v.graphs != 1) || v.fuse_below < -1 ||
         (v.pdl != 0 && v.pdl != 1) || (v.ghost_compose != 0 && v.ghost_compose != 1) ||
-        (v.relax_occupancy != 0 && v.relax_occupancy != 1) || (v.relax_matrix_free != 0 && v.relax_matrix_free != 1))
+        (v.relax_occupancy != 0 && v.relax_occupancy != 1) || v.relax_matrix_free < 0 || v.relax_matrix_free > 2)
         return sulf_fail(SULF_EINVAL, "solver controls out of range");
     h->solver = v;
     if (int rc = refresh_ghost_ops(h)) return rc;
     if (v.smoother == 2)
         if (int rc = ensure_lex(h)) return rc;
-    if (v.precision == 1) return ensure32(h);
+    if (v.precision == 1) {
+        if (int rc = ensure32(h)) return rc;
+        if (v.relax_matrix_free == 2) return ensure_tiles(h);
+    }
     return SULF_OK;
 }
 
@@ -1491,13 +1556,17 @@ int autotune(sulf_domain* d, double dt, sulf_tune_result* out) {
             r.relax_occupancy = occ;
         }
     } else if (base.smoother == 0) {
-        double ms = 0;
-        const int mf = 1 - base.relax_matrix_free;
-        if (int rc = trial(r.fuse_below, r.ghost_compose, r.pdl, &ms, -1, mf)) return rc;
-        r.candidates++;
-        if (ms < best) {
-            best = ms;
-            r.relax_matrix_free = mf;
+        for (int mf = 0; mf <= (d->dim == 3 ? 2 : 1); mf++) {
+            if (mf == base.relax_matrix_free) continue;
+            if (mf == 2)
+                if (int rc = ensure_tiles(d)) return rc;
+            double ms = 0;
+            if (int rc = trial(r.fuse_below, r.ghost_compose, r.pdl, &ms, -1, mf)) return rc;
+            r.candidates++;
+            if (ms < best) {
+                best = ms;
+                r.relax_matrix_free = mf;
+            }
         }
     }
     r.ms_per_cycle = best;
@@ -1536,6 +1605,8 @@ int sulf_autotune(sulf_handle h, double dt, int use_cache, sulf_tune_result* out
         h->solver.pdl = r.pdl;
         h->solver.relax_occupancy = r.relax_occupancy;
         h->solver.relax_matrix_free = r.relax_matrix_free;
+        if (r.relax_matrix_free == 2 && h->solver.precision == 1)
+            if (int rc = ensure_tiles(h)) return rc;
         if (int rc = refresh_ghost_ops(h)) return rc;
     } else {
         const double dt0 = h->dt;

@@ -101,6 +101,10 @@ struct LevelGeo {
     int* lex = nullptr;
     int* lexptr = nullptr;
     int nlexd = 0;
+    // tiles of the temporally blocked FP32 sweep (3-D): ids ((tz * tile_ny) +
+    // ty) * tile_nx + tx of the 32 x 8 x 16 tiles that hold an inside node
+    int* tiles = nullptr;
+    int ntiles = 0, tile_nx = 0, tile_ny = 0;
     int nact = 0;            // coarsest level: active list and map
     int* act = nullptr;
     int* apos = nullptr;
@@ -116,6 +120,7 @@ struct LevelVec {
     T2* x = nullptr;    // unknown: Newton update (finest) or coarse-grid error
     T2* res = nullptr;  // defect rhs - J x (band entries: extended defect)
     T* gbuf[2] = {nullptr, nullptr};   // ghost s values between relaxation passes
+    T2* x2 = nullptr;   // the other unknown buffer of the tiled sweep (which writes one while reading the other)
     T* Ainv = nullptr;  // coarsest level: inverse of the assembled Jacobian
     T* A = nullptr;     // coarsest level: work matrix
     // Jacobian stencil coefficients, refreshed once per Newton iteration from
@@ -198,6 +203,12 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
 // order of a lexicographic sweep); snap as in launch_relax_inside
 template <int D, typename T>
 int launch_relax_lex(const LevelGeo& L, const LevelVec<T>& V, T* snap, cudaStream_t s);
+// one red-black sweep of the FP32 collective smoother (both colours,
+// stencil coefficients from (s, c)) over the level's tiles, temporally
+// blocked in shared memory (3-D): reads xin, writes xout at the inside nodes
+// and ghosts; snap as in launch_relax_inside
+int launch_sweep_tiled(const LevelGeo& L, const float2* Wc, const float2* rhs, const float2* xin, float2* xout,
+                       const Coef<float>& c, float* snap, cudaStream_t s);
 // the ghost relaxation of one sweep: the composed map when `composed` (the
 // caller checked ghost_op_ready and had the preceding inside launch copy the
 // ghosts' s into V.gbuf[0]), else pass by pass

@@ -261,3 +261,34 @@ def test_matrix_free_fp32_relaxation(sulfmg, oracle_mod, name, mk):
         _close(c[act], rc[act], MIXED_TOL)
     _close(out[1][0][act], out[0][0][act], 1e-12)
     _close(out[1][1][act], out[0][1][act], 1e-12)
+
+
+def test_tiled_fp32_sweep(sulfmg, oracle_mod):
+    """the temporally blocked FP32 sweep (both colours in one kernel, 3-D
+    levels with >= 100k inside nodes) gives the two colour launches' numbers:
+    the mixed-precision steps agree with the per-colour matrix-free kernel
+    and with the oracle (1e-8)"""
+    N, cN = 64, 4
+    phi = workloads.rounded_box(N)
+    dt = 0.25 * 2.0 / N
+    out, cyc = [], []
+    for mf in (1, 2):
+        dom = sulfmg.Domain(phi, 3, (-1.0, 1.0), N, coarsest_N=cN)
+        dom.set_model(workloads.PAPER_MODEL)
+        dom.set_solver(precision=1, relax_matrix_free=mf)
+        dom.step(dt, 2)
+        out.append(dom.get_state())
+        cyc.append(dom.stats()["cycles_total"])
+        dom.close()
+    ref = oracle_mod.Oracle(phi, 3, -1.0, 1.0, N, cN)
+    ref.set_model(workloads.PAPER_MODEL)
+    ref.set_solver()
+    ref.step(dt, 2)
+    rs, rc, rt = ref.get_state()
+    act = (rt == 1) | (rt == 2)
+    for s, c, _ in out:
+        _close(s[act], rs[act], MIXED_TOL)
+        _close(c[act], rc[act], MIXED_TOL)
+    _close(out[1][0][act], out[0][0][act], 1e-12)
+    _close(out[1][1][act], out[0][1][act], 1e-12)
+    assert cyc[0] == cyc[1]
