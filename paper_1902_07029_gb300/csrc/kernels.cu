@@ -373,6 +373,46 @@ __device__ __forceinline__ float2 tile_update(const float2 (*X)[kTileRN], const 
     return out;
 }
 
+// the planes' staged data in the dynamic shared memory of k_sweep_tile
+struct TileSmem {
+    float2 XO[4][kTileRN];  // x before the sweep
+    float2 XR[4][kTileRN];  // x after the red half (ring 1 and tile)
+    float2 WS[4][kTileRN];  // coefficient source (s, c)
+    float2 RH[4][kTileRN];  // right-hand side
+    int8_t TS[4][kTileRN];  // node type
+};
+constexpr int kTilePer = (kTileRN + kTileThreads - 1) / kTileThreads;  // staged nodes per thread
+
+// a thread's share of one plane (region with the two-node halo), fetched one
+// iteration ahead of its use
+struct TilePlane {
+    float2 xo[kTilePer], wc[kTilePer], rh[kTilePer];
+    int8_t ty[kTilePer];
+};
+
+__device__ __forceinline__ void tile_fetch(TilePlane& f, int zl, int X0, int Y0, int n, long long st1, long long st2,
+                                           const int8_t* __restrict__ type, const float2* __restrict__ Wc,
+                                           const float2* __restrict__ rhs, const float2* __restrict__ xin) {
+#pragma unroll
+    for (int k = 0; k < kTilePer; k++) {
+        const int t = threadIdx.x + k * kTileThreads;
+        const int gx = X0 - 2 + t % kTileRX, gy = Y0 - 2 + t / kTileRX;
+        f.xo[k] = make_float2(0.f, 0.f);
+        f.wc[k] = make_float2(0.f, 0.f);
+        f.rh[k] = make_float2(0.f, 0.f);
+        f.ty[k] = T_OUT;
+        if (t < kTileRN && zl >= 0 && zl < n && gx >= 0 && gx < n && gy >= 0 && gy < n) {
+            // every load issued at once (no dependence on the type): values at
+            // inactive nodes are read but never used
+            const long long p = gx + gy * st1 + zl * st2;
+            f.ty[k] = type[p];
+            f.xo[k] = xin[p];
+            f.wc[k] = Wc[p];
+            f.rh[k] = rhs[p];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kTileThreads) k_sweep_tile(const int* __restrict__ tiles, int ntx, int nty, int n,
                                                              const int8_t* __restrict__ type,
                                                              const float2* __restrict__ Wc,
@@ -380,10 +420,8 @@ __global__ void __launch_bounds__(kTileThreads) k_sweep_tile(const int* __restri
                                                              const float2* __restrict__ xin, float2* __restrict__ xout,
                                                              Coef<float> c, const int* __restrict__ gidx, int ng,
                                                              float* snap) {
-    __shared__ float2 XO[4][kTileRN];
-    __shared__ float2 XR[4][kTileRN];
-    __shared__ float2 WS[4][kTileRN];
-    __shared__ int8_t TS[4][kTileRN];
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    TileSmem& S = *reinterpret_cast<TileSmem*>(tile_smem);
     const int tile = tiles[blockIdx.x];
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const int X0 = tx * kTileX, Y0 = ty * kTileY, Z0 = tz * kTileZ;
@@ -397,27 +435,25 @@ __global__ void __launch_bounds__(kTileThreads) k_sweep_tile(const int* __restri
         xout[g] = v;
         if (snap) snap[gi] = v.x;
     }
+    TilePlane f;
+    tile_fetch(f, Z0 - 2, X0, Y0, n, st1, st2, type, Wc, rhs, xin);
     for (int z = Z0 - 3; z <= Z0 + kTileZ; z++) {
-        // stage plane z + 1 with its halo (outside the box: inactive)
+        // plane z + 1 (fetched during the previous iteration) into its slot,
+        // then the fetch of plane z + 2 starts
         {
-            const int zl = z + 1, sl = zl & 3;
-            for (int t = threadIdx.x; t < kTileRN; t += kTileThreads) {
-                const int gx = X0 - 2 + t % kTileRX, gy = Y0 - 2 + t / kTileRX;
-                float2 xo = make_float2(0.f, 0.f), wc = make_float2(0.f, 0.f);
-                int8_t ty8 = T_OUT;
-                if (zl >= 0 && zl < n && gx >= 0 && gx < n && gy >= 0 && gy < n) {
-                    const long long p = gx + gy * st1 + zl * st2;
-                    ty8 = type[p];
-                    if (ty8 == T_IN || ty8 == T_GHOST) {
-                        xo = xin[p];
-                        wc = Wc[p];
-                    }
+            const int sl = (z + 1) & 3;
+#pragma unroll
+            for (int k = 0; k < kTilePer; k++) {
+                const int t = threadIdx.x + k * kTileThreads;
+                if (t < kTileRN) {
+                    S.XO[sl][t] = f.xo[k];
+                    S.WS[sl][t] = f.wc[k];
+                    S.RH[sl][t] = f.rh[k];
+                    S.TS[sl][t] = f.ty[k];
                 }
-                XO[sl][t] = xo;
-                WS[sl][t] = wc;
-                TS[sl][t] = ty8;
             }
         }
+        if (z + 2 <= Z0 + kTileZ + 1) tile_fetch(f, z + 2, X0, Y0, n, st1, st2, type, Wc, rhs, xin);
         __syncthreads();
         // red nodes of plane z over the tile and a one-node ring
         if (z >= Z0 - 1) {
@@ -426,12 +462,10 @@ __global__ void __launch_bounds__(kTileThreads) k_sweep_tile(const int* __restri
                 const int li = 1 + t % (kTileX + 2), lj = 1 + t / (kTileX + 2);
                 const int r = li + lj * kTileRX;
                 const int gx = X0 - 2 + li, gy = Y0 - 2 + lj;
-                float2 v = XO[sl][r];
-                if (TS[sl][r] == T_IN && ((gx + gy + z) & 1) == 0) {
-                    const long long p = gx + gy * st1 + z * st2;
-                    v = tile_update(XO, WS, sl, r, zl, zh, rhs[p], c);
-                }
-                XR[sl][r] = v;
+                float2 v = S.XO[sl][r];
+                if (S.TS[sl][r] == T_IN && ((gx + gy + z) & 1) == 0)
+                    v = tile_update(S.XO, S.WS, sl, r, zl, zh, S.RH[sl][r], c);
+                S.XR[sl][r] = v;
             }
         }
         __syncthreads();
@@ -444,10 +478,10 @@ __global__ void __launch_bounds__(kTileThreads) k_sweep_tile(const int* __restri
                 const int li = 2 + t % kTileX, lj = 2 + t / kTileX;
                 const int r = li + lj * kTileRX;
                 const int gx = X0 - 2 + li, gy = Y0 - 2 + lj;
-                if (gx >= n || gy >= n || TS[sl][r] != T_IN) continue;
+                if (gx >= n || gy >= n || S.TS[sl][r] != T_IN) continue;
                 const long long p = gx + gy * st1 + zb * st2;
-                float2 v = XR[sl][r];
-                if (((gx + gy + zb) & 1) == 1) v = tile_update(XR, WS, sl, r, zl, zh, rhs[p], c);
+                float2 v = S.XR[sl][r];
+                if (((gx + gy + zb) & 1) == 1) v = tile_update(S.XR, S.WS, sl, r, zl, zh, S.RH[sl][r], c);
                 xout[p] = v;
             }
         }
@@ -1279,8 +1313,12 @@ int launch_relax_lex(const LevelGeo& L, const LevelVec<T>& V, T* snap, cudaStrea
 int launch_sweep_tiled(const LevelGeo& L, const float2* Wc, const float2* rhs, const float2* xin, float2* xout,
                        const Coef<float>& c, float* snap, cudaStream_t s) {
     if (!L.tiles || L.ntiles == 0) return 0;
-    launch_k(k_sweep_tile, (unsigned)L.ntiles, kTileThreads, 0, s, L.tiles, L.tile_nx, L.tile_ny, L.n, L.type, Wc, rhs,
-             xin, xout, c, L.gidx, L.ng, snap);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_sweep_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+    });
+    launch_k(k_sweep_tile, (unsigned)L.ntiles, kTileThreads, sizeof(TileSmem), s, L.tiles, L.tile_nx, L.tile_ny, L.n,
+             L.type, Wc, rhs, xin, xout, c, L.gidx, L.ng, snap);
     return 1;
 }
 
