@@ -111,3 +111,30 @@ def test_w21_lexicographic_convergence_factor_on_test3(sulfmg, oracle_mod):
     late = rho[starts[5]:]
     late = late[~first[starts[5]:].astype(bool)]
     assert abs(np.median(late) - 0.119) <= 0.05
+
+
+def test_convergence_factor_bounded_at_large_n(sulfmg):
+    """The multigrid factor stays bounded as h decreases, at the sizes the
+    oracle is too slow for: V(2,2) collective red-black cycles on the star,
+    Jacobian after one CN step at dt = h, seeded random right-hand side,
+    geometric mean of the defect ratios of cycles 4..12.  The oracle test pins
+    N = 64 ... 512 (factors 0.25, 0.11, 0.12, 0.085); here N = 512 ... 2048."""
+    rhos = {}
+    for N in (512, 1024, 2048):
+        dom = sulfmg.Domain(workloads.star(N), 2, (-1.0, 1.0), N)
+        dom.set_model(MODEL)
+        dom.step(2.0 / N, 1)
+        s, c, t = dom.get_state()
+        W = np.zeros(2 * s.size)
+        W[0::2] = s.ravel()
+        W[1::2] = c.ravel()
+        act = ((t == 1) | (t == 2)).ravel()
+        rng = np.random.default_rng(7)
+        rhs = np.zeros_like(W)
+        rhs[0::2][act] = rng.standard_normal(act.sum())
+        rhs[1::2][act] = rng.standard_normal(act.sum())
+        _, rn = dom.cycles(2.0 / N, W, rhs, 12)
+        rhos[N] = float(np.exp(np.mean(np.log(rn[3:] / rn[2:-1]))))
+        dom.close()
+    assert max(rhos.values()) <= 0.25, rhos
+    assert rhos[1024] <= rhos[512] + 0.07 and rhos[2048] <= rhos[1024] + 0.07, rhos
