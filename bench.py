@@ -76,6 +76,10 @@ RELAX_TRAFFIC = {
     ("rbox257", "fp64"): (258.0 * 4142122, "profiles/relax_inside_fp64_rbox129.md (258 B per update measured at "
                                            "129^3, scaled to the 4 142 122 updates of a 257^3 launch)"),
     ("star1025", "fp64"): (31.30e6 + 17.0e3, "profiles/relax_inside_fp64_star1025.md"),
+    # 129^3 capture of the matrix-free FP32 kernel (profiles/relax_mf_fp32_rbox129.md): 31.6 MB per
+    # 521 488 updates = 60.6 B per update, scaled to the 257^3 launch
+    ("rbox257", "mixed"): (60.6 * 4142122, "profiles/relax_mf_fp32_rbox129.md (60.6 B per update measured at "
+                                          "129^3, scaled to the 4 142 122 updates of a 257^3 launch)"),
 }
 
 
@@ -398,7 +402,8 @@ def _roofline(m, name, prec_name, peaks):
                 "stream_bytes": f"{STREAM_BYTES[dim][prec_name]} B per update as streamed (precomputed "
                                 f"coefficients)",
                 "traffic": traffic[0], "traffic_source": traffic[1]}
-    common = {"kernel": "k_relax_inside (finest level, one colour)", "avg_launch_us": avg_us,
+    kname = "k_relax_inside" if prec_name == "fp64" else "k_relax_mf (coefficients from (s, c))"
+    common = {"kernel": f"{kname} (finest level, one colour)", "avg_launch_us": avg_us,
               "launches": m["relax_n"], "sample": "one event bracket around the two back-to-back colour launches of "
               "the first finest-level sweep of every cycle of the last timed step (library stream)"}
     if prec_name == "fp64":
