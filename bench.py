@@ -50,12 +50,14 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # One colour launch updates half of the inside nodes; per updated node it is
 # charged these bytes.
 SWEEP_BYTES = {"fp64": 64, "mixed": 32}
-# Compulsory bytes of one colour update as this library streams it (the
-# stencil coefficients are precomputed once per Newton iteration): rhs, the
+# Compulsory bytes of one colour update as this library streams it.  FP64:
+# the stencil coefficients precomputed once per Newton iteration -- rhs, the
 # rows of the inverse 2x2 block, the own and the other colour's edge
-# coefficients and the unknown read and written.  2-D: 16 + 32 + 2*16 + 2*16 +
-# 32 = 144 B; 3-D: 16 + 32 + 3*16 + 3*16 + 32 = 176 B (FP64); half in FP32.
-STREAM_BYTES = {2: {"fp64": 144, "mixed": 72}, 3: {"fp64": 176, "mixed": 88}}
+# coefficients and the unknown read and written: 2-D 16 + 32 + 2*16 + 2*16 +
+# 32 = 144 B, 3-D 16 + 32 + 3*16 + 3*16 + 32 = 176 B.  FP32 (coefficients
+# recomputed from (s, c)): (s, c) of the node and of one node of the other
+# colour, x of the other colour, rhs, x written: 5 * 8 = 40 B.
+STREAM_BYTES = {2: {"fp64": 144, "mixed": 40}, 3: {"fp64": 176, "mixed": 40}}
 # FP64/FP32 arithmetic of one update: per axis four fused multiply-adds for
 # the off-diagonal part, then two fused multiply-adds and two multiplies for
 # the 2x2 block solve: 2-D 10 FMA + 2 MUL = 22 flop, 3-D 14 FMA + 2 MUL = 30.
@@ -399,8 +401,9 @@ def _roofline(m, name, prec_name, peaks):
                                f"recomputed); {n:.0f} nodes per launch",
                 "achieved_stream_bytes": ach_stream,
                 "frac_stream_bytes": (ach_stream / hbm) if (ach_stream and hbm) else None,
-                "stream_bytes": f"{STREAM_BYTES[dim][prec_name]} B per update as streamed (precomputed "
-                                f"coefficients)",
+                "stream_bytes": f"{STREAM_BYTES[dim][prec_name]} B per update as streamed ("
+                                + ("precomputed coefficients)" if prec_name == "fp64" else
+                                   "coefficients recomputed from (s, c))"),
                 "traffic": traffic[0], "traffic_source": traffic[1]}
     kname = "k_relax_inside" if prec_name == "fp64" else "k_relax_mf (coefficients from (s, c))"
     common = {"kernel": f"{kname} (finest level, one colour)", "avg_launch_us": avg_us,
