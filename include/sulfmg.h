@@ -96,10 +96,11 @@ typedef struct {
                  tau_s, ghost_sweeps and the boundary condition, and only
                  where it stays within 24 (2-D) / 27 (3-D) entries per ghost
                  on average); 0 = pass by pass.  Equal up to rounding.  default 1
-   relax_occupancy 1 = the FP64 inside relaxation is compiled for five
-                 resident CTAs per SM (a few spilled values) instead of four:
-                 more warps hide the load latency; no effect in FP32.
-                 Same results either way.                          default 0
+   relax_occupancy 1 = the FP64 inside relaxation loads its coefficients
+                 after the dependent-launch wait instead of prefetching them
+                 across it, and is compiled for six resident CTAs per SM
+                 instead of four: more warps hide the load latency; no effect
+                 in FP32.  Same results either way.                default 0
    relax_matrix_free 1 = the FP32 red-black collective relaxation of the
                  mixed form recomputes each node's stencil coefficients from
                  (s, c) instead of reading the stored ones (same expressions:

@@ -197,12 +197,8 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
 
 // one colour of inside nodes; with snap_n > 0 also the copy of the ghosts' s
 // (nodes sidx) into snap that the composed ghost relaxation starts from
-// HO: the register budget is set for five resident CTAs per SM instead of
-// the four that the FP64 update's 52 registers (prefetched coefficients)
-// allow: more warps to hide the load latency, at the price of a few spilled
-// values (sulf_solver::relax_occupancy; FP32 runs eight CTAs either way)
-template <int D, typename T, bool PW, bool HO>
-__global__ void __launch_bounds__(kT, HO ? 5 : 1) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
+template <int D, typename T, bool PW>
+__global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
                                                       const typename V2<T>::t* __restrict__ rhs,
                                                       typename V2<T>::t* __restrict__ x, long long st1, long long st2,
                                                       const int* __restrict__ sidx, int snap_n, T* snap) {
@@ -221,6 +217,27 @@ __global__ void __launch_bounds__(kT, HO ? 5 : 1) k_relax_inside(const int* __re
     if (t < snap_n) snap[t] = reinterpret_cast<const T*>(x + sg)[0];
     if (t >= cnt) return;
     stages::relax_apply<D, T, PW, false>(p, k, rhs, x, st);
+}
+
+// The variant for large levels, where all but the first wave of CTAs start
+// after the predecessor has finished anyway: the coefficients are loaded
+// after the dependent-launch wait instead of held in registers across it,
+// and the register budget is set for six resident CTAs per SM (more warps to
+// hide the load latency); sulf_solver::relax_occupancy, FP64 collective only
+template <int D, typename T>
+__global__ void __launch_bounds__(kT, 6) k_relax_inside_ho(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
+                                                            const typename V2<T>::t* __restrict__ rhs,
+                                                            typename V2<T>::t* __restrict__ x, long long st1,
+                                                            long long st2, const int* __restrict__ sidx, int snap_n,
+                                                            T* snap) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long st[3] = {1, st1, st2};
+    const long long p = t < cnt ? list[t] : 0;
+    const int sg = t < snap_n ? sidx[t] : 0;
+    pdl_enter();
+    if (t < snap_n) snap[t] = reinterpret_cast<const T*>(x + sg)[0];
+    if (t >= cnt) return;
+    stages::relax_node<D, T, false, false>(p, cf, rhs, x, st);
 }
 
 // lexicographic collective Gauss-Seidel (Sec. 3.5.1, the paper's smoother):
@@ -1291,11 +1308,11 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
         return 1;
     }
     if (pointwise)
-        launch_k(k_relax_inside<D, T, true, false>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
+        launch_k(k_relax_inside<D, T, true>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
                  V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     else
-        launch_k(std::is_same<T, double>::value && launch_occupancy() ? k_relax_inside<D, T, false, true>
-                                                                       : k_relax_inside<D, T, false, false>,
+        launch_k(std::is_same<T, double>::value && launch_occupancy() ? k_relax_inside_ho<D, T>
+                                                                       : k_relax_inside<D, T, false>,
                  grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
                  V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     return 1;
