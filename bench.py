@@ -776,7 +776,9 @@ def main():
     ap.add_argument("--impl", default="sulfmg", choices=["sulfmg", "reference"])
     ap.add_argument("--workload", default="rbox257", choices=sorted(workloads.WORKLOADS) + ["batch", "serve", "rho"])
     ap.add_argument("--instances", type=int, default=256, help="batch: number of instances")
-    ap.add_argument("--streams", type=int, default=8, help="batch/serve: worker streams")
+    ap.add_argument("--streams", type=int, default=16,
+                    help="batch/serve: worker streams (256-instance batch, 10 steps: 42.8 M node-updates/s with 8, "
+                         "58.1 M with 16, 58.9 M with 32)")
     ap.add_argument("--seq-steps", type=int, default=10, help="batch: CN steps of the sequential FP64 arm")
     ap.add_argument("--jobs", type=int, default=32, help="serve: number of jobs")
     ap.add_argument("--rate", default="auto",
