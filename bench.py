@@ -504,10 +504,12 @@ def run_gpu(args):
 def run_batch(args):
     """256 random-star instances, sizes uniform in {129, 257, 513, 1025}^2,
     s_ext ~ U(0.5, 1), dt = h, advanced together by the batching runtime after
-    the autotuner has picked each size's speed-only controls.  Three arms:
-    batched mixed precision, batched FP64 and the same instances advanced one
-    after the other in FP64.  Accuracy: each arm's state after two CN steps on
-    an 8-instance subset (two per size) against the CPU oracle."""
+    the autotuner has picked each size's speed-only controls.  Arms: batched
+    mixed precision, batched FP64, the same two in lock-step mode (the
+    instances of one size advance together, one launch per cycle phase for all
+    of them; default controls) and the instances advanced one after the other
+    in FP64.  Accuracy: each arm's state after two CN steps on an 8-instance
+    subset (two per size) against the CPU oracle."""
     import torch
 
     import oracle
@@ -545,13 +547,15 @@ def run_batch(args):
         o.set_solver()
         o.step(dts[i], 2)
         ref[i] = o.get_state()
+    arms = (("batched_mixed", 1, "batched"), ("batched_fp64", 0, "batched"), ("lockstep_mixed", 1, "lockstep"),
+            ("lockstep_fp64", 0, "lockstep"), ("sequential_fp64", 0, "sequential"))
     acc = {}
-    for label, precision, batched in (("batched_mixed", 1, True), ("batched_fp64", 0, True),
-                                      ("sequential_fp64", 0, False)):
+    for label, precision, mode in arms:
         doms = make(subset, precision)
-        if batched:
-            b = pkg.Batch(doms, nstreams=args.streams)
-            b.autotune([dts[i] for i in subset])
+        if mode != "sequential":
+            b = pkg.Batch(doms, nstreams=args.streams, lockstep=mode == "lockstep")
+            if mode == "batched":
+                b.autotune([dts[i] for i in subset])
             b.step([dts[i] for i in subset], 2)
             b.close()
         else:
@@ -570,17 +574,16 @@ def run_batch(args):
     steps = args.steps
     seq_steps = max(1, min(steps, args.seq_steps))
     out, tuned = {}, None
-    for label, precision, batched in (("batched_mixed", 1, True), ("batched_fp64", 0, True),
-                                      ("sequential_fp64", 0, False)):
+    for label, precision, mode in arms:
         doms = make(range(n_inst), precision)
         nact = sum(d.stats()["n_inside"] + d.stats()["n_ghost"] for d in doms)
-        k = steps if batched else seq_steps
-        if batched:
-            b = pkg.Batch(doms, nstreams=args.streams)
+        k = steps if mode != "sequential" else seq_steps
+        if mode != "sequential":
+            b = pkg.Batch(doms, nstreams=args.streams, lockstep=mode == "lockstep")
             t0 = time.perf_counter()
-            res = b.autotune(dts)
+            res = b.autotune(dts) if mode == "batched" else None
             t_tune = time.perf_counter() - t0
-            if precision == 1:
+            if precision == 1 and mode == "batched":
                 tuned = {}
                 for N, r in zip(sizes, res):
                     if N not in tuned or not r["cached"]:
@@ -622,8 +625,11 @@ def run_batch(args):
                                    "(two per size), 2 CN steps"},
             "tuned": {str(k): v for k, v in sorted(tuned.items())} if tuned else None,
             "batched_mixed": out["batched_mixed"], "batched_fp64": out["batched_fp64"],
+            "lockstep_mixed": out["lockstep_mixed"], "lockstep_fp64": out["lockstep_fp64"],
             "sequential_fp64": out["sequential_fp64"],
             "mixed_vs_fp64_batched": out["batched_mixed"]["value"] / out["batched_fp64"]["value"],
+            "lockstep_vs_batched": {"mixed": out["lockstep_mixed"]["value"] / out["batched_mixed"]["value"],
+                                    "fp64": out["lockstep_fp64"]["value"] / out["batched_fp64"]["value"]},
             "batched_vs_sequential_fp64": out["batched_fp64"]["value"] / out["sequential_fp64"]["value"]}
     print(json.dumps(line), flush=True)
 

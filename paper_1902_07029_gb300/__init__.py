@@ -97,6 +97,7 @@ _SIGS = {
     "sulf_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]),
     "sulf_batch_step": (ctypes.c_int, [P, _dp, ctypes.POINTER(ctypes.c_int)]),
     "sulf_batch_status": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
+    "sulf_batch_set_lockstep": (ctypes.c_int, [P, ctypes.c_int]),
     "sulf_batch_autotune": (ctypes.c_int, [P, _dp, ctypes.POINTER(SulfTuneResult)]),
     "sulf_autotune": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(SulfTuneResult)]),
     "sulf_batch_destroy": (None, [P]),
@@ -405,13 +406,19 @@ class Domain:
 class Batch:
     """Many domains advanced together (each keeps its own state and results)."""
 
-    def __init__(self, domains, nstreams=8):
+    def __init__(self, domains, nstreams=8, lockstep=False):
         self.lib = load()
         self.domains = list(domains)
         arr = (P * len(self.domains))(*[d.h for d in self.domains])
         b = P()
         _chk(self.lib, self.lib.sulf_batch_create(arr, len(self.domains), nstreams, ctypes.byref(b)))
         self.b = b
+        if lockstep:
+            self.set_lockstep(True)
+
+    def set_lockstep(self, on):
+        """sulf_batch_set_lockstep: same-class instances step in lock step"""
+        _chk(self.lib, self.lib.sulf_batch_set_lockstep(self.b, 1 if on else 0))
 
     def step(self, dt, nsteps):
         n = len(self.domains)

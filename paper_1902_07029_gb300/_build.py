@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OBJ_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(HERE, "libsulfmg.so")
-SOURCES = ("geometry.cu", "kernels.cu", "solver.cu", "noalloc.cu", "tail.cu", "runtime.cu", "levelset.cu")
+SOURCES = ("geometry.cu", "kernels.cu", "solver.cu", "noalloc.cu", "tail.cu", "runtime.cu", "levelset.cu", "lockstep.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -4,7 +4,10 @@
 // nstreams host workers owns a CUDA stream and takes the next instance (largest
 // work first); an instance's multigrid cycles are its own captured CUDA graphs,
 // so the GPU runs the kernels of several instances at once while each worker
-// waits on its instance's convergence tests.
+// waits on its instance's convergence tests.  In lock-step mode the instances
+// of one size class (same dimension, grid, levels, model-independent solver
+// controls, dt and step count) form one work item: each phase of their cycles
+// is one launch over all of them (solver.cu, lockstep.cu).
 //
 // Server: jobs (a level set, a model, a number of CN steps) are submitted at any
 // time and admitted first-come-first-served among those whose device-memory
@@ -79,6 +82,7 @@ struct sulf_batch_s {
     std::vector<int> status;
     std::vector<std::string> errors;
     int device = 0;
+    int lockstep = 0;
 };
 
 extern "C" int sulf_batch_create(const sulf_handle* handles, int n, int nstreams, sulf_batch* out) {
@@ -105,34 +109,85 @@ extern "C" int sulf_batch_create(const sulf_handle* handles, int n, int nstreams
     return SULF_OK;
 }
 
+extern "C" int sulf_batch_set_lockstep(sulf_batch b, int on) {
+    if (!b || (on != 0 && on != 1)) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    b->lockstep = on;
+    return SULF_OK;
+}
+
 extern "C" int sulf_batch_step(sulf_batch b, const double* dt, const int* nsteps) {
     if (!b || !dt || !nsteps) return sulf_fail(SULF_EINVAL, "invalid arguments");
     const int n = (int)b->h.size();
-    // largest work first: active nodes times steps
-    std::vector<int> order(n);
-    std::vector<double> work(n);
-    for (int i = 0; i < n; i++) {
-        sulf_stats st;
-        sulf_get_stats(b->h[i], &st);
-        work[i] = (double)(st.n_inside + st.n_ghost) * nsteps[i];
-        order[i] = i;
+    // work items: one instance, or (lock-step mode) a class of instances
+    std::vector<std::vector<int>> items;
+    if (b->lockstep) {
+        std::vector<std::vector<double>> keys;
+        for (int i = 0; i < n; i++) {
+            std::vector<double> k;
+            if (dt[i] > 0 && nsteps[i] > 0 && sulf::lockstep_key(b->h[i], k)) {
+                k.push_back(dt[i]);
+                k.push_back((double)nsteps[i]);
+                size_t c = 0;
+                while (c < keys.size() && keys[c] != k) c++;
+                if (c == keys.size()) {
+                    keys.push_back(k);
+                    items.push_back({});
+                }
+                items[c].push_back(i);
+            } else {
+                items.push_back({i});
+                keys.push_back({-1.0});  // matches no class key
+            }
+        }
+    } else {
+        for (int i = 0; i < n; i++) items.push_back({i});
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    // largest work first: active nodes times steps
+    std::vector<double> work(items.size(), 0.0);
+    for (size_t j = 0; j < items.size(); j++)
+        for (int i : items[j]) {
+            sulf_stats st;
+            sulf_get_stats(b->h[i], &st);
+            work[j] += (double)(st.n_inside + st.n_ghost) * nsteps[i];
+        }
+    std::vector<size_t> order(items.size());
+    for (size_t j = 0; j < order.size(); j++) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return work[a] > work[c]; });
     std::atomic<int> next(0);
     auto worker = [&](int k) {
         cudaSetDevice(b->device);
         for (;;) {
-            int j = next.fetch_add(1);
-            if (j >= n) break;
-            int i = order[j];
-            int rc = sulf_set_stream(b->h[i], b->streams[k]);
-            if (rc == SULF_OK) rc = sulf_step(b->h[i], dt[i], nsteps[i]);
-            b->status[i] = rc;
-            b->errors[i] = rc ? sulf_last_error() : "";
+            const int j = next.fetch_add(1);
+            if (j >= (int)order.size()) break;
+            const std::vector<int>& it = items[order[j]];
+            if (it.size() == 1) {
+                const int i = it[0];
+                int rc = sulf_set_stream(b->h[i], b->streams[k]);
+                if (rc == SULF_OK) rc = sulf_step(b->h[i], dt[i], nsteps[i]);
+                b->status[i] = rc;
+                b->errors[i] = rc ? sulf_last_error() : "";
+                continue;
+            }
+            std::vector<sulf_handle> hs;
+            for (int i : it) {
+                sulf_set_stream(b->h[i], b->streams[k]);
+                hs.push_back(b->h[i]);
+            }
+            std::vector<int> st(it.size(), SULF_OK);
+            std::vector<std::string> err;
+            int rc = sulf::lockstep_advance(hs.data(), (int)hs.size(), dt[it[0]], nsteps[it[0]], st.data(), err,
+                                            b->streams[k]);
+            const std::string cls = rc ? sulf_last_error() : "";
+            for (size_t q = 0; q < it.size(); q++) {
+                const int i = it[q];
+                b->status[i] = rc ? rc : st[q];
+                b->errors[i] = rc ? cls : err[q];
+            }
         }
     };
     std::vector<std::thread> th;
-    for (int k = 0; k < (int)b->streams.size(); k++) th.emplace_back(worker, k);
+    const int nw = std::min((int)b->streams.size(), (int)items.size());
+    for (int k = 0; k < nw; k++) th.emplace_back(worker, k);
     for (auto& t : th) t.join();
     for (int i = 0; i < n; i++)
         if (b->status[i] != SULF_OK) return sulf_fail(b->status[i], "batch instance " + std::to_string(i) + ": " + b->errors[i]);

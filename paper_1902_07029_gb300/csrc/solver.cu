@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/sulfmg_debug.h"
+#include "lockstep.cuh"
 #include "sulf_internal.cuh"
 
 using namespace sulf;
@@ -1451,6 +1452,435 @@ int sulf_dbg_coarsest_solve(sulf_handle h, double dt, const double* Wc0, const d
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Lock-step batching: K domains of one size class advance their Newton
+// iterations and multigrid cycles in lock step, each phase of a cycle one
+// launch over all instances' work lists (lockstep.cu); an instance leaves a
+// linear solve (or the Newton loop) when its own test says so and is masked
+// from then on, so every instance runs the iterations and cycles it runs
+// alone.  The Newton-level steps (old-time part, residual F, update, the
+// coefficients and the coarsest inverse of each Newton iteration) run per
+// instance on the class's stream.
+namespace {
+
+constexpr int kBatchT = 256;
+constexpr int kLockMaxCoarsest = 2048;  // coarsest active nodes (32 KB of FP64 right-hand side)
+
+template <int D, typename T>
+BLev<D, T> blev_of(sulf_domain* d, LevelVec<T>* V, int l) {
+    const LevelGeo& G = d->geo[l];
+    LevelVec<T>& v = V[l];
+    BLev<D, T> b;
+    b.ls = stages::make_lists(G);
+    b.tb = stages::ghost_tab<T>(G);
+    b.cf = stages::coef_ptr<D, T>(v);
+    b.rhs = v.rhs;
+    b.x = v.x;
+    b.res = v.res;
+    b.type = G.type;
+    b.n = G.n;
+    b.st1 = G.st[1];
+    b.st2 = G.st[2];
+    b.gop_ptr = G.gop_ptr;
+    b.gop_code = G.gop_code;
+    b.gop_val = std::is_same<T, float>::value ? (const T*)G.gop_val32 : (const T*)G.gop_val;
+    b.gc = v.gc;
+    b.gci = v.gci;
+    b.snap = v.gbuf[0];
+    b.nb = G.nb;
+    b.eptr = G.eptr;
+    b.eidx = G.eidx;
+    b.bidx = G.bidx;
+    b.eval = std::is_same<T, float>::value ? (const T*)G.eval32 : (const T*)G.eval;
+    b.nact = G.nact;
+    b.act = G.act;
+    b.Ainv = v.Ainv;
+    return b;
+}
+
+// device memory of one lock-step call, released at its end
+struct Scratch {
+    std::vector<void*> p;
+    cudaStream_t s;
+    void* get(size_t n) {
+        void* q = nullptr;
+        if (cudaMallocAsync(&q, n < 256 ? 256 : n, s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p.push_back(q);
+        return q;
+    }
+    ~Scratch() {
+        for (void* q : p) cudaFreeAsync(q, s);
+        cudaStreamSynchronize(s);
+    }
+};
+
+// CTA prefix over instances (pre[i] = CTAs of instances < i), uploaded
+struct Blocks {
+    const int* d = nullptr;
+    int total = 0;
+};
+
+template <int D>
+struct LockClass {
+    std::vector<sulf_domain*> h;
+    int K = 0, L = 0;
+    cudaStream_t s = nullptr;
+    Scratch* mem = nullptr;
+    const BLev<D, double>* l64[SULF_MAXLEV] = {};
+    const BLev<D, float>* l32[SULF_MAXLEV] = {};
+    Blocks red[SULF_MAXLEV], black[SULF_MAXLEV], gop[SULF_MAXLEV], act[SULF_MAXLEV], ext[SULF_MAXLEV], coarse;
+    int max_nact = 0;
+    int* dactive = nullptr;
+    std::vector<int> active;
+    unsigned long long* dnorm = nullptr;
+    std::vector<unsigned long long> hnorm;
+    long long launches = 0;
+
+    int upload_blocks(Blocks& b, const std::vector<long long>& units, int per_cta) {
+        std::vector<int> pre(K + 1, 0);
+        for (int i = 0; i < K; i++) pre[i + 1] = pre[i] + (int)((units[i] + per_cta - 1) / per_cta);
+        int* dp = (int*)mem->get(sizeof(int) * (K + 1));
+        if (!dp) return sulf_fail(SULF_ENOMEM, "out of device memory");
+        SULF_CUDA_TRY(cudaMemcpyAsync(dp, pre.data(), sizeof(int) * (K + 1), cudaMemcpyHostToDevice, s));
+        b.d = dp;
+        b.total = pre[K];
+        return SULF_OK;
+    }
+
+    template <typename T>
+    int upload_levels(LevelVec<T>* (*vec)(sulf_domain*), const BLev<D, T>** out) {
+        for (int l = 0; l < L; l++) {
+            std::vector<BLev<D, T>> v(K);
+            for (int i = 0; i < K; i++) v[i] = blev_of<D, T>(h[i], vec(h[i]), l);
+            BLev<D, T>* dv = (BLev<D, T>*)mem->get(sizeof(BLev<D, T>) * K);
+            if (!dv) return sulf_fail(SULF_ENOMEM, "out of device memory");
+            SULF_CUDA_TRY(cudaMemcpyAsync(dv, v.data(), sizeof(BLev<D, T>) * K, cudaMemcpyHostToDevice, s));
+            SULF_CUDA_TRY(cudaStreamSynchronize(s));  // the host vector goes out of scope
+            out[l] = dv;
+        }
+        return SULF_OK;
+    }
+
+    int setup() {
+        const bool mixed = h[0]->solver.precision == 1;
+        if (int rc = upload_levels<double>([](sulf_domain* d) { return d->v64; }, l64)) return rc;
+        if (mixed)
+            if (int rc = upload_levels<float>([](sulf_domain* d) { return d->v32; }, l32)) return rc;
+        for (int l = 0; l < L; l++) {
+            std::vector<long long> r(K), b(K), g(K), a(K), e(K);
+            for (int i = 0; i < K; i++) {
+                const LevelGeo& G = h[i]->geo[l];
+                r[i] = G.nin[0];
+                b[i] = G.nin[1] > G.ng ? G.nin[1] : G.ng;
+                g[i] = (long long)G.ng * stages::kGopLanes;
+                a[i] = (long long)G.nin[0] + G.nin[1] + G.ng;
+                e[i] = G.nb;
+            }
+            if (int rc = upload_blocks(red[l], r, kBatchT)) return rc;
+            if (int rc = upload_blocks(black[l], b, kBatchT)) return rc;
+            if (int rc = upload_blocks(gop[l], g, kBatchT)) return rc;
+            if (int rc = upload_blocks(act[l], a, kBatchT)) return rc;
+            if (int rc = upload_blocks(ext[l], e, kBatchT)) return rc;
+        }
+        std::vector<long long> rows(K);
+        for (int i = 0; i < K; i++) {
+            rows[i] = 2LL * h[i]->geo[L - 1].nact;
+            max_nact = std::max(max_nact, h[i]->geo[L - 1].nact);
+        }
+        if (int rc = upload_blocks(coarse, rows, kBatchT / 32)) return rc;
+        dactive = (int*)mem->get(sizeof(int) * K);
+        dnorm = (unsigned long long*)mem->get(sizeof(unsigned long long) * K);
+        if (!dactive || !dnorm) return sulf_fail(SULF_ENOMEM, "out of device memory");
+        active.assign(K, 0);
+        hnorm.assign(K, 0);
+        SULF_CUDA_TRY(cudaStreamSynchronize(s));
+        return SULF_OK;
+    }
+
+    int set_active() {
+        SULF_CUDA_TRY(cudaMemcpyAsync(dactive, active.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+        SULF_CUDA_TRY(cudaStreamSynchronize(s));
+        return SULF_OK;
+    }
+
+    template <typename T>
+    void relax(const BLev<D, T>* const* lv, int l) {
+        launches += launch_batched<D, T>(BPhase::relax, lv[l], nullptr, red[l].d, red[l].total, K, dactive, 0,
+                                         nullptr, 0, s);
+        launches += launch_batched<D, T>(BPhase::relax, lv[l], nullptr, black[l].d, black[l].total, K, dactive, 1,
+                                         nullptr, 0, s);
+        launches += launch_batched<D, T>(BPhase::ghost_op, lv[l], nullptr, gop[l].d, gop[l].total, K, dactive, 0,
+                                         nullptr, 0, s);
+    }
+
+    template <typename T>
+    void cycle(const BLev<D, T>* const* lv, int l) {
+        if (l == L - 1) {
+            launches += launch_batched<D, T>(BPhase::coarsest, lv[l], nullptr, coarse.d, coarse.total, K, dactive, 0,
+                                             nullptr, sizeof(T) * 2 * (size_t)max_nact, s);
+            return;
+        }
+        const sulf_solver& sv = h[0]->solver;
+        for (int k = 0; k < sv.nu1; k++) relax<T>(lv, l);
+        launches += launch_batched<D, T>(BPhase::residual, lv[l], nullptr, act[l].d, act[l].total, K, dactive, 0,
+                                         nullptr, 0, s);
+        launches += launch_batched<D, T>(BPhase::extend, lv[l], nullptr, ext[l].d, ext[l].total, K, dactive, 0,
+                                         nullptr, 0, s);
+        launches += launch_batched<D, T>(BPhase::restrict_to, lv[l], lv[l + 1], act[l + 1].d, act[l + 1].total, K,
+                                         dactive, 0, nullptr, 0, s);
+        cycle<T>(lv, l + 1);
+        launches += launch_batched<D, T>(BPhase::prolong_from, lv[l], lv[l + 1], act[l].d, act[l].total, K, dactive,
+                                         0, nullptr, 0, s);
+        for (int k = 0; k < sv.nu2; k++) relax<T>(lv, l);
+    }
+
+    // one cycle of every active instance's linear solve, then the FP64
+    // defect with each instance's max-norm (read back)
+    int cycle_body() {
+        const bool mixed = h[0]->solver.precision == 1;
+        if (mixed) {
+            launches += launch_batched_mixed<D>(BPhase::zero32, l64[0], l32[0], act[0].d, act[0].total, K, dactive,
+                                                s);
+            cycle<float>(l32, 0);
+            launches += launch_batched_mixed<D>(BPhase::accumulate, l64[0], l32[0], act[0].d, act[0].total, K,
+                                                dactive, s);
+        } else {
+            cycle<double>(l64, 0);
+        }
+        SULF_CUDA_TRY(cudaMemsetAsync(dnorm, 0, sizeof(unsigned long long) * K, s));
+        launches += launch_batched<D, double>(BPhase::residual, l64[0], nullptr, act[0].d, act[0].total, K, dactive,
+                                              0, dnorm, 0, s);
+        if (mixed)
+            launches += launch_batched_mixed<D>(BPhase::to_float, l64[0], l32[0], act[0].d, act[0].total, K,
+                                                dactive, s);
+        SULF_CUDA_TRY(
+            cudaMemcpyAsync(hnorm.data(), dnorm, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, s));
+        SULF_CUDA_TRY(cudaStreamSynchronize(s));
+        std::string e = take_launch_error();
+        if (!e.empty()) return sulf_fail(SULF_EDEVICE, "lock-step launch failed: " + e);
+        return SULF_OK;
+    }
+};
+
+// one CN step of every instance whose status is SULF_OK, Newton iterations
+// and cycles in lock step; an instance that fails gets its code in status[i]
+// and its message in err[i] (and keeps the state it failed in)
+template <int D>
+int lockstep_step(LockClass<D>& C, int* status, std::vector<std::string>& err) {
+    const int K = C.K;
+    auto fail = [&](int i, int code, const std::string& msg) {
+        status[i] = sulf_fail(code, msg);
+        err[i] = msg;
+    };
+    std::vector<double> fn(K, 0.0);
+    for (int i = 0; i < K; i++) {
+        if (status[i] != SULF_OK) continue;
+        sulf_domain* d = C.h[i];
+        const LevelGeo& G0 = d->geo[0];
+        FConst fc = make_fconst(d);
+        SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, C.s));
+        d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, C.s);
+        SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, C.s));
+        d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm, C.s);
+        SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, C.s));
+        d->newton_last = 0;
+        d->cycles_last = 0;
+    }
+    SULF_CUDA_TRY(cudaStreamSynchronize(C.s));
+    std::vector<int> inewton(K, 0);  // instance still in its Newton loop
+    for (int i = 0; i < K; i++) {
+        if (status[i] != SULF_OK) continue;
+        sulf_domain* d = C.h[i];
+        fn[i] = bits_to_double(d->hnorm[0]);
+        if (fn[i] < d->solver.newton_tol) {
+            d->t += d->dt;
+            d->steps_total++;
+            d->last_fnorm = fn[i];
+        } else {
+            inewton[i] = 1;
+        }
+    }
+    const sulf_solver& sv = C.h[0]->solver;
+    for (int k = 1; k <= sv.max_newton; k++) {
+        bool any = false;
+        for (int i = 0; i < K; i++) any = any || inewton[i];
+        if (!any) break;
+        // per instance: the Jacobian of this Newton iteration on every level
+        for (int i = 0; i < K; i++) {
+            if (!inewton[i]) continue;
+            sulf_domain* d = C.h[i];
+            const LevelGeo& G0 = d->geo[0];
+            SULF_CUDA_TRY(cudaMemsetAsync(d->v64[0].x, 0, sizeof(double2) * G0.nn, C.s));
+            int rc;
+            if (sv.precision == 0) {
+                rc = MG<D, double>{d, d->v64}.prepare();
+            } else {
+                d->launches += launch_to_float(G0, d->W, d->v32[0].Wc, C.s);
+                d->launches += launch_coefs<D, double>(G0, d->v64[0], make_coef<double>(d, 0), C.s);
+                rc = MG<D, float>{d, d->v32}.prepare();
+                if (!rc) d->launches += launch_to_float(G0, d->v64[0].rhs, d->v32[0].rhs, C.s);
+                // the batched cycles zero the FP32 error at the active nodes
+                // only; the others stay zero from here
+                SULF_CUDA_TRY(cudaMemsetAsync(d->v32[0].x, 0, sizeof(float2) * G0.nn, C.s));
+            }
+            if (rc) return rc;
+            SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, C.s));
+        }
+        SULF_CUDA_TRY(cudaStreamSynchronize(C.s));
+        for (int i = 0; i < K; i++) {
+            C.active[i] = inewton[i];
+            if (inewton[i] && *(int*)(C.h[i]->hnorm + 6)) {
+                fail(i, SULF_ENOTCONV, "singular coarsest-level Jacobian");
+                inewton[i] = 0;
+                C.active[i] = 0;
+            }
+        }
+        // the cycles of the linear solves, in lock step
+        std::vector<double> rprev(fn);
+        std::vector<int> cyc(K, 0);
+        if (int rc = C.set_active()) return rc;
+        for (int c = 1; c <= sv.max_cycles; c++) {
+            bool on = false;
+            for (int i = 0; i < K; i++) on = on || C.active[i];
+            if (!on) break;
+            if (int rc = C.cycle_body()) return rc;
+            bool changed = false;
+            for (int i = 0; i < K; i++) {
+                if (!C.active[i]) continue;
+                sulf_domain* d = C.h[i];
+                const double rn = bits_to_double(C.hnorm[i]);
+                d->last_rho = rprev[i] > 0 ? rn / rprev[i] : 0.0;
+                rprev[i] = rn;
+                cyc[i] = c;
+                if (rn <= sv.lin_rtol * fn[i] || rn != rn || c == sv.max_cycles) {
+                    C.active[i] = 0;
+                    changed = true;
+                }
+            }
+            if (changed)
+                if (int rc = C.set_active()) return rc;
+        }
+        // per instance: the Newton update, the new residual and the test
+        for (int i = 0; i < K; i++) {
+            if (!inewton[i]) continue;
+            sulf_domain* d = C.h[i];
+            const LevelGeo& G0 = d->geo[0];
+            FConst fc = make_fconst(d);
+            d->cycles_last += cyc[i];
+            d->cycles_total += cyc[i];
+            SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, C.s));
+            d->launches += launch_newton_update(G0, d->W, d->v64[0].x, d->dnorm, C.s);
+            d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm + 2, C.s);
+            SULF_CUDA_TRY(
+                cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, C.s));
+        }
+        SULF_CUDA_TRY(cudaStreamSynchronize(C.s));
+        for (int i = 0; i < K; i++) {
+            if (!inewton[i]) continue;
+            sulf_domain* d = C.h[i];
+            const double dn = bits_to_double(d->hnorm[0]), wn = bits_to_double(d->hnorm[1]);
+            fn[i] = bits_to_double(d->hnorm[2]);
+            d->newton_last = k;
+            d->newton_total++;
+            d->last_fnorm = fn[i];
+            const double rel = wn > 0 ? dn / wn : dn;
+            if (fn[i] != fn[i] || dn != dn) {
+                inewton[i] = 0;
+                char buf[128];
+                snprintf(buf, sizeof buf, "Newton did not converge (|F|_inf = %g)", fn[i]);
+                fail(i, SULF_ENOTCONV, buf);
+            } else if ((fn[i] < rel ? fn[i] : rel) < d->solver.newton_tol) {
+                inewton[i] = 0;
+                d->t += d->dt;
+                d->steps_total++;
+            }
+        }
+    }
+    for (int i = 0; i < K; i++)
+        if (inewton[i]) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "Newton did not converge (|F|_inf = %g)", fn[i]);
+            fail(i, SULF_ENOTCONV, buf);
+        }
+    return SULF_OK;
+}
+
+// nsteps CN steps of the class hs (each handle's stream is s); status and
+// err per instance; the return code is that of a failure of the class as a
+// whole (device memory, a launch)
+template <int D>
+int lockstep_run(const std::vector<sulf_domain*>& hs, double dt, int nsteps, int* status,
+                 std::vector<std::string>& err, cudaStream_t s) {
+    LockClass<D> C;
+    Scratch mem;
+    mem.s = s;
+    C.h = hs;
+    C.K = (int)hs.size();
+    C.L = hs[0]->L;
+    C.s = s;
+    C.mem = &mem;
+    for (sulf_domain* d : hs) {
+        d->dt = dt;
+        if (d->solver.precision == 1)
+            if (int rc = ensure32(d)) return rc;
+        if (int rc = refresh_ghost_ops(d)) return rc;
+    }
+    if (int rc = C.setup()) return rc;
+    PdlScope pdl(hs[0]->solver.pdl != 0, 0, 0);
+    for (int k = 0; k < nsteps; k++) {
+        if (int rc = lockstep_step<D>(C, status, err)) return rc;
+        bool any = false;
+        for (int i = 0; i < C.K; i++) any = any || status[i] == SULF_OK;
+        if (!any) break;
+    }
+    // the batched launches, shared out over the instances
+    const long long per = C.launches / C.K;
+    for (sulf_domain* d : hs) d->launches += per;
+    return SULF_OK;
+}
+
+}  // namespace
+
+namespace sulf {
+
+// whether a domain can join a lock-step class, and the class key
+bool lockstep_key(sulf_handle h, std::vector<double>& key) {
+    const sulf_domain* d = h;
+    const sulf_solver& v = d->solver;
+    if (v.cycle != 1 || v.smoother != 0 || !v.ghost_compose || d->src_on || d->sbg_on || d->prof || d->L < 2)
+        return false;
+    // the batched coarsest solve stages the right-hand side in shared memory
+    if (d->geo[d->L - 1].nact > kLockMaxCoarsest) return false;
+    for (int l = 0; l < d->L; l++) {
+        const LevelGeo& G = d->geo[l];
+        if (G.ng == 0) continue;
+        const double tau = level_tau(d, l);
+        if (!(G.gop_on && G.gop_bc == d->bc && G.gop_passes == v.ghost_sweeps && G.gop_tau == tau)) return false;
+    }
+    key = {(double)d->dim, (double)d->N, (double)d->L, (double)d->bc, (double)v.precision, (double)v.nu1,
+           (double)v.nu2, (double)v.ghost_sweeps, v.tau_s, v.newton_tol, v.lin_rtol, (double)v.max_newton,
+           (double)v.max_cycles, (double)v.pdl};
+    return true;
+}
+
+int lockstep_advance(const sulf_handle* hs, int K, double dt, int nsteps, int* status, std::vector<std::string>& err,
+                     cudaStream_t s) {
+    std::vector<sulf_domain*> v(hs, hs + K);
+    err.assign(K, std::string());
+    for (int i = 0; i < K; i++) status[i] = SULF_OK;
+    for (sulf_domain* d : v)
+        if (d->stream != s) return sulf_fail(SULF_EINVAL, "lock-step class on mixed streams");
+    int rc = v[0]->dim == 2 ? lockstep_run<2>(v, dt, nsteps, status, err, s)
+                            : lockstep_run<3>(v, dt, nsteps, status, err, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+}  // namespace sulf
 
 // ---------------------------------------------------------------------------
 // Autotuning of the controls that change only speed: the fused-level

@@ -341,6 +341,12 @@ cudaStream_t handle_stream(sulf_handle h);
 void handle_count_launches(sulf_handle h, int n);
 int handle_device(sulf_handle h);       // the device the handle was created on
 void** handle_noalloc_slot(sulf_handle h);  // per-handle cache of a device address (noalloc.cu)
+// lock-step batching (solver.cu): whether a domain can join a class (and the
+// class key: domains with equal keys and equal (dt, nsteps) step together),
+// and nsteps CN steps of K such domains, all on stream s, in lock step
+bool lockstep_key(sulf_handle h, std::vector<double>& key);
+int lockstep_advance(const sulf_handle* hs, int K, double dt, int nsteps, int* status, std::vector<std::string>& err,
+                     cudaStream_t s);
 
 }  // namespace sulf
 
