@@ -321,26 +321,27 @@ int sulf_batch_create(const sulf_handle* handles, int n, int nstreams, sulf_batc
    failing instance's error (all instances are attempted) */
 int sulf_batch_step(sulf_batch b, const double* dt, const int* nsteps);
 int sulf_batch_status(sulf_batch b, int* status); /* per-instance return codes of the last step */
-/* Lock-step mode (on = 1; off = 0, the default) for the next sulf_batch_step
-   calls.  Instances that share dimension, N, number of levels, boundary
-   condition and the solver controls that shape a cycle (precision, nu1, nu2,
-   ghost_sweeps, tau_s, tolerances, iteration caps, pdl), and in the step call
-   dt and nsteps, form one class, provided their solver uses V-cycles (cycle
+/* Lock-step mode for the next sulf_batch_step calls: 0 off (the default);
+   1 on, each class split into chunks of at most 32 instances; m >= 2 on,
+   chunks of at most m instances (chunks run on the worker streams).  Instances that share dimension, N, number of
+   levels, boundary condition and the solver controls that shape a cycle
+   (precision, nu1, nu2, ghost_sweeps, tau_s, tolerances, iteration caps,
+   pdl), and in the step call dt and nsteps, form one class, provided their solver uses V-cycles (cycle
    1), the red-black smoother (smoother 0) and the composed ghost relaxation,
-   and no source term or time-dependent boundary value is set.  A class of two
+   and no source term or time-dependent boundary value is set.  A chunk of two
    or more advances together: every phase of the multigrid cycle of Sec. 3.5
    (a colour of the relaxation of Sec. 3.5.1, the ghost relaxation, the
    residual, the band extension and restriction of Sec. 3.5.2, the
-   prolongation, the coarsest solve) is one launch over all the class's
-   instances, and an instance stops cycling (or leaves the Newton loop of Sec.
+   prolongation of Sec. 3.5.3, the coarsest solve) is one launch over all the
+   chunk's instances, and an instance stops cycling (or leaves the Newton loop of Sec.
    3.4) when its own test says so, so it runs the Newton iterations and cycles
    it runs alone.  The stored FP32 coefficients are used in mixed precision
    (relax_matrix_free has no effect) and the coarsest levels are not fused
    (fuse_below has none), so results agree with stepping each instance alone
    up to rounding.  Other instances run alone as in the default mode.  The
-   class's batched launches are counted into its instances' launch counters
-   in equal shares.  Returns SULF_EINVAL for a bad on. */
-int sulf_batch_set_lockstep(sulf_batch b, int on);
+   chunk's batched launches are counted into its instances' launch counters
+   in equal shares.  Returns SULF_EINVAL for a negative mode. */
+int sulf_batch_set_lockstep(sulf_batch b, int mode);
 /* sulf_autotune of every instance (dt[i] its step), through the process cache:
    one timing per problem class (dim, N, precision, ...), the others take the
    result; out (may be NULL) receives one result per instance */

@@ -414,11 +414,12 @@ class Batch:
         _chk(self.lib, self.lib.sulf_batch_create(arr, len(self.domains), nstreams, ctypes.byref(b)))
         self.b = b
         if lockstep:
-            self.set_lockstep(True)
+            self.set_lockstep(lockstep)
 
-    def set_lockstep(self, on):
-        """sulf_batch_set_lockstep: same-class instances step in lock step"""
-        _chk(self.lib, self.lib.sulf_batch_set_lockstep(self.b, 1 if on else 0))
+    def set_lockstep(self, mode):
+        """sulf_batch_set_lockstep: same-class instances step in lock step
+        (False/0 off, True/1 chunks of at most 32, m >= 2 chunks of at most m)"""
+        _chk(self.lib, self.lib.sulf_batch_set_lockstep(self.b, int(mode)))
 
     def step(self, dt, nsteps):
         n = len(self.domains)

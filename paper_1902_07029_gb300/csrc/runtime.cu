@@ -76,6 +76,8 @@ extern "C" unsigned long long sulf_estimate_device_bytes(int dim, int N, int coa
 // ---------------------------------------------------------------------------
 // batch
 
+constexpr int kLockChunk = 32;  // instances per lock-step chunk (mode 1)
+
 struct sulf_batch_s {
     std::vector<sulf_handle> h;
     std::vector<cudaStream_t> streams;
@@ -109,9 +111,9 @@ extern "C" int sulf_batch_create(const sulf_handle* handles, int n, int nstreams
     return SULF_OK;
 }
 
-extern "C" int sulf_batch_set_lockstep(sulf_batch b, int on) {
-    if (!b || (on != 0 && on != 1)) return sulf_fail(SULF_EINVAL, "invalid arguments");
-    b->lockstep = on;
+extern "C" int sulf_batch_set_lockstep(sulf_batch b, int mode) {
+    if (!b || mode < 0) return sulf_fail(SULF_EINVAL, "invalid arguments");
+    b->lockstep = mode;
     return SULF_OK;
 }
 
@@ -142,14 +144,34 @@ extern "C" int sulf_batch_step(sulf_batch b, const double* dt, const int* nsteps
     } else {
         for (int i = 0; i < n; i++) items.push_back({i});
     }
+    std::vector<double> wi(n);
+    for (int i = 0; i < n; i++) {
+        sulf_stats st;
+        sulf_get_stats(b->h[i], &st);
+        wi[i] = (double)(st.n_inside + st.n_ghost) * nsteps[i];
+    }
+    if (b->lockstep) {
+        // split the classes into chunks of at most `lockstep` instances
+        // (mode 1: kLockChunk), dealt round-robin; the worker streams overlap
+        // one chunk's host tests and per-instance set-up with the others'
+        // cycles (on the 256-star batch, chunks of 32 ran 2-7 % faster than
+        // of 8, of 64, or one chunk per stream)
+        const int cap = b->lockstep >= 2 ? b->lockstep : kLockChunk;
+        std::vector<std::vector<int>> split;
+        for (auto& it : items) {
+            const int k = (int)it.size();
+            const int chunks = (k + cap - 1) / cap;
+            for (int c = 0; c < chunks; c++) {
+                split.push_back({});
+                for (int q = c; q < k; q += chunks) split.back().push_back(it[q]);
+            }
+        }
+        items.swap(split);
+    }
     // largest work first: active nodes times steps
     std::vector<double> work(items.size(), 0.0);
     for (size_t j = 0; j < items.size(); j++)
-        for (int i : items[j]) {
-            sulf_stats st;
-            sulf_get_stats(b->h[i], &st);
-            work[j] += (double)(st.n_inside + st.n_ghost) * nsteps[i];
-        }
+        for (int i : items[j]) work[j] += wi[i];
     std::vector<size_t> order(items.size());
     for (size_t j = 0; j < order.size(); j++) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return work[a] > work[c]; });

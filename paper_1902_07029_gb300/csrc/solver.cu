@@ -1499,9 +1499,9 @@ BLev<D, T> blev_of(sulf_domain* d, LevelVec<T>* V, int l) {
     return b;
 }
 
-// device memory of one lock-step call, released at its end
+// device and pinned host memory of one lock-step call, released at its end
 struct Scratch {
-    std::vector<void*> p;
+    std::vector<void*> p, ph;
     cudaStream_t s;
     void* get(size_t n) {
         void* q = nullptr;
@@ -1512,9 +1512,35 @@ struct Scratch {
         p.push_back(q);
         return q;
     }
+    void* get_host(size_t n) {
+        void* q = nullptr;
+        if (cudaMallocHost(&q, n < 256 ? 256 : n) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ph.push_back(q);
+        return q;
+    }
     ~Scratch() {
+        cudaStreamSynchronize(s);
         for (void* q : p) cudaFreeAsync(q, s);
         cudaStreamSynchronize(s);
+        for (void* q : ph) cudaFreeHost(q);
+    }
+};
+
+// One phase of a lock-step step (its work enqueued by a function on the
+// class's stream), replayed from a CUDA graph captured at its first run: the
+// kernel parameters of every phase are fixed for the whole call (pointers,
+// dt, the models), only device data changes between runs.  The launch
+// counts of the captured run are added again at every replay.
+struct PhaseGraph {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;
+    long long dclass = 0;
+    std::vector<long long> dinst;
+    ~PhaseGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
     }
 };
 
@@ -1537,8 +1563,86 @@ struct LockClass {
     int* dactive = nullptr;
     std::vector<int> active;
     unsigned long long* dnorm = nullptr;
-    std::vector<unsigned long long> hnorm;
+    unsigned long long* hnorm = nullptr;  // pinned
     long long launches = 0;
+    bool graphs = true;
+    // branches of the per-instance phases (instance i on aux[i % naux])
+    static constexpr int kMaxAux = 8;
+    cudaStream_t aux[kMaxAux] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxAux] = {};
+    int naux = 0;
+
+    ~LockClass() {
+        for (int j = 0; j < naux; j++) {
+            if (aux[j]) cudaStreamDestroy(aux[j]);
+            if (ev_join[j]) cudaEventDestroy(ev_join[j]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
+
+    // fn(i, stream) for every instance, on parallel branches joined back
+    // into the class's stream (each handle's stream is the branch's meanwhile)
+    template <class F>
+    int per_instance(F&& fn) {
+        SULF_CUDA_TRY(cudaEventRecord(ev_fork, s));
+        for (int j = 0; j < naux; j++) SULF_CUDA_TRY(cudaStreamWaitEvent(aux[j], ev_fork, 0));
+        int rc = SULF_OK;
+        for (int i = 0; i < K && rc == SULF_OK; i++) {
+            cudaStream_t b = aux[i % naux];
+            h[i]->stream = b;
+            rc = fn(i, b);
+            h[i]->stream = s;
+        }
+        for (int j = 0; j < naux; j++) {
+            SULF_CUDA_TRY(cudaEventRecord(ev_join[j], aux[j]));
+            SULF_CUDA_TRY(cudaStreamWaitEvent(s, ev_join[j], 0));
+        }
+        return rc;
+    }
+
+    // run phase fn: replay its graph, or capture it (falling back to direct
+    // launches where capture fails), then wait for it
+    template <class F>
+    int run_phase(PhaseGraph& g, F&& fn) {
+        if (g.exec) {
+            SULF_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+            launches += g.dclass;
+            for (int i = 0; i < K; i++) h[i]->launches += g.dinst[i];
+        } else {
+            const long long c0 = launches;
+            std::vector<long long> i0(K);
+            for (int i = 0; i < K; i++) i0[i] = h[i]->launches;
+            bool done = false;
+            if (graphs && !g.failed && cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                int rc = fn();
+                cudaGraph_t gr = nullptr;
+                cudaError_t e = cudaStreamEndCapture(s, &gr);
+                if (rc == SULF_OK && e == cudaSuccess && gr && take_launch_error().empty() &&
+                    cudaGraphInstantiate(&g.exec, gr, 0) == cudaSuccess) {
+                    g.dclass = launches - c0;
+                    g.dinst.resize(K);
+                    for (int i = 0; i < K; i++) g.dinst[i] = h[i]->launches - i0[i];
+                    done = cudaGraphLaunch(g.exec, s) == cudaSuccess;
+                }
+                if (gr) cudaGraphDestroy(gr);
+                if (!done) {
+                    if (g.exec) cudaGraphExecDestroy(g.exec);
+                    g.exec = nullptr;
+                    g.failed = true;
+                    cudaGetLastError();
+                    take_launch_error();
+                    launches = c0;
+                    for (int i = 0; i < K; i++) h[i]->launches = i0[i];
+                }
+            }
+            if (!done)
+                if (int rc = fn()) return rc;
+        }
+        SULF_CUDA_TRY(cudaStreamSynchronize(s));
+        std::string e = take_launch_error();
+        if (!e.empty()) return sulf_fail(SULF_EDEVICE, "lock-step launch failed: " + e);
+        return SULF_OK;
+    }
 
     int upload_blocks(Blocks& b, const std::vector<long long>& units, int per_cta) {
         std::vector<int> pre(K + 1, 0);
@@ -1594,9 +1698,16 @@ struct LockClass {
         if (int rc = upload_blocks(coarse, rows, kBatchT / 32)) return rc;
         dactive = (int*)mem->get(sizeof(int) * K);
         dnorm = (unsigned long long*)mem->get(sizeof(unsigned long long) * K);
-        if (!dactive || !dnorm) return sulf_fail(SULF_ENOMEM, "out of device memory");
+        hnorm = (unsigned long long*)mem->get_host(sizeof(unsigned long long) * K);
+        if (!dactive || !dnorm || !hnorm) return sulf_fail(SULF_ENOMEM, "out of memory");
         active.assign(K, 0);
-        hnorm.assign(K, 0);
+        SULF_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        naux = std::min(K, kMaxAux);
+        for (int j = 0; j < naux; j++) {
+            SULF_CUDA_TRY(cudaStreamCreateWithFlags(&aux[j], cudaStreamNonBlocking));
+            SULF_CUDA_TRY(cudaEventCreateWithFlags(&ev_join[j], cudaEventDisableTiming));
+        }
+        graphs = h[0]->solver.graphs != 0;
         SULF_CUDA_TRY(cudaStreamSynchronize(s));
         return SULF_OK;
     }
@@ -1639,7 +1750,7 @@ struct LockClass {
     }
 
     // one cycle of every active instance's linear solve, then the FP64
-    // defect with each instance's max-norm (read back)
+    // defect with each instance's max-norm (copied to hnorm)
     int cycle_body() {
         const bool mixed = h[0]->solver.precision == 1;
         if (mixed) {
@@ -1657,11 +1768,7 @@ struct LockClass {
         if (mixed)
             launches += launch_batched_mixed<D>(BPhase::to_float, l64[0], l32[0], act[0].d, act[0].total, K,
                                                 dactive, s);
-        SULF_CUDA_TRY(
-            cudaMemcpyAsync(hnorm.data(), dnorm, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, s));
-        SULF_CUDA_TRY(cudaStreamSynchronize(s));
-        std::string e = take_launch_error();
-        if (!e.empty()) return sulf_fail(SULF_EDEVICE, "lock-step launch failed: " + e);
+        SULF_CUDA_TRY(cudaMemcpyAsync(hnorm, dnorm, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, s));
         return SULF_OK;
     }
 };
@@ -1670,31 +1777,44 @@ struct LockClass {
 // and cycles in lock step; an instance that fails gets its code in status[i]
 // and its message in err[i] (and keeps the state it failed in)
 template <int D>
-int lockstep_step(LockClass<D>& C, int* status, std::vector<std::string>& err) {
+struct LockGraphs {
+    PhaseGraph begin, prepare, cycle, update;
+};
+
+// The per-instance phases run for every instance of the class, whatever its
+// state: an instance that left its Newton loop (converged, or failed) gets a
+// zero update (its x is zeroed by the set-up and its cycles are masked), so
+// its state does not change, and its norms are not read.
+template <int D>
+int lockstep_step(LockClass<D>& C, LockGraphs<D>& P, int* status, std::vector<std::string>& err) {
     const int K = C.K;
+    const sulf_solver& sv = C.h[0]->solver;
     auto fail = [&](int i, int code, const std::string& msg) {
         status[i] = sulf_fail(code, msg);
         err[i] = msg;
     };
     std::vector<double> fn(K, 0.0);
-    for (int i = 0; i < K; i++) {
-        if (status[i] != SULF_OK) continue;
-        sulf_domain* d = C.h[i];
-        const LevelGeo& G0 = d->geo[0];
-        FConst fc = make_fconst(d);
-        SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, C.s));
-        d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, C.s);
-        SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, C.s));
-        d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm, C.s);
-        SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, C.s));
-        d->newton_last = 0;
-        d->cycles_last = 0;
-    }
-    SULF_CUDA_TRY(cudaStreamSynchronize(C.s));
+    // the old-time part of each CN system and its first residual
+    int rc = C.run_phase(P.begin, [&] {
+        return C.per_instance([&](int i, cudaStream_t b) {
+            sulf_domain* d = C.h[i];
+            const LevelGeo& G0 = d->geo[0];
+            FConst fc = make_fconst(d);
+            SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, b));
+            d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, b);
+            SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, b));
+            d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm, b);
+            SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, b));
+            return SULF_OK;
+        });
+    });
+    if (rc) return rc;
     std::vector<int> inewton(K, 0);  // instance still in its Newton loop
     for (int i = 0; i < K; i++) {
         if (status[i] != SULF_OK) continue;
         sulf_domain* d = C.h[i];
+        d->newton_last = 0;
+        d->cycles_last = 0;
         fn[i] = bits_to_double(d->hnorm[0]);
         if (fn[i] < d->solver.newton_tol) {
             d->t += d->dt;
@@ -1704,33 +1824,34 @@ int lockstep_step(LockClass<D>& C, int* status, std::vector<std::string>& err) {
             inewton[i] = 1;
         }
     }
-    const sulf_solver& sv = C.h[0]->solver;
     for (int k = 1; k <= sv.max_newton; k++) {
         bool any = false;
         for (int i = 0; i < K; i++) any = any || inewton[i];
         if (!any) break;
         // per instance: the Jacobian of this Newton iteration on every level
-        for (int i = 0; i < K; i++) {
-            if (!inewton[i]) continue;
-            sulf_domain* d = C.h[i];
-            const LevelGeo& G0 = d->geo[0];
-            SULF_CUDA_TRY(cudaMemsetAsync(d->v64[0].x, 0, sizeof(double2) * G0.nn, C.s));
-            int rc;
-            if (sv.precision == 0) {
-                rc = MG<D, double>{d, d->v64}.prepare();
-            } else {
-                d->launches += launch_to_float(G0, d->W, d->v32[0].Wc, C.s);
-                d->launches += launch_coefs<D, double>(G0, d->v64[0], make_coef<double>(d, 0), C.s);
-                rc = MG<D, float>{d, d->v32}.prepare();
-                if (!rc) d->launches += launch_to_float(G0, d->v64[0].rhs, d->v32[0].rhs, C.s);
-                // the batched cycles zero the FP32 error at the active nodes
-                // only; the others stay zero from here
-                SULF_CUDA_TRY(cudaMemsetAsync(d->v32[0].x, 0, sizeof(float2) * G0.nn, C.s));
-            }
-            if (rc) return rc;
-            SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, C.s));
-        }
-        SULF_CUDA_TRY(cudaStreamSynchronize(C.s));
+        rc = C.run_phase(P.prepare, [&] {
+            return C.per_instance([&](int i, cudaStream_t b) {
+                sulf_domain* d = C.h[i];
+                const LevelGeo& G0 = d->geo[0];
+                SULF_CUDA_TRY(cudaMemsetAsync(d->v64[0].x, 0, sizeof(double2) * G0.nn, b));
+                int r;
+                if (sv.precision == 0) {
+                    r = MG<D, double>{d, d->v64}.prepare();
+                } else {
+                    d->launches += launch_to_float(G0, d->W, d->v32[0].Wc, b);
+                    d->launches += launch_coefs<D, double>(G0, d->v64[0], make_coef<double>(d, 0), b);
+                    r = MG<D, float>{d, d->v32}.prepare();
+                    if (!r) d->launches += launch_to_float(G0, d->v64[0].rhs, d->v32[0].rhs, b);
+                    // the batched cycles zero the FP32 error at the active
+                    // nodes only; the others stay zero from here
+                    SULF_CUDA_TRY(cudaMemsetAsync(d->v32[0].x, 0, sizeof(float2) * G0.nn, b));
+                }
+                if (r) return r;
+                SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, b));
+                return SULF_OK;
+            });
+        });
+        if (rc) return rc;
         for (int i = 0; i < K; i++) {
             C.active[i] = inewton[i];
             if (inewton[i] && *(int*)(C.h[i]->hnorm + 6)) {
@@ -1747,7 +1868,7 @@ int lockstep_step(LockClass<D>& C, int* status, std::vector<std::string>& err) {
             bool on = false;
             for (int i = 0; i < K; i++) on = on || C.active[i];
             if (!on) break;
-            if (int rc = C.cycle_body()) return rc;
+            if ((rc = C.run_phase(P.cycle, [&] { return C.cycle_body(); }))) return rc;
             bool changed = false;
             for (int i = 0; i < K; i++) {
                 if (!C.active[i]) continue;
@@ -1765,23 +1886,25 @@ int lockstep_step(LockClass<D>& C, int* status, std::vector<std::string>& err) {
                 if (int rc = C.set_active()) return rc;
         }
         // per instance: the Newton update, the new residual and the test
+        rc = C.run_phase(P.update, [&] {
+            return C.per_instance([&](int i, cudaStream_t b) {
+                sulf_domain* d = C.h[i];
+                const LevelGeo& G0 = d->geo[0];
+                FConst fc = make_fconst(d);
+                SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, b));
+                d->launches += launch_newton_update(G0, d->W, d->v64[0].x, d->dnorm, b);
+                d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm + 2, b);
+                SULF_CUDA_TRY(
+                    cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, b));
+                return SULF_OK;
+            });
+        });
+        if (rc) return rc;
         for (int i = 0; i < K; i++) {
             if (!inewton[i]) continue;
             sulf_domain* d = C.h[i];
-            const LevelGeo& G0 = d->geo[0];
-            FConst fc = make_fconst(d);
             d->cycles_last += cyc[i];
             d->cycles_total += cyc[i];
-            SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, C.s));
-            d->launches += launch_newton_update(G0, d->W, d->v64[0].x, d->dnorm, C.s);
-            d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm + 2, C.s);
-            SULF_CUDA_TRY(
-                cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, C.s));
-        }
-        SULF_CUDA_TRY(cudaStreamSynchronize(C.s));
-        for (int i = 0; i < K; i++) {
-            if (!inewton[i]) continue;
-            sulf_domain* d = C.h[i];
             const double dn = bits_to_double(d->hnorm[0]), wn = bits_to_double(d->hnorm[1]);
             fn[i] = bits_to_double(d->hnorm[2]);
             d->newton_last = k;
@@ -1831,8 +1954,9 @@ int lockstep_run(const std::vector<sulf_domain*>& hs, double dt, int nsteps, int
     }
     if (int rc = C.setup()) return rc;
     PdlScope pdl(hs[0]->solver.pdl != 0, 0, 0);
+    LockGraphs<D> P;
     for (int k = 0; k < nsteps; k++) {
-        if (int rc = lockstep_step<D>(C, status, err)) return rc;
+        if (int rc = lockstep_step<D>(C, P, status, err)) return rc;
         bool any = false;
         for (int i = 0; i < C.K; i++) any = any || status[i] == SULF_OK;
         if (!any) break;

@@ -167,3 +167,16 @@ def test_ineligible_solver_runs_alone(sulfmg):
             d.close()
     for (s0, c0), (s1, c1) in zip(*res):
         assert np.array_equal(s0, s1) and np.array_equal(c0, c1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lockstep_graphs_are_bitwise_neutral(sulfmg, precision):
+    """the phases replayed from captured graphs (with the per-instance work on
+    parallel branches) compute exactly what direct launches compute"""
+    specs = [_star_spec(128, 740 + k) for k in range(5)] + [_box_spec(32, 0.9), _box_spec(32, 0.6)]
+    runs = [_run_lockstep(sulfmg, specs, precision=precision, graphs=g) for g in (0, 1)]
+    for (st0, o0), (st1, o1) in [runs]:
+        assert st0 == st1 == [0] * len(specs)
+        for ((s0, c0, _), a0), ((s1, c1, _), a1) in zip(o0, o1):
+            assert np.array_equal(s0, s1) and np.array_equal(c0, c1)
+            assert a0["cycles_total"] == a1["cycles_total"] and a0["newton_total"] == a1["newton_total"]
