@@ -326,7 +326,8 @@ int sulf_batch_status(sulf_batch b, int* status); /* per-instance return codes o
    chunks of at most m instances (chunks run on the worker streams).  Instances that share dimension, N, number of
    levels, boundary condition and the solver controls that shape a cycle
    (precision, nu1, nu2, ghost_sweeps, tau_s, tolerances, iteration caps,
-   pdl), and in the step call dt and nsteps, form one class, provided their solver uses V-cycles (cycle
+   pdl, in mixed precision whether relax_matrix_free is 0), and in the step
+   call dt and nsteps, form one class, provided their solver uses V-cycles (cycle
    1), the red-black smoother (smoother 0) and the composed ghost relaxation,
    and no source term or time-dependent boundary value is set.  A chunk of two
    or more advances together: every phase of the multigrid cycle of Sec. 3.5
@@ -335,10 +336,12 @@ int sulf_batch_status(sulf_batch b, int* status); /* per-instance return codes o
    prolongation of Sec. 3.5.3, the coarsest solve) is one launch over all the
    chunk's instances, and an instance stops cycling (or leaves the Newton loop of Sec.
    3.4) when its own test says so, so it runs the Newton iterations and cycles
-   it runs alone.  The stored FP32 coefficients are used in mixed precision
-   (relax_matrix_free has no effect) and the coarsest levels are not fused
-   (fuse_below has none), so results agree with stepping each instance alone
-   up to rounding.  Other instances run alone as in the default mode.  The
+   it runs alone.  In mixed precision relax_matrix_free 1 and 2 both select
+   the matrix-free FP32 relaxation (no temporally blocked sweep), and the
+   coarse levels from the first
+   level that every instance's fuse_below threshold fuses run as one launch
+   with one CTA per instance, so results agree with stepping each instance
+   alone up to rounding.  Other instances run alone as in the default mode.  The
    chunk's batched launches are counted into its instances' launch counters
    in equal shares.  Returns SULF_EINVAL for a negative mode. */
 int sulf_batch_set_lockstep(sulf_batch b, int mode);

@@ -279,56 +279,16 @@ __global__ void __launch_bounds__(kT) k_relax_mf(const int* __restrict__ list, i
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const long long st[3] = {1, st1, st2};
     long long p = 0;
-    float g[2 * D], e[2 * D];
-    float i00 = 0, i01 = 0, i10 = 0, i11 = 0;
+    stages::MfCoef<D> k;
     if (t < cnt) {
         p = list[t];
-        const float2 w = Wc[p];
-        const float s = w.x, cp = w.y;
-        const float ph = c.alpha * cp + c.beta;
-        float sg = 0, se = 0;
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-#pragma unroll
-            for (int dir = 0; dir < 2; dir++) {
-                const float2 wq = Wc[dir ? p - st[a] : p + st[a]];
-                const float gq = c.kap * ((c.alpha * wq.y + c.beta) + ph);
-                const float eq = c.kap * c.alpha * (s - wq.x);
-                g[2 * a + dir] = gq;
-                e[2 * a + dir] = eq;
-                sg += gq;
-                se += eq;
-            }
-        }
-        const float Pcs = c.a2ms * ph * cp;
-        const float Pcc = c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
-        const float Pss = ph * c.idt + c.a2mc * ph * cp + sg;
-        const float Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s) + se;
-        const float inv = 1.0f / (Pss * Pcc - Psc * Pcs);
-        i00 = Pcc * inv;
-        i01 = -Psc * inv;
-        i10 = -Pcs * inv;
-        i11 = Pss * inv;
+        k = stages::mf_coef<D>(p, Wc, c, st);
     }
     const int sg = t < snap_n ? sidx[t] : 0;
     pdl_enter();
     if (t < snap_n) snap[t] = reinterpret_cast<const float*>(x + sg)[0];
     if (t >= cnt) return;
-    const float2 b = rhs[p];
-    float r = b.x;
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        const float2 xe = x[p + st[a]];
-        const float2 xw = x[p - st[a]];
-        r = __fmaf_rn(g[2 * a], xe.x, r);
-        r = __fmaf_rn(-e[2 * a], xe.y, r);
-        r = __fmaf_rn(g[2 * a + 1], xw.x, r);
-        r = __fmaf_rn(-e[2 * a + 1], xw.y, r);
-    }
-    float2 out;
-    out.x = __fmaf_rn(i00, r, i01 * b.y);
-    out.y = __fmaf_rn(i10, r, i11 * b.y);
-    x[p] = out;
+    stages::mf_apply<D>(p, k, rhs, x, st);
 }
 
 // ---------------------------------------------------------------------------

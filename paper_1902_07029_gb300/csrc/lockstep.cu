@@ -62,6 +62,29 @@ __global__ void __launch_bounds__(kBT) kb_relax(const BLev<D, T>* __restrict__ l
     if (t < cnt) stages::relax_node<D, T, false, false>(list[t], L.cf, L.rhs, L.x, st);
 }
 
+// the same with the coefficients formed from Wc (FP32): fewer bytes per
+// update than the stored coefficient arrays
+template <int D>
+__global__ void __launch_bounds__(kBT) kb_relax_mf(const BLev<D, float>* __restrict__ lv, const int* __restrict__ pre,
+                                                    int K, const int* __restrict__ active, int colour) {
+    const int i = find_instance(pre, K, blockIdx.x);
+    if (!active[i]) return;
+    const BLev<D, float>& L = lv[i];
+    const int t = (blockIdx.x - pre[i]) * kBT + threadIdx.x;
+    const long long st[3] = {1, L.st1, L.st2};
+    const int cnt = colour ? L.ls.n1 : L.ls.n0;
+    const int* list = colour ? L.ls.l1 : L.ls.l0;
+    long long p = 0;
+    stages::MfCoef<D> k;
+    if (t < cnt) {
+        p = list[t];
+        k = stages::mf_coef<D>(p, L.Wc, L.c, st);
+    }
+    pdl_enter();
+    if (colour == 1 && t < L.ls.ng) L.snap[t] = reinterpret_cast<const float*>(L.x + L.ls.lg[t])[0];
+    if (t < cnt) stages::mf_apply<D>(p, k, L.rhs, L.x, st);
+}
+
 // the composed ghost relaxation: kGopLanes lanes per ghost row
 template <int D, typename T>
 __global__ void __launch_bounds__(kBT) kb_ghost_op(const BLev<D, T>* __restrict__ lv, const int* __restrict__ pre,
@@ -227,6 +250,11 @@ int launch_batched(BPhase ph, const BLev<D, T>* lv, const BLev<D, T>* lc, const 
     switch (ph) {
         case BPhase::relax:
             launch_k(kb_relax<D, T>, (unsigned)nblocks, kBT, 0, s, lv, pre, K, active, colour);
+            break;
+        case BPhase::relax_mf:
+            if (!std::is_same<T, float>::value) return 0;
+            launch_k(kb_relax_mf<D>, (unsigned)nblocks, kBT, 0, s, reinterpret_cast<const BLev<D, float>*>(lv), pre,
+                     K, active, colour);
             break;
         case BPhase::ghost_op:
             launch_k(kb_ghost_op<D, T>, (unsigned)nblocks, kBT, 0, s, lv, pre, K, active);

@@ -14,6 +14,8 @@ struct BLev {
     stages::Lists ls;            // inside colour 0, colour 1, ghosts
     stages::GhostTab<T> tb;      // boundary rows (residual)
     stages::CoefPtr<D, T> cf;    // stencil coefficients
+    Coef<T> c;                   // the level's constants (matrix-free FP32 relaxation)
+    const typename V2<T>::t* Wc; // the (s, c) the coefficients are formed from
     T2* rhs;
     T2* x;
     T2* res;
@@ -39,14 +41,15 @@ struct BLev {
     const T* Ainv;
 };
 
-enum class BPhase { relax, ghost_op, residual, extend, restrict_to, prolong_from, coarsest, zero32, accumulate,
-                    to_float };
+enum class BPhase { relax, relax_mf, ghost_op, residual, extend, restrict_to, prolong_from, coarsest, zero32,
+                    accumulate, to_float };
 
 // one launch of phase ph over the instances' work lists: CTA b serves the
 // instance i with pre[i] <= b < pre[i+1]; masked instances (active[i] == 0)
 // are skipped.  lc: the coarse level of a restriction / prolongation (lv is
 // the fine one); colour: of a relaxation; norms: per-instance max-norm slots
-// of a residual (or NULL); smem: dynamic shared memory of the coarsest solve
+// of a residual (or NULL); smem: dynamic shared memory of the coarsest solve.
+// relax_mf (FP32 only): the relaxation with the coefficients formed from Wc.
 template <int D, typename T>
 int launch_batched(BPhase ph, const BLev<D, T>* lv, const BLev<D, T>* lc, const int* pre, int nblocks, int K,
                    const int* active, int colour, unsigned long long* norms, size_t smem, cudaStream_t s);

@@ -172,6 +172,69 @@ __device__ __forceinline__ void relax_apply(long long p, const InsideCoef<D, T>&
     x[p] = out;
 }
 
+// Matrix-free FP32 collective update (Eq. matrixP with the Jacobian entries
+// of Eqs. JssI, JscI, JcsI, JccI formed from Wc on the fly): the stencil
+// coefficients of inside node p and the inverse of its 2x2 block, from the
+// (s, c) of the node and its axis neighbours (neighbour order +a, -a per axis)
+template <int D>
+struct MfCoef {
+    float g[2 * D], e[2 * D];
+    float i00, i01, i10, i11;
+};
+
+template <int D>
+__device__ __forceinline__ MfCoef<D> mf_coef(long long p, const float2* Wc, const Coef<float>& c, const long long* st) {
+    MfCoef<D> k;
+    const float2 w = Wc[p];
+    const float s = w.x, cp = w.y;
+    const float ph = c.alpha * cp + c.beta;
+    float sg = 0, se = 0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+#pragma unroll
+        for (int dir = 0; dir < 2; dir++) {
+            const float2 wq = Wc[dir ? p - st[a] : p + st[a]];
+            const float gq = c.kap * ((c.alpha * wq.y + c.beta) + ph);
+            const float eq = c.kap * c.alpha * (s - wq.x);
+            k.g[2 * a + dir] = gq;
+            k.e[2 * a + dir] = eq;
+            sg += gq;
+            se += eq;
+        }
+    }
+    const float Pcs = c.a2ms * ph * cp;
+    const float Pcc = c.idt + c.a2ms * (c.alpha * s * cp + ph * s);
+    const float Pss = ph * c.idt + c.a2mc * ph * cp + sg;
+    const float Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s) + se;
+    const float inv = 1.0f / (Pss * Pcc - Psc * Pcs);
+    k.i00 = Pcc * inv;
+    k.i01 = -Psc * inv;
+    k.i10 = -Pcs * inv;
+    k.i11 = Pss * inv;
+    return k;
+}
+
+// x_p <- P^{-1} (b - (J - P) x) from the coefficients of mf_coef
+template <int D>
+__device__ __forceinline__ void mf_apply(long long p, const MfCoef<D>& k, const float2* rhs, float2* x,
+                                         const long long* st) {
+    const float2 b = rhs[p];
+    float r = b.x;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        const float2 xe = x[p + st[a]];
+        const float2 xw = x[p - st[a]];
+        r = __fmaf_rn(k.g[2 * a], xe.x, r);
+        r = __fmaf_rn(-k.e[2 * a], xe.y, r);
+        r = __fmaf_rn(k.g[2 * a + 1], xw.x, r);
+        r = __fmaf_rn(-k.e[2 * a + 1], xw.y, r);
+    }
+    float2 out;
+    out.x = __fmaf_rn(k.i00, r, k.i01 * b.y);
+    out.y = __fmaf_rn(k.i10, r, k.i11 * b.y);
+    x[p] = out;
+}
+
 // relax_value when every x is zero (the coarse-grid error right after
 // restriction): the same operations with zero operands, so the same bits
 template <int D, typename T, bool PW>

@@ -1475,6 +1475,8 @@ BLev<D, T> blev_of(sulf_domain* d, LevelVec<T>* V, int l) {
     b.ls = stages::make_lists(G);
     b.tb = stages::ghost_tab<T>(G);
     b.cf = stages::coef_ptr<D, T>(v);
+    b.c = make_coef<T>(d, l);
+    b.Wc = v.Wc;
     b.rhs = v.rhs;
     b.x = v.x;
     b.res = v.res;
@@ -1566,6 +1568,11 @@ struct LockClass {
     unsigned long long* hnorm = nullptr;  // pinned
     long long launches = 0;
     bool graphs = true;
+    // the fused coarse levels ltail .. L-1 (-1: none), one CTA per instance:
+    // the instances' descriptors (device array) and level geometry
+    int ltail = -1;
+    const void* const* dtail = nullptr;
+    std::vector<const LevelGeo*> geos;
     // branches of the per-instance phases (instance i on aux[i % naux])
     static constexpr int kMaxAux = 8;
     cudaStream_t aux[kMaxAux] = {};
@@ -1708,6 +1715,31 @@ struct LockClass {
             SULF_CUDA_TRY(cudaEventCreateWithFlags(&ev_join[j], cudaEventDisableTiming));
         }
         graphs = h[0]->solver.graphs != 0;
+        // the fused coarse levels: from the first level that every
+        // instance's threshold fuses
+        for (int i = 0; i < K; i++) {
+            const int t = tail_level(h[i]);
+            if (t < 0) {
+                ltail = -1;
+                break;
+            }
+            ltail = std::max(ltail, t);
+        }
+        if (ltail >= 0) {
+            std::vector<const void*> dd(K);
+            for (int i = 0; i < K; i++) {
+                sulf_domain* d = h[i];
+                int rc = mixed ? ensure_tail<D, float>(d, d->v32) : ensure_tail<D, double>(d, d->v64);
+                if (rc) return rc;
+                dd[i] = d->tail_desc[mixed ? 1 : 0];
+                geos.push_back(d->geo);
+            }
+            void* p = mem->get(sizeof(void*) * K);
+            if (!p) return sulf_fail(SULF_ENOMEM, "out of device memory");
+            SULF_CUDA_TRY(cudaMemcpyAsync(p, dd.data(), sizeof(void*) * K, cudaMemcpyHostToDevice, s));
+            SULF_CUDA_TRY(cudaStreamSynchronize(s));
+            dtail = (const void* const*)p;
+        }
         SULF_CUDA_TRY(cudaStreamSynchronize(s));
         return SULF_OK;
     }
@@ -1720,16 +1752,23 @@ struct LockClass {
 
     template <typename T>
     void relax(const BLev<D, T>* const* lv, int l) {
-        launches += launch_batched<D, T>(BPhase::relax, lv[l], nullptr, red[l].d, red[l].total, K, dactive, 0,
-                                         nullptr, 0, s);
-        launches += launch_batched<D, T>(BPhase::relax, lv[l], nullptr, black[l].d, black[l].total, K, dactive, 1,
-                                         nullptr, 0, s);
+        // FP32: coefficients formed from Wc where the solver asks for it
+        const BPhase ph = std::is_same<T, float>::value && h[0]->solver.relax_matrix_free ? BPhase::relax_mf
+                                                                                          : BPhase::relax;
+        launches += launch_batched<D, T>(ph, lv[l], nullptr, red[l].d, red[l].total, K, dactive, 0, nullptr, 0, s);
+        launches += launch_batched<D, T>(ph, lv[l], nullptr, black[l].d, black[l].total, K, dactive, 1, nullptr, 0,
+                                         s);
         launches += launch_batched<D, T>(BPhase::ghost_op, lv[l], nullptr, gop[l].d, gop[l].total, K, dactive, 0,
                                          nullptr, 0, s);
     }
 
     template <typename T>
     void cycle(const BLev<D, T>* const* lv, int l) {
+        if (l == ltail) {
+            launches += launch_tail_batched<D, T>(dtail, K, dactive, geos.data(), l, L, h[0]->solver, h[0]->bc,
+                                                  true, s);
+            return;
+        }
         if (l == L - 1) {
             launches += launch_batched<D, T>(BPhase::coarsest, lv[l], nullptr, coarse.d, coarse.total, K, dactive, 0,
                                              nullptr, sizeof(T) * 2 * (size_t)max_nact, s);
@@ -1987,7 +2026,7 @@ bool lockstep_key(sulf_handle h, std::vector<double>& key) {
     }
     key = {(double)d->dim, (double)d->N, (double)d->L, (double)d->bc, (double)v.precision, (double)v.nu1,
            (double)v.nu2, (double)v.ghost_sweeps, v.tau_s, v.newton_tol, v.lin_rtol, (double)v.max_newton,
-           (double)v.max_cycles, (double)v.pdl};
+           (double)v.max_cycles, (double)v.pdl, (double)(v.precision == 1 && v.relax_matrix_free != 0)};
     return true;
 }
 

@@ -278,6 +278,12 @@ int upload_tail_desc(const LevelGeo* G, const LevelVec<T>* V, int L, void* dev, 
 template <int D, typename T>
 int launch_tail(const void* dev_desc, const LevelGeo* G, int l0, int L, const sulf_solver& sv, int bc, bool compose,
                 cudaStream_t s);
+// the fused levels l0 .. L-1 of K instances' cycles in one launch (one CTA
+// per instance; dev_descs: device array of the instances' descriptors; G[i]:
+// instance i's level geometry; masked instances skipped)
+template <int D, typename T>
+int launch_tail_batched(const void* const* dev_descs, int K, const int* active, const LevelGeo* const* G, int l0,
+                        int L, const sulf_solver& sv, int bc, bool compose, cudaStream_t s);
 
 // factor of tau_s for Neumann ghost rows on a level of spacing h (Eq.
 // CFLcondN): 4 h / (3 sqrt(dim)), i.e. 2 sqrt(2) h / 3 in 2-D

@@ -9,6 +9,7 @@
 // down and back up with __syncthreads between phases, on L1-resident data.
 // Each phase calls the same per-node stage functions as the per-level kernels
 // (mg_stages.cuh), in the same order, so the result is the same.
+#include <algorithm>
 #include <mutex>
 
 #include "mg_stages.cuh"
@@ -154,9 +155,9 @@ __device__ void tail_relax(const TailLevel<T>& v, const TailParams& pr, int tid,
     }
 }
 
+// the fused levels pr.l0 .. pr.L-1 of one instance's cycle, by the whole CTA
 template <int D, typename T>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T>* __restrict__ lv, TailParams pr) {
-    pdl_enter();
+__device__ __forceinline__ void tail_cycle(const TailLevel<T>* __restrict__ lv, const TailParams& pr) {
     typedef typename V2<T>::t T2;
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -269,6 +270,22 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T>* __
     }
 }
 
+template <int D, typename T>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T>* __restrict__ lv, TailParams pr) {
+    pdl_enter();
+    tail_cycle<D, T>(lv, pr);
+}
+
+// the fused levels of many instances (lock-step batching): CTA i runs
+// instance i's, unless it is masked
+template <int D, typename T>
+__global__ void __launch_bounds__(kTailThreads, 1)
+    k_tail_batched(const TailLevel<T>* const* __restrict__ lvs, const int* __restrict__ active, TailParams pr) {
+    if (!active[blockIdx.x]) return;
+    pdl_enter();
+    tail_cycle<D, T>(lvs[blockIdx.x], pr);
+}
+
 template <typename T>
 TailLevel<T> describe(const LevelGeo& G, const LevelVec<T>& V) {
     TailLevel<T> t;
@@ -378,6 +395,50 @@ int launch_tail(const void* dev_desc, const LevelGeo* G, int l0, int L, const su
     return SULF_OK;
 }
 
+template <int D, typename T>
+int launch_tail_batched(const void* const* dev_descs, int K, const int* active, const LevelGeo* const* G, int l0,
+                        int L, const sulf_solver& sv, int bc, bool compose, cudaStream_t s) {
+    TailParams pr = make_params(l0, L, sv, bc, compose, D);
+    // staging as in launch_tail, decided for all instances at once: on where
+    // every instance's data fits; the shared memory is the largest need
+    size_t gop_max = 0, all_max = 0;
+    bool gop_fits = compose, all_fit = true;
+    for (int i = 0; i < K; i++) {
+        size_t off = 0;
+        if (compose)
+            for (int l = l0; l < L; l++)
+                if (G[i][l].gop_on && G[i][l].ng > 0) off += gop_stage_bytes(G[i][l].ng, (int)G[i][l].gop_nnz, sizeof(T));
+        gop_fits = gop_fits && off <= kTailStageCap;
+        gop_max = std::max(gop_max, off);
+        const size_t m = 2 * (size_t)G[i][L - 1].nact;
+        all_fit = all_fit && off + m * m * sizeof(T) <= kTailStageCap;
+        all_max = std::max(all_max, off + m * m * sizeof(T));
+    }
+    size_t smem = 0;
+    if (gop_fits) {
+        pr.stage_gop = 1;
+        smem = gop_max;
+        if (all_fit) {
+            pr.stage_ainv = 1;
+            smem = all_max;
+        }
+    }
+    static std::mutex mu;
+    static bool raised[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64 || !raised[dev]) {
+            cudaFuncSetAttribute(k_tail_batched<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailStageCap);
+            if (dev >= 0 && dev < 64) raised[dev] = true;
+        }
+    }
+    launch_k(k_tail_batched<D, T>, (unsigned)K, kTailThreads, smem, s, (const TailLevel<T>* const*)dev_descs, active,
+             pr);
+    return 1;
+}
+
 template int upload_tail_desc<double>(const LevelGeo*, const LevelVec<double>*, int, void*, cudaStream_t);
 template int upload_tail_desc<float>(const LevelGeo*, const LevelVec<float>*, int, void*, cudaStream_t);
 template int launch_tail<2, double>(const void*, const LevelGeo*, int, int, const sulf_solver&, int, bool,
@@ -386,5 +447,12 @@ template int launch_tail<2, float>(const void*, const LevelGeo*, int, int, const
 template int launch_tail<3, double>(const void*, const LevelGeo*, int, int, const sulf_solver&, int, bool,
                                     cudaStream_t);
 template int launch_tail<3, float>(const void*, const LevelGeo*, int, int, const sulf_solver&, int, bool, cudaStream_t);
+#define SULF_INST_TAIL_BATCHED(D, T)                                                                            \
+    template int launch_tail_batched<D, T>(const void* const*, int, const int*, const LevelGeo* const*, int, int, \
+                                           const sulf_solver&, int, bool, cudaStream_t);
+SULF_INST_TAIL_BATCHED(2, double)
+SULF_INST_TAIL_BATCHED(2, float)
+SULF_INST_TAIL_BATCHED(3, double)
+SULF_INST_TAIL_BATCHED(3, float)
 
 }  // namespace sulf
