@@ -615,11 +615,12 @@ def run_batch(args):
                       "autotune_seconds": t_tune, "max_rel_err_vs_oracle_subset": acc[label]}
         for d in doms:
             d.close()
-    line = {"metric": METRIC, "value": out["batched_mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+    line = {"metric": METRIC, "value": out["lockstep_mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
             "config": {"workload": f"batch of {n_inst} random stars, sizes uniform in {{129,257,513,1025}}^2, dt = h",
-                       "precision": "mixed", "streams": args.streams, "cn_steps_per_instance": steps,
+                       "precision": "mixed", "mode": "lock-step, chunks of at most 32 instances",
+                       "streams": args.streams, "cn_steps_per_instance": steps,
                        "sequential_arm_steps": seq_steps,
                        "accuracy": "max relative difference from the oracle over s and c, 8-instance subset "
                                    "(two per size), 2 CN steps"},

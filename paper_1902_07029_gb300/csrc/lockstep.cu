@@ -222,6 +222,24 @@ __global__ void __launch_bounds__(kBT) kb_accumulate(const BLev<D, double>* __re
     }
 }
 
+// the FP64 defect of the mixed form written straight into the FP32
+// right-hand side of the next FP32 cycle, with each instance's max-norm
+template <int D>
+__global__ void __launch_bounds__(kBT) kb_residual_to32(const BLev<D, double>* __restrict__ l64,
+                                                         const BLev<D, float>* __restrict__ l32,
+                                                         const int* __restrict__ pre, int K,
+                                                         const int* __restrict__ active, unsigned long long* norms) {
+    const int i = find_instance(pre, K, blockIdx.x);
+    if (!active[i]) return;
+    const BLev<D, double>& V = l64[i];
+    const int t = (blockIdx.x - pre[i]) * kBT + threadIdx.x;
+    pdl_enter();
+    unsigned long long nb = 0;
+    if (t < V.ls.n0 + V.ls.n1 + V.ls.ng)
+        nb = stages::residual_node<D, double, false>(t, V.ls, V.tb, V.cf, V.rhs, V.x, l32[i].rhs, V.st1, V.st2);
+    block_max_to(nb, norms + i);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kBT) kb_to_float(const BLev<D, double>* __restrict__ l64,
                                                     const BLev<D, float>* __restrict__ l32,
@@ -282,9 +300,12 @@ int launch_batched(BPhase ph, const BLev<D, T>* lv, const BLev<D, T>* lc, const 
 
 template <int D>
 int launch_batched_mixed(BPhase ph, const BLev<D, double>* l64, const BLev<D, float>* l32, const int* pre,
-                         int nblocks, int K, const int* active, cudaStream_t s) {
+                         int nblocks, int K, const int* active, cudaStream_t s, unsigned long long* norms) {
     if (nblocks <= 0) return 0;
     switch (ph) {
+        case BPhase::residual_to32:
+            launch_k(kb_residual_to32<D>, (unsigned)nblocks, kBT, 0, s, l64, l32, pre, K, active, norms);
+            break;
         case BPhase::zero32:
             launch_k(kb_zero32<D>, (unsigned)nblocks, kBT, 0, s, l32, pre, K, active);
             break;
@@ -308,8 +329,8 @@ SULF_INST_BATCHED(3, double)
 SULF_INST_BATCHED(2, float)
 SULF_INST_BATCHED(3, float)
 template int launch_batched_mixed<2>(BPhase, const BLev<2, double>*, const BLev<2, float>*, const int*, int, int,
-                                     const int*, cudaStream_t);
+                                     const int*, cudaStream_t, unsigned long long*);
 template int launch_batched_mixed<3>(BPhase, const BLev<3, double>*, const BLev<3, float>*, const int*, int, int,
-                                     const int*, cudaStream_t);
+                                     const int*, cudaStream_t, unsigned long long*);
 
 }  // namespace sulf

@@ -42,7 +42,7 @@ struct BLev {
 };
 
 enum class BPhase { relax, relax_mf, ghost_op, residual, extend, restrict_to, prolong_from, coarsest, zero32,
-                    accumulate, to_float };
+                    accumulate, to_float, residual_to32 };
 
 // one launch of phase ph over the instances' work lists: CTA b serves the
 // instance i with pre[i] <= b < pre[i+1]; masked instances (active[i] == 0)
@@ -54,9 +54,11 @@ template <int D, typename T>
 int launch_batched(BPhase ph, const BLev<D, T>* lv, const BLev<D, T>* lc, const int* pre, int nblocks, int K,
                    const int* active, int colour, unsigned long long* norms, size_t smem, cudaStream_t s);
 // the mixed form's per-cycle steps on the finest level (zero the FP32 error,
-// accumulate it into the FP64 update, next FP32 right-hand side)
+// accumulate it into the FP64 update, next FP32 right-hand side from the FP64
+// defect: to_float converts a stored one, residual_to32 computes it with the
+// max-norms into norms)
 template <int D>
 int launch_batched_mixed(BPhase ph, const BLev<D, double>* l64, const BLev<D, float>* l32, const int* pre,
-                         int nblocks, int K, const int* active, cudaStream_t s);
+                         int nblocks, int K, const int* active, cudaStream_t s, unsigned long long* norms = nullptr);
 
 }  // namespace sulf

@@ -435,11 +435,19 @@ __device__ __forceinline__ void gop_group(bool on, int ln, int gi, const int* pt
 
 // defect r = rhs - J x at node p of kind 1 (inside, coefficients k) or 2
 // (ghost gi, its row and c-row q); returns max(|r_s|, |r_c|) as bits
-template <int D, typename T, bool CG>
+// the defect stored in res's element type (an FP64 defect into FP32: the
+// next right-hand side of the mixed form's FP32 cycle, rounded to nearest)
+__device__ __forceinline__ void store_res(double2* res, long long p, double2 r) { res[p] = r; }
+__device__ __forceinline__ void store_res(float2* res, long long p, float2 r) { res[p] = r; }
+__device__ __forceinline__ void store_res(float2* res, long long p, double2 r) {
+    res[p] = make_float2((float)r.x, (float)r.y);
+}
+
+template <int D, typename T, bool CG, typename R2>
 __device__ __forceinline__ unsigned long long residual_apply(long long p, int kind, int gi, const InsideCoef<D, T>& k,
                                                              const GhostTab<T>& tb, const Members<T>* pre,
                                                              typename V2<T>::t q, const typename V2<T>::t* rhs,
-                                                             const typename V2<T>::t* x, typename V2<T>::t* res,
+                                                             const typename V2<T>::t* x, R2* res,
                                                              long long st1, long long st2) {
     typedef typename V2<T>::t T2;
     T2 b = ldx<CG>(rhs + p);
@@ -455,7 +463,7 @@ __device__ __forceinline__ unsigned long long residual_apply(long long p, int ki
         r.x = b.x - acc;
         r.y = b.y - (q.x * xp.x + q.y * xp.y);
     }
-    res[p] = r;
+    store_res(res, p, r);
     unsigned long long a0 = abs_bits(r.x), a1 = abs_bits(r.y);
     return a0 > a1 ? a0 : a1;
 }
@@ -478,11 +486,11 @@ __device__ __forceinline__ long long fetch_residual(int t, const Lists& ls, cons
     return p;
 }
 
-template <int D, typename T, bool CG>
+template <int D, typename T, bool CG, typename R2>
 __device__ __forceinline__ unsigned long long residual_node(int t, const Lists& ls, const GhostTab<T>& tb,
                                                             const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
-                                                            const typename V2<T>::t* x, typename V2<T>::t* res,
-                                                            long long st1, long long st2) {
+                                                            const typename V2<T>::t* x, R2* res, long long st1,
+                                                            long long st2) {
     int kind, gi;
     InsideCoef<D, T> k;
     Members<T> m;

@@ -1802,11 +1802,12 @@ struct LockClass {
             cycle<double>(l64, 0);
         }
         SULF_CUDA_TRY(cudaMemsetAsync(dnorm, 0, sizeof(unsigned long long) * K, s));
-        launches += launch_batched<D, double>(BPhase::residual, l64[0], nullptr, act[0].d, act[0].total, K, dactive,
-                                              0, dnorm, 0, s);
-        if (mixed)
-            launches += launch_batched_mixed<D>(BPhase::to_float, l64[0], l32[0], act[0].d, act[0].total, K,
-                                                dactive, s);
+        if (mixed)  // the FP64 defect goes straight into the next FP32 right-hand side
+            launches += launch_batched_mixed<D>(BPhase::residual_to32, l64[0], l32[0], act[0].d, act[0].total, K,
+                                                dactive, s, dnorm);
+        else
+            launches += launch_batched<D, double>(BPhase::residual, l64[0], nullptr, act[0].d, act[0].total, K,
+                                                  dactive, 0, dnorm, 0, s);
         SULF_CUDA_TRY(cudaMemcpyAsync(hnorm, dnorm, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, s));
         return SULF_OK;
     }
