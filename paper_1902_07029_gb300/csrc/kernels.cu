@@ -132,7 +132,8 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2<T>::t* __restrict__ Wc,
                                                typename V2<T>::t* e0, typename V2<T>::t* e1, typename V2<T>::t* e2,
                                                typename V2<T>::t* Pa, typename V2<T>::t* Pb, typename V2<T>::t* Ia,
-                                               typename V2<T>::t* Ib, typename V2<T>::t* gc, T* gci, Coef<T> c) {
+                                               typename V2<T>::t* Ib, typename V2<T>::t* Pc, typename V2<T>::t* Ic,
+                                               typename V2<T>::t* gc, T* gci, Coef<T> c) {
     pdl_enter();
     typedef typename V2<T>::t T2;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,19 +171,24 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
         T Pss = ph * c.idt + c.a2mc * ph * cp + sg;
         T Psc = c.alpha * s * c.idt + c.a2mc * (c.alpha * s * cp + ph * s) + se;
         T inv = (T)1 / (Pss * Pcc - Psc * Pcs);
+        // box order and list order (t is the node's inside-list position)
         T2 v;
         v.x = Pss;
         v.y = Psc;
         Pa[p] = v;
+        Pc[2 * (long long)t] = v;
         v.x = Pcs;
         v.y = Pcc;
         Pb[p] = v;
+        Pc[2 * (long long)t + 1] = v;
         v.x = Pcc * inv;
         v.y = -Psc * inv;
         Ia[p] = v;
+        Ic[2 * (long long)t] = v;
         v.x = -Pcs * inv;
         v.y = Pss * inv;
         Ib[p] = v;
+        Ic[2 * (long long)t + 1] = v;
     } else {
         T2 v;
         v.x = Pcs;
@@ -197,8 +203,9 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
 
 // one colour of inside nodes; with snap_n > 0 also the copy of the ghosts' s
 // (nodes sidx) into snap that the composed ghost relaxation starts from
+// (t0: the position of the colour's list in the concatenated inside lists)
 template <int D, typename T, bool PW>
-__global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
+__global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, int t0, CoefPtr<D, T> cf,
                                                       const typename V2<T>::t* __restrict__ rhs,
                                                       typename V2<T>::t* __restrict__ x, long long st1, long long st2,
                                                       const int* __restrict__ sidx, int snap_n, T* snap) {
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
     stages::InsideCoef<D, T> k;
     if (t < cnt) {
         p = list[t];
-        k = stages::fetch_inside<D, T, PW>(p, cf, st);
+        k = stages::fetch_inside_at<D, T, PW>(p, t0 + t, cf, st);
     }
     const int sg = t < snap_n ? sidx[t] : 0;
     pdl_enter();
@@ -225,8 +232,8 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
 // and the register budget is set for six resident CTAs per SM (more warps to
 // hide the load latency); sulf_solver::relax_occupancy, FP64 collective only
 template <int D, typename T>
-__global__ void __launch_bounds__(kT, 6) k_relax_inside_ho(const int* __restrict__ list, int cnt, CoefPtr<D, T> cf,
-                                                            const typename V2<T>::t* __restrict__ rhs,
+__global__ void __launch_bounds__(kT, 6) k_relax_inside_ho(const int* __restrict__ list, int cnt, int t0,
+                                                            CoefPtr<D, T> cf, const typename V2<T>::t* __restrict__ rhs,
                                                             typename V2<T>::t* __restrict__ x, long long st1,
                                                             long long st2, const int* __restrict__ sidx, int snap_n,
                                                             T* snap) {
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kT, 6) k_relax_inside_ho(const int* __restrict
     pdl_enter();
     if (t < snap_n) snap[t] = reinterpret_cast<const T*>(x + sg)[0];
     if (t >= cnt) return;
-    stages::relax_node<D, T, false, false>(p, cf, rhs, x, st);
+    stages::relax_node_at<D, T, false, false>(p, t0 + t, cf, rhs, x, st);
 }
 
 // lexicographic collective Gauss-Seidel (Sec. 3.5.1, the paper's smoother):
@@ -1239,8 +1246,8 @@ int launch_coefs(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, cuda
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
-    launch_k(k_coefs<D, T>, grid_for(tot), block_for(tot), 0, s, ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa, V.Pb, V.Ia, V.Ib,
-                                            V.gc, V.gci, c);
+    launch_k(k_coefs<D, T>, grid_for(tot), block_for(tot), 0, s, ls, L.n, V.Wc, V.edge[0], V.edge[1], V.edge[2], V.Pa,
+             V.Pb, V.Ia, V.Ib, V.Pc, V.Ic, V.gc, V.gci, c);
     return 1;
 }
 
@@ -1267,13 +1274,14 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
                  reinterpret_cast<float*>(snap));
         return 1;
     }
+    const int t0 = colour ? L.nin[0] : 0;
     if (pointwise)
-        launch_k(k_relax_inside<D, T, true>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
+        launch_k(k_relax_inside<D, T, true>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, t0, cf,
                  V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     else
         launch_k(std::is_same<T, double>::value && launch_occupancy() ? k_relax_inside_ho<D, T>
                                                                        : k_relax_inside<D, T, false>,
-                 grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, cf,
+                 grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, t0, cf,
                  V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     return 1;
 }

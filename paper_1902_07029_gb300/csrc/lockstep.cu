@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kBT) kb_relax(const BLev<D, T>* __restrict__ l
     const int* list = colour ? L.ls.l1 : L.ls.l0;
     pdl_enter();
     if (colour == 1 && t < L.ls.ng) L.snap[t] = reinterpret_cast<const T*>(L.x + L.ls.lg[t])[0];
-    if (t < cnt) stages::relax_node<D, T, false, false>(list[t], L.cf, L.rhs, L.x, st);
+    if (t < cnt) stages::relax_node_at<D, T, false, false>(list[t], (colour ? L.ls.n0 : 0) + t, L.cf, L.rhs, L.x, st);
 }
 
 // the same with the coefficients formed from Wc (FP32): fewer bytes per

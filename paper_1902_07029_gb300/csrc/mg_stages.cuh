@@ -89,6 +89,9 @@ struct CoefPtr {
     const T2* Ia;
     const T2* Ib;
     const T2* gc;
+    // (Pa, Pb) and (Ia, Ib) per inside-list position (null: read the box arrays)
+    const T2* Pc;
+    const T2* Ic;
 };
 
 template <int D, typename T>
@@ -100,6 +103,8 @@ inline CoefPtr<D, T> coef_ptr(const LevelVec<T>& V) {
     c.Ia = V.Ia;
     c.Ib = V.Ib;
     c.gc = V.gc;
+    c.Pc = V.Pc;
+    c.Ic = V.Ic;
     return c;
 }
 
@@ -148,6 +153,28 @@ __device__ __forceinline__ InsideCoef<D, T> fetch_inside(long long p, const Coef
     }
     k.m0 = PW ? cf.Pa[p] : cf.Ia[p];
     k.m1 = PW ? cf.Pb[p] : cf.Ib[p];
+    return k;
+}
+
+// the same for the inside node p at position t of the inside lists, the 2x2
+// block (or its inverse) read from the list-ordered copy where there is one
+template <int D, typename T, bool PW>
+__device__ __forceinline__ InsideCoef<D, T> fetch_inside_at(long long p, int t, const CoefPtr<D, T>& cf,
+                                                            const long long* st) {
+    InsideCoef<D, T> k;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        k.ge[a] = cf.edge[a][p];
+        k.gw[a] = cf.edge[a][p - st[a]];
+    }
+    const typename V2<T>::t* c = PW ? cf.Pc : cf.Ic;
+    if (c) {
+        k.m0 = c[2 * (long long)t];
+        k.m1 = c[2 * (long long)t + 1];
+    } else {
+        k.m0 = PW ? cf.Pa[p] : cf.Ia[p];
+        k.m1 = PW ? cf.Pb[p] : cf.Ib[p];
+    }
     return k;
 }
 
@@ -264,6 +291,15 @@ template <int D, typename T, bool PW, bool CG>
 __device__ __forceinline__ void relax_node(long long p, const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
                                            typename V2<T>::t* x, const long long* st) {
     InsideCoef<D, T> k = fetch_inside<D, T, PW>(p, cf, st);
+    relax_apply<D, T, PW, CG>(p, k, rhs, x, st);
+}
+
+// the same for the node at position t of the inside lists
+template <int D, typename T, bool PW, bool CG>
+__device__ __forceinline__ void relax_node_at(long long p, int t, const CoefPtr<D, T>& cf,
+                                              const typename V2<T>::t* rhs, typename V2<T>::t* x,
+                                              const long long* st) {
+    InsideCoef<D, T> k = fetch_inside_at<D, T, PW>(p, t, cf, st);
     relax_apply<D, T, PW, CG>(p, k, rhs, x, st);
 }
 
@@ -478,7 +514,7 @@ __device__ __forceinline__ long long fetch_residual(int t, const Lists& ls, cons
     long long p = list_node(ls, t, kind, gi);
     if (kind == 1) {
         const long long st[3] = {1, st1, st2};
-        k = fetch_inside<D, T, true>(p, cf, st);
+        k = fetch_inside_at<D, T, true>(p, t, cf, st);
     } else {
         if (D == 2) fetch_members<T>(tb, gi, 0, m);
         q = cf.gc[gi];

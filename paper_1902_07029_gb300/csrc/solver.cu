@@ -260,9 +260,13 @@ int alloc_vectors(sulf_domain* d, LevelVec<T>* V, bool share_state) {
         v.Pb = (T2*)d->mem.get(nb2);
         v.Ia = (T2*)d->mem.get(nb2);
         v.Ib = (T2*)d->mem.get(nb2);
+        const size_t nc2 = sizeof(T2) * 2 * ((size_t)G.nin[0] + G.nin[1] + 1);
+        v.Pc = (T2*)d->mem.get(nc2);
+        v.Ic = (T2*)d->mem.get(nc2);
         v.gc = (T2*)d->mem.get(sizeof(T2) * (G.ng + 1));
         v.gci = (T*)d->mem.get(sizeof(T) * (G.ng + 1));
-        if (!v.Pa || !v.Pb || !v.Ia || !v.Ib || !v.gc || !v.gci || !v.edge[0] || !v.edge[1] || (G.dim == 3 && !v.edge[2]))
+        if (!v.Pa || !v.Pb || !v.Ia || !v.Ib || !v.Pc || !v.Ic || !v.gc || !v.gci || !v.edge[0] || !v.edge[1] ||
+            (G.dim == 3 && !v.edge[2]))
             return sulf_fail(SULF_ENOMEM, "out of device memory");
         if ((!share_state || l > 0) && !v.Wc) return sulf_fail(SULF_ENOMEM, "out of device memory");
         if (!v.rhs || !v.x || !v.res || !v.gbuf[0] || !v.gbuf[1])

@@ -131,6 +131,12 @@ struct LevelVec {
     T2* Pb = nullptr;  //               (J^cs_pp, J^cc_pp)
     T2* Ia = nullptr;  //               rows of the inverse of that 2x2 block
     T2* Ib = nullptr;
+    // the same blocks per position t of the inside lists (colour 0, then
+    // colour 1): (Pa, Pb) at 2t, 2t+1 of Pc and (Ia, Ib) of Ic.  A colour's
+    // sweep visits every other node of a box row, so box-ordered arrays give
+    // it half-used 32-byte sectors; these give it whole ones
+    T2* Pc = nullptr;
+    T2* Ic = nullptr;
     T2* gc = nullptr;  // per ghost: (J^cs_gg, J^cc_gg)
     T* gci = nullptr;  // per ghost: 1 / J^cc_gg (an FP64 division costs ~10 instructions
                        // of a pipe with two lanes per SM per clock: divided once per

@@ -100,6 +100,8 @@ __device__ __forceinline__ stages::CoefPtr<D, T> coefs_of(const TailLevel<T>& v)
     c.Ia = v.Ia;
     c.Ib = v.Ib;
     c.gc = v.gc;
+    c.Pc = nullptr;  // the fused levels read the box-ordered blocks
+    c.Ic = nullptr;
     return c;
 }
 
