@@ -502,7 +502,8 @@ def run_gpu(args):
 
 
 def run_batch(args):
-    """256 random-star instances, sizes uniform in {129, 257, 513, 1025}^2,
+    """256 random-star instances, sizes uniform in {129, 257, 513, 1025}^2
+    (--instances, --sizes),
     s_ext ~ U(0.5, 1), dt = h, advanced together by the batching runtime after
     the autotuner has picked each size's speed-only controls.  Arms: batched
     mixed precision, batched FP64, the same two in lock-step mode (the
@@ -518,7 +519,8 @@ def run_batch(args):
     pkg.build()
     rng = np.random.default_rng(4)
     n_inst = args.instances
-    sizes = [int(x) for x in rng.choice([128, 256, 512, 1024], size=n_inst)]
+    size_set = [int(x) for x in args.sizes.split(",")]
+    sizes = [int(x) for x in rng.choice(size_set, size=n_inst)]
     params = [workloads.random_star_params(rng) for _ in range(n_inst)]
     dts = [2.0 / N for N in sizes]
 
@@ -538,7 +540,7 @@ def run_batch(args):
 
     # accuracy on the subset: two instances per size, two CN steps, each arm
     subset = []
-    for N in (128, 256, 512, 1024):
+    for N in size_set:
         subset += [i for i in range(n_inst) if sizes[i] == N][:2]
     ref = {}
     for i in subset:
@@ -549,6 +551,9 @@ def run_batch(args):
         ref[i] = o.get_state()
     arms = (("batched_mixed", 1, "batched"), ("batched_fp64", 0, "batched"), ("lockstep_mixed", 1, "lockstep"),
             ("lockstep_fp64", 0, "lockstep"), ("sequential_fp64", 0, "sequential"))
+    if args.arms:
+        keep = args.arms.split(",")
+        arms = tuple(a for a in arms if a[0] in keep)
     acc = {}
     for label, precision, mode in arms:
         doms = make(subset, precision)
@@ -615,23 +620,28 @@ def run_batch(args):
                       "autotune_seconds": t_tune, "max_rel_err_vs_oracle_subset": acc[label]}
         for d in doms:
             d.close()
-    line = {"metric": METRIC, "value": out["lockstep_mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
-            "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
-            "data": "synthetic",
-            "config": {"workload": f"batch of {n_inst} random stars, sizes uniform in {{129,257,513,1025}}^2, dt = h",
-                       "precision": "mixed", "mode": "lock-step, chunks of at most 32 instances",
+    def ratio(a, b):
+        return out[a]["value"] / out[b]["value"] if a in out and b in out else None
+
+    head = next(a for a in ("lockstep_mixed", "batched_mixed", "lockstep_fp64", "batched_fp64", "sequential_fp64")
+                if a in out)
+    sizes_txt = ",".join(str(N + 1) for N in size_set)
+    line = {"metric": METRIC, "value": out[head]["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head.endswith("fp64") else "f64+f32", "data": "synthetic",
+            "config": {"workload": f"batch of {n_inst} random stars, sizes uniform in {{{sizes_txt}}}^2, dt = h",
+                       "value_arm": head, "lockstep_chunks": "at most 32 instances",
                        "streams": args.streams, "cn_steps_per_instance": steps,
                        "sequential_arm_steps": seq_steps,
-                       "accuracy": "max relative difference from the oracle over s and c, 8-instance subset "
-                                   "(two per size), 2 CN steps"},
+                       "accuracy": "max relative difference from the oracle over s and c, subset of two "
+                                   "instances per size, 2 CN steps"},
             "tuned": {str(k): v for k, v in sorted(tuned.items())} if tuned else None,
-            "batched_mixed": out["batched_mixed"], "batched_fp64": out["batched_fp64"],
-            "lockstep_mixed": out["lockstep_mixed"], "lockstep_fp64": out["lockstep_fp64"],
-            "sequential_fp64": out["sequential_fp64"],
-            "mixed_vs_fp64_batched": out["batched_mixed"]["value"] / out["batched_fp64"]["value"],
-            "lockstep_vs_batched": {"mixed": out["lockstep_mixed"]["value"] / out["batched_mixed"]["value"],
-                                    "fp64": out["lockstep_fp64"]["value"] / out["batched_fp64"]["value"]},
-            "batched_vs_sequential_fp64": out["batched_fp64"]["value"] / out["sequential_fp64"]["value"]}
+            "mixed_vs_fp64_batched": ratio("batched_mixed", "batched_fp64"),
+            "lockstep_vs_batched": {"mixed": ratio("lockstep_mixed", "batched_mixed"),
+                                    "fp64": ratio("lockstep_fp64", "batched_fp64")},
+            "batched_vs_sequential_fp64": ratio("batched_fp64", "sequential_fp64")}
+    for a in out:
+        line[a] = out[a]
     print(json.dumps(line), flush=True)
 
 
@@ -787,6 +797,9 @@ def main():
                     help="batch/serve: worker streams (256-instance batch, 10 steps: 42.8 M node-updates/s with 8, "
                          "58.1 M with 16, 58.9 M with 32)")
     ap.add_argument("--seq-steps", type=int, default=10, help="batch: CN steps of the sequential FP64 arm")
+    ap.add_argument("--sizes", default="128,256,512,1024", help="batch: grid sizes N the instances draw from")
+    ap.add_argument("--arms", default="", help="batch: comma list of arms to run (default all: batched_mixed, "
+                                                "batched_fp64, lockstep_mixed, lockstep_fp64, sequential_fp64)")
     ap.add_argument("--jobs", type=int, default=32, help="serve: number of jobs")
     ap.add_argument("--rate", default="auto",
                     help="serve: Poisson arrival rate(s) in jobs/s, comma-separated; auto = 0.5, 1, 2 x capacity")
