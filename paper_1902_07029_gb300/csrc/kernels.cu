@@ -575,12 +575,13 @@ __global__ void k_ghost_scatter(int ng, const int* __restrict__ gidx, const T* _
 // ---------------------------------------------------------------------------
 // defect r = rhs - J x on every active node, with its max-norm
 
-template <int D, typename T>
+// (R2: the element type the defect is stored in; an FP64 defect stored into
+// FP32 is the next right-hand side of the mixed form's FP32 cycle)
+template <int D, typename T, typename R2>
 __global__ void __launch_bounds__(kT) k_residual(Lists ls, GhostTab<T> tb, CoefPtr<D, T> cf,
                                                   const typename V2<T>::t* __restrict__ rhs,
-                                                  const typename V2<T>::t* __restrict__ x,
-                                                  typename V2<T>::t* __restrict__ res, long long st1, long long st2,
-                                                  unsigned long long* norm) {
+                                                  const typename V2<T>::t* __restrict__ x, R2* __restrict__ res,
+                                                  long long st1, long long st2, unsigned long long* norm) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool on = t < ls.n0 + ls.n1 + ls.ng;
     // lists, coefficients and ghost rows are fixed during the linear solve:
@@ -1341,10 +1342,25 @@ int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, u
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
     (void)c;
-    launch_k(k_residual<D, T>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<T>(L), coef_ptr<D, T>(V),
-             V.rhs, V.x, V.res, L.st[1], L.st[2], norm);
+    launch_k(k_residual<D, T, typename V2<T>::t>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<T>(L),
+             coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2], norm);
     return 1;
 }
+
+template <int D>
+int launch_residual_to32(const LevelGeo& L, const LevelVec<double>& V, float2* out, unsigned long long* norm,
+                         cudaStream_t s) {
+    Lists ls = make_lists(L);
+    int tot = ls.n0 + ls.n1 + ls.ng;
+    if (tot == 0) return 0;
+    launch_k(k_residual<D, double, float2>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<double>(L),
+             coef_ptr<D, double>(V), V.rhs, V.x, out, L.st[1], L.st[2], norm);
+    return 1;
+}
+template int launch_residual_to32<2>(const LevelGeo&, const LevelVec<double>&, float2*, unsigned long long*,
+                                     cudaStream_t);
+template int launch_residual_to32<3>(const LevelGeo&, const LevelVec<double>&, float2*, unsigned long long*,
+                                     cudaStream_t);
 
 template <int D, typename T>
 int launch_extend(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s) {

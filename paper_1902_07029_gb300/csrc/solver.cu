@@ -555,13 +555,15 @@ int cycle_body(sulf_domain* d, const cudaGraphConditionalHandle* loop = nullptr,
         d->launches += launch_accumulate(G0, V0.x, U0.x, d->stream);
     }
     SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 2, d->stream));
-    d->launches += launch_residual<D, double>(G0, V0, make_coef<double>(d, 0), d->dnorm, d->stream);
+    if (d->solver.precision == 1)  // straight into the next FP32 right-hand side
+        d->launches += launch_residual_to32<D>(G0, V0, d->v32[0].rhs, d->dnorm, d->stream);
+    else
+        d->launches += launch_residual<D, double>(G0, V0, make_coef<double>(d, 0), d->dnorm, d->stream);
     if (!loop) {
         SULF_CUDA_TRY(
             cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, d->stream));
         SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm + 6, d->dsing, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
     }
-    if (d->solver.precision == 1) d->launches += launch_to_float(G0, V0.res, d->v32[0].rhs, d->stream);
     if (loop) d->launches += launch_cycle_check(*loop, d->dnorm, d->dsing, d->dthr, max_cycles, d->dcyc, d->drn, d->stream);
     return SULF_OK;
 }

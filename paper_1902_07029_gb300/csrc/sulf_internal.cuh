@@ -224,6 +224,11 @@ int launch_relax_ghosts(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
 template <int D, typename T>
 int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, unsigned long long* norm,
                     cudaStream_t s);
+// the finest-level FP64 defect of the mixed form stored, rounded to FP32, as
+// the next FP32 right-hand side (the FP64 defect itself is not stored)
+template <int D>
+int launch_residual_to32(const LevelGeo& L, const LevelVec<double>& V, float2* out, unsigned long long* norm,
+                         cudaStream_t s);
 template <int D, typename T>
 int launch_extend(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t s);
 // first_red: also the red half of the coarse level's first relaxation from
