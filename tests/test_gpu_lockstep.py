@@ -49,6 +49,8 @@ def _specs():
 def _domain(sulfmg, sp, **solver):
     d = sulfmg.Domain(sp["phi"], sp["dim"], (-1.0, 1.0), sp["N"], sp["cN"])
     d.set_model(sp["model"])
+    if sp.get("bc"):
+        d.set_bc(sp["bc"])
     d.set_solver(**solver)
     return d
 
@@ -186,3 +188,34 @@ def test_lockstep_graphs_are_bitwise_neutral(sulfmg, precision):
         for ((s0, c0, _), a0), ((s1, c1, _), a1) in zip(o0, o1):
             assert np.array_equal(s0, s1) and np.array_equal(c0, c1)
             assert a0["cycles_total"] == a1["cycles_total"] and a0["newton_total"] == a1["newton_total"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lockstep_neumann_coarsest4_without_dependent_launch(sulfmg, oracle_mod, precision):
+    """a class of Neumann stars (Sec. 3.6 rows) and a class of 3-D boxes whose
+    hierarchy ends at a 5^3 coarsest grid, stepped in lock step with dependent
+    launch off, against the oracle"""
+    sp = []
+    for k in range(3):
+        x = _star_spec(128, 750 + k)
+        x.update(bc=1, dt=0.25 * 2.0 / 128)
+        sp.append(x)
+    for s_ext in (1.0, 0.8):
+        x = _box_spec(32, s_ext)
+        x.update(cN=4)
+        sp.append(x)
+    st, out = _run_lockstep(sulfmg, sp, precision=precision, pdl=0)
+    assert st == [0] * len(sp)
+    tol = RUN_TOL if precision == 0 else MIXED_TOL
+    for x, ((s, c, t), stats) in zip(sp, out):
+        ref = oracle_mod.Oracle(x["phi"], x["dim"], -1.0, 1.0, x["N"], x["cN"])
+        ref.set_model(x["model"])
+        if x.get("bc"):
+            ref.set_bc(x["bc"])
+        ref.set_solver()
+        ref.step(x["dt"], x["nsteps"])
+        rs, rc, rt = ref.get_state()
+        act = (rt == 1) | (rt == 2)
+        _close(s[act], rs[act], tol)
+        _close(c[act], rc[act], tol)
+        assert stats["steps_total"] == x["nsteps"]
