@@ -73,11 +73,10 @@ CYCLE_BYTES = {2: 344.0 * 4 / 3, 3: 344.0 * 8 / 7}
 # DRAM bytes (read + write) of one finest-level relaxation launch from an ncu
 # capture of the current kernel (cold cache), per workload and precision
 RELAX_TRAFFIC = {
-    # 129^3 capture (profiles/relax_inside_fp64_rbox129.md): 113.9 MB per
-    # 521 488 updates = 218.3 B per update, scaled to the 257^3 launch
-    ("rbox257", "fp64"): (218.3 * 4142122, "profiles/relax_inside_fp64_rbox129.md (218.3 B per update measured at "
-                                           "129^3, scaled to the 4 142 122 updates of a 257^3 launch)"),
-    ("star1025", "fp64"): (26.11e6 + 1.2e3, "profiles/relax_inside_fp64_star1025.md"),
+    # the FP64 relaxation reads the right-hand side in list order since its
+    # last capture: no traffic figure until it is captured again
+    ("rbox257", "fp64"): (None, "not captured since the list-ordered right-hand side"),
+    ("star1025", "fp64"): (None, "not captured since the list-ordered right-hand side"),
     # 129^3 capture of the matrix-free FP32 kernel (profiles/relax_mf_fp32_rbox129.md): 31.6 MB per
     # 521 488 updates = 60.6 B per update, scaled to the 257^3 launch
     ("rbox257", "mixed"): (60.6 * 4142122, "profiles/relax_mf_fp32_rbox129.md (60.6 B per update measured at "

@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(kT) k_coefs(Lists ls, int n, const typename V2
 template <int D, typename T, bool PW>
 __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ list, int cnt, int t0, CoefPtr<D, T> cf,
                                                       const typename V2<T>::t* __restrict__ rhs,
+                                                      const typename V2<T>::t* __restrict__ rhsc,
                                                       typename V2<T>::t* __restrict__ x, long long st1, long long st2,
                                                       const int* __restrict__ sidx, int snap_n, T* snap) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
     pdl_enter();
     if (t < snap_n) snap[t] = reinterpret_cast<const T*>(x + sg)[0];
     if (t >= cnt) return;
-    stages::relax_apply<D, T, PW, false>(p, k, rhs, x, st);
+    stages::relax_apply_b<D, T, PW, false>(p, k, rhsc ? rhsc[t0 + t] : rhs[p], x, st);
 }
 
 // The variant for large levels, where all but the first wave of CTAs start
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(kT) k_relax_inside(const int* __restrict__ lis
 template <int D, typename T>
 __global__ void __launch_bounds__(kT, 6) k_relax_inside_ho(const int* __restrict__ list, int cnt, int t0,
                                                             CoefPtr<D, T> cf, const typename V2<T>::t* __restrict__ rhs,
+                                                            const typename V2<T>::t* __restrict__ rhsc,
                                                             typename V2<T>::t* __restrict__ x, long long st1,
                                                             long long st2, const int* __restrict__ sidx, int snap_n,
                                                             T* snap) {
@@ -244,7 +246,8 @@ __global__ void __launch_bounds__(kT, 6) k_relax_inside_ho(const int* __restrict
     pdl_enter();
     if (t < snap_n) snap[t] = reinterpret_cast<const T*>(x + sg)[0];
     if (t >= cnt) return;
-    stages::relax_node_at<D, T, false, false>(p, t0 + t, cf, rhs, x, st);
+    const stages::InsideCoef<D, T> k = stages::fetch_inside_at<D, T, false>(p, t0 + t, cf, st);
+    stages::relax_apply_b<D, T, false, false>(p, k, rhsc ? rhsc[t0 + t] : rhs[p], x, st);
 }
 
 // lexicographic collective Gauss-Seidel (Sec. 3.5.1, the paper's smoother):
@@ -581,7 +584,8 @@ template <int D, typename T, typename R2>
 __global__ void __launch_bounds__(kT) k_residual(Lists ls, GhostTab<T> tb, CoefPtr<D, T> cf,
                                                   const typename V2<T>::t* __restrict__ rhs,
                                                   const typename V2<T>::t* __restrict__ x, R2* __restrict__ res,
-                                                  long long st1, long long st2, unsigned long long* norm) {
+                                                  long long st1, long long st2, unsigned long long* norm,
+                                                  const typename V2<T>::t* __restrict__ rhsc) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool on = t < ls.n0 + ls.n1 + ls.ng;
     // lists, coefficients and ghost rows are fixed during the linear solve:
@@ -596,7 +600,7 @@ __global__ void __launch_bounds__(kT) k_residual(Lists ls, GhostTab<T> tb, CoefP
     unsigned long long nb = 0;
     if (on)
         nb = stages::residual_apply<D, T, false>(p, kind, gi, k, tb, D == 2 ? &m : nullptr, q, rhs, x, res, st1,
-                                                 st2);
+                                                 st2, rhsc, t);
     if (norm) block_max(nb, norm);
 }
 
@@ -629,7 +633,7 @@ __global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restr
                                                   const typename V2<T>::t* __restrict__ fres,
                                                   typename V2<T>::t* __restrict__ crhs,
                                                   typename V2<T>::t* __restrict__ cx, CoefPtr<D, T> ccf,
-                                                  int first_red) {
+                                                  int first_red, typename V2<T>::t* __restrict__ crhsc) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool on = t < ls.n0 + ls.n1 + ls.ng;
     const bool red = on && first_red && t < ls.n0;
@@ -638,11 +642,11 @@ __global__ void __launch_bounds__(kT) k_restrict(Lists ls, const int8_t* __restr
     if (on) g = stages::fetch_restrict<D, T>(t, ls, ctype, cn, ftype, fn);  // fixed geometry, fetched ahead
     if (red) {
         const long long cst[3] = {1, cn, (long long)cn * cn};
-        k = stages::fetch_inside<D, T, PW>(g.I, ccf, cst);  // fixed coefficients, fetched ahead
+        k = stages::fetch_inside_at<D, T, PW>(g.I, t, ccf, cst);  // fixed coefficients, fetched ahead
     }
     pdl_enter();
     if (!on) return;
-    stages::restrict_apply<D, T, false, PW>(g, fn, fres, crhs, cx, red ? &k : nullptr);
+    stages::restrict_apply<D, T, false, PW>(g, fn, fres, crhs, cx, red ? &k : nullptr, crhsc, t);
 }
 
 // (bi/tri)linear interpolation of the coarse error to every fine active node,
@@ -1113,8 +1117,8 @@ __global__ void k_average_sources(long long nn, const double* __restrict__ f4, d
 
 template <int D>
 __global__ void __launch_bounds__(kT) k_newton_F(Lists ls, GhostTab<double> tb, const double2* __restrict__ W, const double2* __restrict__ G,
-                                                  double2* __restrict__ F, Offs<D> of, long long st1, long long st2,
-                                                  FConst f, unsigned long long* norm) {
+                                                  double2* __restrict__ F, double2* __restrict__ Fc, Offs<D> of,
+                                                  long long st1, long long st2, FConst f, unsigned long long* norm) {
     pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nb = 0;
@@ -1135,6 +1139,7 @@ __global__ void __launch_bounds__(kT) k_newton_F(Lists ls, GhostTab<double> tb, 
             out.x = stages::row_dot<D, double, false>(tb, gi, nullptr, W, nullptr, true) - (f.sbg ? f.sbg[gi] : f.sb);
         }
         F[p] = out;
+        if (Fc) Fc[t] = out;  // the list-ordered copy
         unsigned long long a0 = abs_bits(out.x), a1 = abs_bits(out.y);
         nb = a0 > a1 ? a0 : a1;
     }
@@ -1278,12 +1283,12 @@ int launch_relax_inside(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& 
     const int t0 = colour ? L.nin[0] : 0;
     if (pointwise)
         launch_k(k_relax_inside<D, T, true>, grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, t0, cf,
-                 V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
+                 V.rhs, V.rhsc, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     else
         launch_k(std::is_same<T, double>::value && launch_occupancy() ? k_relax_inside_ho<D, T>
                                                                        : k_relax_inside<D, T, false>,
                  grid_for(tot), block_for(tot), 0, s, L.inl[colour], cnt, t0, cf,
-                 V.rhs, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
+                 V.rhs, V.rhsc, V.x, L.st[1], L.st[2], L.gidx, sn, snap);
     return 1;
 }
 
@@ -1343,7 +1348,7 @@ int launch_residual(const LevelGeo& L, const LevelVec<T>& V, const Coef<T>& c, u
     if (tot == 0) return 0;
     (void)c;
     launch_k(k_residual<D, T, typename V2<T>::t>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<T>(L),
-             coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2], norm);
+             coef_ptr<D, T>(V), V.rhs, V.x, V.res, L.st[1], L.st[2], norm, V.rhsc);
     return 1;
 }
 
@@ -1354,7 +1359,7 @@ int launch_residual_to32(const LevelGeo& L, const LevelVec<double>& V, float2* o
     int tot = ls.n0 + ls.n1 + ls.ng;
     if (tot == 0) return 0;
     launch_k(k_residual<D, double, float2>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<double>(L),
-             coef_ptr<D, double>(V), V.rhs, V.x, out, L.st[1], L.st[2], norm);
+             coef_ptr<D, double>(V), V.rhs, V.x, out, L.st[1], L.st[2], norm, V.rhsc);
     return 1;
 }
 template int launch_residual_to32<2>(const LevelGeo&, const LevelVec<double>&, float2*, unsigned long long*,
@@ -1378,10 +1383,27 @@ int launch_restrict(const LevelGeo& F, const LevelVec<T>& FV, const LevelGeo& C,
     CoefPtr<D, T> ccf = coef_ptr<D, T>(CV);
     if (pointwise)
         launch_k(k_restrict<D, T, true>, grid_for(tot), block_for(tot), 0, s, ls, C.type, C.n, F.type, F.n, FV.res,
-                 CV.rhs, CV.x, ccf, first_red ? 1 : 0);
+                 CV.rhs, CV.x, ccf, first_red ? 1 : 0, CV.rhsc);
     else
         launch_k(k_restrict<D, T, false>, grid_for(tot), block_for(tot), 0, s, ls, C.type, C.n, F.type, F.n, FV.res,
-                 CV.rhs, CV.x, ccf, first_red ? 1 : 0);
+                 CV.rhs, CV.x, ccf, first_red ? 1 : 0, CV.rhsc);
+    return 1;
+}
+
+// a box-ordered vector gathered into list order (the rhsc copy of rhs)
+__global__ void k_gather_list(Lists ls, const double2* __restrict__ box, double2* __restrict__ list) {
+    pdl_enter();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ls.n0 + ls.n1 + ls.ng) return;
+    int kind, gi;
+    list[t] = box[list_node(ls, t, kind, gi)];
+}
+
+int launch_gather_list(const LevelGeo& L, const double2* box, double2* list, cudaStream_t s) {
+    Lists ls = make_lists(L);
+    const int tot = ls.n0 + ls.n1 + ls.ng;
+    if (tot == 0 || !list) return 0;
+    launch_k(k_gather_list, grid_for(tot), block_for(tot), 0, s, ls, box, list);
     return 1;
 }
 
@@ -1472,11 +1494,11 @@ int launch_old_time(const LevelGeo& L, const double2* Wn, double2* G, const FCon
 }
 
 template <int D>
-int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, double2* F, const FConst& fc,
-                    unsigned long long* norm, cudaStream_t s) {
+int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, double2* F, double2* Fc,
+                    const FConst& fc, unsigned long long* norm, cudaStream_t s) {
     Lists ls = make_lists(L);
     int tot = ls.n0 + ls.n1 + ls.ng;
-    launch_k(k_newton_F<D>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<double>(L), W, G, F,
+    launch_k(k_newton_F<D>, grid_for(tot), block_for(tot), 0, s, ls, stages::ghost_tab<double>(L), W, G, F, Fc,
              make_offs<D>(L.st[1], L.st[2]), L.st[1], L.st[2], fc, norm);
     return 1;
 }
@@ -1579,9 +1601,9 @@ SULF_INST(3, float)
 
 template int launch_old_time<2>(const LevelGeo&, const double2*, double2*, const FConst&, cudaStream_t);
 template int launch_old_time<3>(const LevelGeo&, const double2*, double2*, const FConst&, cudaStream_t);
-template int launch_newton_F<2>(const LevelGeo&, const double2*, const double2*, double2*, const FConst&,
+template int launch_newton_F<2>(const LevelGeo&, const double2*, const double2*, double2*, double2*, const FConst&,
                                 unsigned long long*, cudaStream_t);
-template int launch_newton_F<3>(const LevelGeo&, const double2*, const double2*, double2*, const FConst&,
+template int launch_newton_F<3>(const LevelGeo&, const double2*, const double2*, double2*, double2*, const FConst&,
                                 unsigned long long*, cudaStream_t);
 
 }  // namespace sulf

@@ -59,7 +59,12 @@ __global__ void __launch_bounds__(kBT) kb_relax(const BLev<D, T>* __restrict__ l
     const int* list = colour ? L.ls.l1 : L.ls.l0;
     pdl_enter();
     if (colour == 1 && t < L.ls.ng) L.snap[t] = reinterpret_cast<const T*>(L.x + L.ls.lg[t])[0];
-    if (t < cnt) stages::relax_node_at<D, T, false, false>(list[t], (colour ? L.ls.n0 : 0) + t, L.cf, L.rhs, L.x, st);
+    if (t < cnt) {
+        const int tl = (colour ? L.ls.n0 : 0) + t;
+        const long long p = list[t];
+        const stages::InsideCoef<D, T> k = stages::fetch_inside_at<D, T, false>(p, tl, L.cf, st);
+        stages::relax_apply_b<D, T, false, false>(p, k, L.rhsc ? L.rhsc[tl] : L.rhs[p], L.x, st);
+    }
 }
 
 // the same with the coefficients formed from Wc (FP32): fewer bytes per
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(kBT) kb_residual(const BLev<D, T>* __restrict_
     pdl_enter();
     unsigned long long nb = 0;
     if (t < L.ls.n0 + L.ls.n1 + L.ls.ng)
-        nb = stages::residual_node<D, T, false>(t, L.ls, L.tb, L.cf, L.rhs, L.x, L.res, L.st1, L.st2);
+        nb = stages::residual_node<D, T, false>(t, L.ls, L.tb, L.cf, L.rhs, L.x, L.res, L.st1, L.st2, L.rhsc);
     if (norms) block_max_to(nb, norms + i);
 }
 
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(kBT) kb_restrict(const BLev<D, T>* __restrict_
     const int t = (blockIdx.x - pre[i]) * kBT + threadIdx.x;
     pdl_enter();
     if (t < C.ls.n0 + C.ls.n1 + C.ls.ng)
-        stages::restrict_node<D, T, false>(t, C.ls, C.type, C.n, F.type, F.n, F.res, C.rhs, C.x);
+        stages::restrict_node<D, T, false>(t, C.ls, C.type, C.n, F.type, F.n, F.res, C.rhs, C.x, C.rhsc);
 }
 
 // (bi/tri)linear interpolation of the coarse error added to the fine one
@@ -236,7 +241,8 @@ __global__ void __launch_bounds__(kBT) kb_residual_to32(const BLev<D, double>* _
     pdl_enter();
     unsigned long long nb = 0;
     if (t < V.ls.n0 + V.ls.n1 + V.ls.ng)
-        nb = stages::residual_node<D, double, false>(t, V.ls, V.tb, V.cf, V.rhs, V.x, l32[i].rhs, V.st1, V.st2);
+        nb = stages::residual_node<D, double, false>(t, V.ls, V.tb, V.cf, V.rhs, V.x, l32[i].rhs, V.st1, V.st2,
+                                                     V.rhsc);
     block_max_to(nb, norms + i);
 }
 

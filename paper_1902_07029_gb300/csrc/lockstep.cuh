@@ -17,6 +17,7 @@ struct BLev {
     Coef<T> c;                   // the level's constants (matrix-free FP32 relaxation)
     const typename V2<T>::t* Wc; // the (s, c) the coefficients are formed from
     T2* rhs;
+    T2* rhsc;  // rhs per list position (FP64 levels; null for FP32)
     T2* x;
     T2* res;
     const int8_t* type;

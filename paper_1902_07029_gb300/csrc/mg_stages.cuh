@@ -182,10 +182,9 @@ __device__ __forceinline__ InsideCoef<D, T> fetch_inside_at(long long p, int t, 
 // inside node p from its fetched coefficients: x_p <- P^{-1} (b - (J - P) x),
 // resp. the diagonal of P
 template <int D, typename T, bool PW, bool CG>
-__device__ __forceinline__ void relax_apply(long long p, const InsideCoef<D, T>& k, const typename V2<T>::t* rhs,
-                                            typename V2<T>::t* x, const long long* st) {
+__device__ __forceinline__ void relax_apply_b(long long p, const InsideCoef<D, T>& k, typename V2<T>::t b,
+                                              typename V2<T>::t* x, const long long* st) {
     typedef typename V2<T>::t T2;
-    T2 b = ldx<CG>(rhs + p);
     T r = s_defect<D, T, CG>(b.x, p, k.ge, k.gw, x, st);
     T2 out;
     if (PW) {
@@ -197,6 +196,13 @@ __device__ __forceinline__ void relax_apply(long long p, const InsideCoef<D, T>&
         out.y = fmadd(k.m1.x, r, k.m1.y * b.y);
     }
     x[p] = out;
+}
+
+// the same with b = rhs(p)
+template <int D, typename T, bool PW, bool CG>
+__device__ __forceinline__ void relax_apply(long long p, const InsideCoef<D, T>& k, const typename V2<T>::t* rhs,
+                                            typename V2<T>::t* x, const long long* st) {
+    relax_apply_b<D, T, PW, CG>(p, k, ldx<CG>(rhs + p), x, st);
 }
 
 // Matrix-free FP32 collective update (Eq. matrixP with the Jacobian entries
@@ -479,14 +485,16 @@ __device__ __forceinline__ void store_res(float2* res, long long p, double2 r) {
     res[p] = make_float2((float)r.x, (float)r.y);
 }
 
+// (rhsc: the list-ordered copy of rhs, read at list position t, or null)
 template <int D, typename T, bool CG, typename R2>
 __device__ __forceinline__ unsigned long long residual_apply(long long p, int kind, int gi, const InsideCoef<D, T>& k,
                                                              const GhostTab<T>& tb, const Members<T>* pre,
                                                              typename V2<T>::t q, const typename V2<T>::t* rhs,
                                                              const typename V2<T>::t* x, R2* res,
-                                                             long long st1, long long st2) {
+                                                             long long st1, long long st2,
+                                                             const typename V2<T>::t* rhsc = nullptr, int t = 0) {
     typedef typename V2<T>::t T2;
-    T2 b = ldx<CG>(rhs + p);
+    T2 b = rhsc ? rhsc[t] : ldx<CG>(rhs + p);
     T2 xp = ldx<CG>(x + p);
     T2 r;
     if (kind == 1) {
@@ -526,13 +534,13 @@ template <int D, typename T, bool CG, typename R2>
 __device__ __forceinline__ unsigned long long residual_node(int t, const Lists& ls, const GhostTab<T>& tb,
                                                             const CoefPtr<D, T>& cf, const typename V2<T>::t* rhs,
                                                             const typename V2<T>::t* x, R2* res, long long st1,
-                                                            long long st2) {
+                                                            long long st2, const typename V2<T>::t* rhsc = nullptr) {
     int kind, gi;
     InsideCoef<D, T> k;
     Members<T> m;
     typename V2<T>::t q;
     long long p = fetch_residual<D, T>(t, ls, tb, cf, st1, st2, kind, gi, k, m, q);
-    return residual_apply<D, T, CG>(p, kind, gi, k, tb, D == 2 ? &m : nullptr, q, rhs, x, res, st1, st2);
+    return residual_apply<D, T, CG>(p, kind, gi, k, tb, D == 2 ? &m : nullptr, q, rhs, x, res, st1, st2, rhsc, t);
 }
 
 // The ghost defect extended into the band along the normal (Sec. 3.5.2): the
@@ -703,10 +711,13 @@ __device__ __forceinline__ RestrictGeo<D, T> fetch_restrict(int t, const Lists& 
 // centre with the weight moved to it); also zeroes the coarse error, or, for a
 // red inside node whose coefficients red holds, sets it to the first red
 // relaxation from zero (relax_value_zero)
+// (crhsc: the coarse level's list-ordered copy of its right-hand side, or
+// null; t: the coarse node's list position)
 template <int D, typename T, bool CG, bool PW = false>
 __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int fn, const typename V2<T>::t* fres,
                                                typename V2<T>::t* crhs, typename V2<T>::t* cx,
-                                               const InsideCoef<D, T>* red = nullptr) {
+                                               const InsideCoef<D, T>* red = nullptr,
+                                               typename V2<T>::t* crhsc = nullptr, int t = 0) {
     typedef typename V2<T>::t T2;
     const long long fst[3] = {1, fn, (long long)fn * fn};
     const int K = D == 2 ? 9 : 27;
@@ -755,6 +766,7 @@ __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int f
     out.x = as + wc * vc.x;
     out.y = ac + wc * vc.y;
     crhs[g.I] = out;
+    if (crhsc) crhsc[t] = out;
     T2 z;
     z.x = 0;
     z.y = 0;
@@ -764,9 +776,10 @@ __device__ __forceinline__ void restrict_apply(const RestrictGeo<D, T>& g, int f
 template <int D, typename T, bool CG>
 __device__ __forceinline__ void restrict_node(int t, const Lists& ls, const int8_t* ctype, int cn,
                                               const int8_t* ftype, int fn, const typename V2<T>::t* fres,
-                                              typename V2<T>::t* crhs, typename V2<T>::t* cx) {
+                                              typename V2<T>::t* crhs, typename V2<T>::t* cx,
+                                              typename V2<T>::t* crhsc = nullptr) {
     RestrictGeo<D, T> g = fetch_restrict<D, T>(t, ls, ctype, cn, ftype, fn);
-    restrict_apply<D, T, CG>(g, fn, fres, crhs, cx);
+    restrict_apply<D, T, CG>(g, fn, fres, crhs, cx, nullptr, crhsc, t);
 }
 
 // The fixed part of the (bi/tri)linear interpolation to fine active node i

@@ -46,11 +46,11 @@ extern "C" unsigned long long sulf_estimate_device_bytes(int dim, int N, int coa
     double nn0 = 1;
     for (int a = 0; a < dim; a++) nn0 *= (double)(N + 1);
     // bytes per box node: FP64 level vectors (Wc, rhs, x, res 64; edges 16 dim;
-    // 2x2 blocks and inverses 64, and their copies in list order, at most 64),
-    // geometry (phi, type, maps, lists, marks ~30), the finest level's W^n,
-    // old-time part and staging (49); FP32 vectors (32 + 8 dim + 32 + 32) when
-    // mixed; coarser levels add 1/(2^dim - 1)
-    double per_level = 192.0 + 16.0 * dim + 30.0;
+    // 2x2 blocks and inverses 64, and their copies and rhs's in list order, at
+    // most 80), geometry (phi, type, maps, lists, marks ~30), the finest
+    // level's W^n, old-time part and staging (49); FP32 vectors (32 + 8 dim +
+    // 32 + 32) when mixed; coarser levels add 1/(2^dim - 1)
+    double per_level = 208.0 + 16.0 * dim + 30.0;
     if (precision == 1) per_level += 96.0 + 8.0 * dim;
     double geo = 1.0 / (1.0 - 1.0 / (double)(1 << dim));
     // ghost-row member tables: 3^dim members x (weight 8 + 4, node 4, ghost

@@ -265,6 +265,12 @@ int alloc_vectors(sulf_domain* d, LevelVec<T>* V, bool share_state) {
         v.Ic = (T2*)d->mem.get(nc2);
         v.gc = (T2*)d->mem.get(sizeof(T2) * (G.ng + 1));
         v.gci = (T*)d->mem.get(sizeof(T) * (G.ng + 1));
+        if (std::is_same<T, double>::value) {
+            const size_t nl = sizeof(T2) * ((size_t)G.nin[0] + G.nin[1] + G.ng + 1);
+            v.rhsc = (T2*)d->mem.get(nl);
+            if (!v.rhsc) return sulf_fail(SULF_ENOMEM, "out of device memory");
+            SULF_CUDA_TRY(cudaMemsetAsync(v.rhsc, 0, nl, d->stream));
+        }
         if (!v.Pa || !v.Pb || !v.Ia || !v.Ib || !v.Pc || !v.Ic || !v.gc || !v.gci || !v.edge[0] || !v.edge[1] ||
             (G.dim == 3 && !v.edge[2]))
             return sulf_fail(SULF_ENOMEM, "out of device memory");
@@ -808,7 +814,7 @@ int cn_step(sulf_domain* d) {
     SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, d->stream));
     d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, d->stream);
     SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, d->stream));
-    d->launches += launch_newton_F<D>(G0, d->W, d->G, V0.rhs, fc, d->dnorm, d->stream);
+    d->launches += launch_newton_F<D>(G0, d->W, d->G, V0.rhs, V0.rhsc, fc, d->dnorm, d->stream);
     int rc = read_norms(d, 1);
     if (rc) return rc;
     double fn = bits_to_double(d->hnorm[0]);
@@ -827,7 +833,7 @@ int cn_step(sulf_domain* d) {
         d->cycles_total += nc;
         SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, d->stream));
         d->launches += launch_newton_update(G0, d->W, V0.x, d->dnorm, d->stream);
-        d->launches += launch_newton_F<D>(G0, d->W, d->G, V0.rhs, fc, d->dnorm + 2, d->stream);
+        d->launches += launch_newton_F<D>(G0, d->W, d->G, V0.rhs, V0.rhsc, fc, d->dnorm + 2, d->stream);
         rc = read_norms(d, 3);
         if (rc) return rc;
         double dn = bits_to_double(d->hnorm[0]), wn = bits_to_double(d->hnorm[1]);
@@ -1345,10 +1351,10 @@ int sulf_dbg_eval_F(sulf_handle h, double dt, const double* W, const double* Wn,
     SULF_CUDA_TRY(cudaMemsetAsync(h->dnorm, 0, 8, h->stream));
     if (h->dim == 2) {
         h->launches += launch_old_time<2>(G0, h->Wn, h->G, fc, h->stream);
-        h->launches += launch_newton_F<2>(G0, h->W, h->G, h->v64[0].rhs, fc, h->dnorm, h->stream);
+        h->launches += launch_newton_F<2>(G0, h->W, h->G, h->v64[0].rhs, h->v64[0].rhsc, fc, h->dnorm, h->stream);
     } else {
         h->launches += launch_old_time<3>(G0, h->Wn, h->G, fc, h->stream);
-        h->launches += launch_newton_F<3>(G0, h->W, h->G, h->v64[0].rhs, fc, h->dnorm, h->stream);
+        h->launches += launch_newton_F<3>(G0, h->W, h->G, h->v64[0].rhs, h->v64[0].rhsc, fc, h->dnorm, h->stream);
     }
     return dbg_copy_out(h, 0, h->v64[0].rhs, F, false);
 }
@@ -1362,6 +1368,7 @@ int sulf_dbg_apply_J(sulf_handle h, int l, double dt, const double* Wc, const do
     if (!rc) rc = copy_in(h, V.x, x, sizeof(double2) * G.nn);
     if (rc) return rc;
     SULF_CUDA_TRY(cudaMemsetAsync(V.rhs, 0, sizeof(double2) * G.nn, h->stream));
+    h->launches += launch_gather_list(G, V.rhs, V.rhsc, h->stream);
     if (h->dim == 2) {
         h->launches += launch_coefs<2, double>(G, V, make_coef<double>(h, l), h->stream);
         h->launches += launch_residual<2, double>(G, V, make_coef<double>(h, l), nullptr, h->stream);
@@ -1383,6 +1390,7 @@ int sulf_dbg_smooth(sulf_handle h, int l, double dt, const double* Wc, const dou
     h->dt = dt;
     int rc = copy_in(h, V.Wc, Wc, sizeof(double2) * G.nn);
     if (!rc) rc = copy_in(h, V.rhs, rhs, sizeof(double2) * G.nn);
+    if (!rc) h->launches += launch_gather_list(G, V.rhs, V.rhsc, h->stream);
     if (!rc) rc = copy_in(h, V.x, x, sizeof(double2) * G.nn);
     if (rc) return rc;
     if (h->dim == 2)
@@ -1449,6 +1457,7 @@ int sulf_dbg_coarsest_solve(sulf_handle h, double dt, const double* Wc0, const d
     rc = h->dim == 2 ? MG<2, double>{h, h->v64}.prepare() : MG<3, double>{h, h->v64}.prepare();
     if (rc) return rc;
     rc = copy_in(h, h->v64[lc].rhs, rhs_c, sizeof(double2) * h->geo[lc].nn);
+    if (!rc) h->launches += launch_gather_list(h->geo[lc], h->v64[lc].rhs, h->v64[lc].rhsc, h->stream);
     if (rc) return rc;
     if (h->dim == 2)
         h->launches += launch_coarsest_solve<2, double>(h->geo[lc], h->v64[lc], h->stream);
@@ -1484,6 +1493,7 @@ BLev<D, T> blev_of(sulf_domain* d, LevelVec<T>* V, int l) {
     b.c = make_coef<T>(d, l);
     b.Wc = v.Wc;
     b.rhs = v.rhs;
+    b.rhsc = v.rhsc;
     b.x = v.x;
     b.res = v.res;
     b.type = G.type;
@@ -1849,7 +1859,7 @@ int lockstep_step(LockClass<D>& C, LockGraphs<D>& P, int* status, std::vector<st
             SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, b));
             d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, b);
             SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, b));
-            d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm, b);
+            d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, d->v64[0].rhsc, fc, d->dnorm, b);
             SULF_CUDA_TRY(cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, b));
             return SULF_OK;
         });
@@ -1939,7 +1949,7 @@ int lockstep_step(LockClass<D>& C, LockGraphs<D>& P, int* status, std::vector<st
                 FConst fc = make_fconst(d);
                 SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, b));
                 d->launches += launch_newton_update(G0, d->W, d->v64[0].x, d->dnorm, b);
-                d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm + 2, b);
+                d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, d->v64[0].rhsc, fc, d->dnorm + 2, b);
                 SULF_CUDA_TRY(
                     cudaMemcpyAsync(d->hnorm, d->dnorm, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, b));
                 return SULF_OK;
@@ -2095,7 +2105,7 @@ int autotune(sulf_domain* d, double dt, sulf_tune_result* out) {
     SULF_CUDA_TRY(cudaMemcpyAsync(d->Wn, d->W, sizeof(double2) * G0.nn, cudaMemcpyDeviceToDevice, d->stream));
     d->launches += launch_old_time<D>(G0, d->Wn, d->G, fc, d->stream);
     SULF_CUDA_TRY(cudaMemsetAsync(d->dnorm, 0, sizeof(unsigned long long) * 4, d->stream));
-    d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, fc, d->dnorm, d->stream);
+    d->launches += launch_newton_F<D>(G0, d->W, d->G, d->v64[0].rhs, d->v64[0].rhsc, fc, d->dnorm, d->stream);
     if (int rc = read_norms(d, 1)) return rc;
     double fn = bits_to_double(d->hnorm[0]);
     if (!(fn > 0)) fn = 1.0;
@@ -2228,6 +2238,7 @@ int sulf_dbg_cycles(sulf_handle h, double dt, const double* Wc0, const double* r
     h->dt = dt;
     int rc = copy_in(h, h->W, Wc0, sizeof(double2) * G0.nn);
     if (!rc) rc = copy_in(h, h->v64[0].rhs, rhs, sizeof(double2) * G0.nn);
+    if (!rc) h->launches += launch_gather_list(G0, h->v64[0].rhs, h->v64[0].rhsc, h->stream);
     if (rc) return rc;
     // the cycles start from x = 0 inside linear_solve; a nonzero start is
     // folded into the right-hand side: J (x0 + y) = rhs  <=>  J y = rhs - J x0

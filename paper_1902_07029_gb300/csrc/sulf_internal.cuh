@@ -117,6 +117,11 @@ struct LevelVec {
     typedef typename V2<T>::t T2;
     T2* Wc = nullptr;   // (s, c) the Jacobian coefficients are evaluated at
     T2* rhs = nullptr;  // right-hand side of J x = rhs on this level
+    // FP64 levels: rhs again per list position (inside colour 0, colour 1,
+    // ghosts), written beside rhs by each of its writers (the Newton residual
+    // F, the restriction, the debug inputs); the colour sweeps and the
+    // residual read it in whole sectors.  Null for FP32 levels.
+    T2* rhsc = nullptr;
     T2* x = nullptr;    // unknown: Newton update (finest) or coarse-grid error
     T2* res = nullptr;  // defect rhs - J x (band entries: extended defect)
     T* gbuf[2] = {nullptr, nullptr};   // ghost s values between relaxation passes
@@ -250,9 +255,13 @@ int launch_coarsest_solve(const LevelGeo& L, const LevelVec<T>& V, cudaStream_t 
 
 template <int D>
 int launch_old_time(const LevelGeo& L, const double2* Wn, double2* G, const FConst& fc, cudaStream_t s);
+// the list-ordered copy (rhsc) of a level's box-ordered rhs, for inputs
+// written into rhs directly
+int launch_gather_list(const LevelGeo& L, const double2* box, double2* list, cudaStream_t s);
+// (Fc: the list-ordered copy of F, the finest level's rhsc, or null)
 template <int D>
-int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, double2* F, const FConst& fc,
-                    unsigned long long* norm, cudaStream_t s);
+int launch_newton_F(const LevelGeo& L, const double2* W, const double2* G, double2* F, double2* Fc,
+                    const FConst& fc, unsigned long long* norm, cudaStream_t s);
 int launch_newton_update(const LevelGeo& L, double2* W, const double2* x, unsigned long long* norms,
                          cudaStream_t s);
 int launch_norm_active(const LevelGeo& L, const double2* v, unsigned long long* norm, cudaStream_t s);
