@@ -73,10 +73,11 @@ CYCLE_BYTES = {2: 344.0 * 4 / 3, 3: 344.0 * 8 / 7}
 # DRAM bytes (read + write) of one finest-level relaxation launch from an ncu
 # capture of the current kernel (cold cache), per workload and precision
 RELAX_TRAFFIC = {
-    # the FP64 relaxation reads the right-hand side in list order since its
-    # last capture: no traffic figure until it is captured again
-    ("rbox257", "fp64"): (None, "not captured since the list-ordered right-hand side"),
-    ("star1025", "fp64"): (None, "not captured since the list-ordered right-hand side"),
+    # 129^3 capture (profiles/relax_inside_fp64_rbox129.md): 103.9 MB per
+    # 521 488 updates = 199.2 B per update, scaled to the 257^3 launch
+    ("rbox257", "fp64"): (199.2 * 4142122, "profiles/relax_inside_fp64_rbox129.md (199.2 B per update measured at "
+                                           "129^3, scaled to the 4 142 122 updates of a 257^3 launch)"),
+    ("star1025", "fp64"): (23.52e6 + 2.0e3, "profiles/relax_inside_fp64_star1025.md"),
     # 129^3 capture of the matrix-free FP32 kernel (profiles/relax_mf_fp32_rbox129.md): 31.6 MB per
     # 521 488 updates = 60.6 B per update, scaled to the 257^3 launch
     ("rbox257", "mixed"): (60.6 * 4142122, "profiles/relax_mf_fp32_rbox129.md (60.6 B per update measured at "
