@@ -7,7 +7,9 @@
 // as exact derivatives of F), refreshed once per Newton iteration by k_coefs:
 // per node the edge pair (g, e) toward each +axis neighbour and the inverse of
 // the 2x2 diagonal block, per ghost its c row.  Each relaxation is then a
-// handful of loads and fused multiply-adds per node.
+// handful of loads and fused multiply-adds per node.  The blocks and the FP64
+// right-hand side are also kept in inside-list order, which is the order the
+// colour sweeps and the residual visit nodes in.
 #include <atomic>
 #include <mutex>
 
@@ -124,8 +126,8 @@ __host__ __device__ inline Offs<D> make_offs(long long st1, long long st2) {
 }
 
 // stencil coefficients of every active node from Wc: edges toward the +axis
-// neighbours, and the 2x2 diagonal block and its inverse (inside) or the c
-// row (ghost).  Sec. 3.4: J^ss_pp = phi/dt + (a/2m_c) phi c + sum g,
+// neighbours, and the 2x2 diagonal block and its inverse (inside; in box order
+// and at the node's list position) or the c row (ghost).  Sec. 3.4: J^ss_pp = phi/dt + (a/2m_c) phi c + sum g,
 // J^sc_pp = alpha s/dt + (a/2m_c)(alpha s c + phi s) + sum e,
 // J^cs_pp = (a/2m_s) phi c, J^cc_pp = 1/dt + (a/2m_s)(alpha s c + phi s).
 template <int D, typename T>
