@@ -1476,7 +1476,9 @@ int sulf_dbg_coarsest_solve(sulf_handle h, double dt, const double* Wc0, const d
 // from then on, so every instance runs the iterations and cycles it runs
 // alone.  The Newton-level steps (old-time part, residual F, update, the
 // coefficients and the coarsest inverse of each Newton iteration) run per
-// instance on the class's stream.
+// instance, on up to eight forked branches of the class's stream.  Each
+// phase of a step (its start, a Newton iteration's set-up, a cycle, a Newton
+// update) is captured once as a CUDA graph and replayed.
 namespace {
 
 constexpr int kBatchT = 256;
