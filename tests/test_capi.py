@@ -52,6 +52,13 @@ def test_argument_errors_without_gpu(sulfmg):
     assert lib.sulf_levelset_from_mask(None, 2, 16, 4, out.ctypes.data_as(dp)) == sulfmg.EINVAL
     assert lib.sulf_set_bc(None, 1) == sulfmg.EINVAL
     assert lib.sulf_set_solver(None, None) == sulfmg.EINVAL
+    # batching: a NULL batch or bad arguments are refused before any device work
+    assert lib.sulf_batch_set_lockstep(None, 1) == sulfmg.EINVAL
+    assert lib.sulf_batch_step(None, None, None) == sulfmg.EINVAL
+    assert lib.sulf_batch_autotune(None, None, None) == sulfmg.EINVAL
+    assert lib.sulf_batch_status(None, None) == sulfmg.EINVAL
+    b = ctypes.c_void_p()
+    assert lib.sulf_batch_create(None, 2, 1, ctypes.byref(b)) == sulfmg.EINVAL and not b.value
     lib.sulf_destroy(None)
 
 
